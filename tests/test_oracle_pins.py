@@ -1,0 +1,473 @@
+"""Pins for the FP64 oracle against what the paper and mathematics fix.
+
+Nothing here compares the oracle with itself: every check uses an
+independent definition (a library routine, exact rational arithmetic,
+quadrature, brute-force enumeration, a hand-derived closed form or an
+invariant the paper states).
+"""
+import itertools
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.spatial
+import scipy.stats
+from scipy.spatial.transform import Rotation
+
+import oracle as O
+from paper_2603_16103_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_spd(rng, scale=1.0):
+    A = rng.normal(size=(3, 3))
+    return scale * (A @ A.T + 0.3 * np.eye(3))
+
+
+def sigma_of(ls, rot):
+    """Covariance from (log-scale, quaternion) through scipy's rotation."""
+    q = np.asarray(rot, dtype=np.float64)
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy is (x,y,z,w)
+    s2 = np.exp(2 * np.asarray(ls, dtype=np.float64))
+    return R @ np.diag(s2) @ R.T
+
+
+# ---------------------------------------------------------------- conversions
+
+def test_quat_to_R_matches_scipy():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        q = rng.normal(size=4) * rng.uniform(0.1, 3)
+        R = O.quat_to_R(q)
+        ref = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        assert np.allclose(R, ref, atol=1e-14)
+
+
+# ---------------------------------------------------------------- eigen (A11)
+
+def test_eig3_reconstruction_and_canonical_form():
+    rng = np.random.default_rng(2)
+    for t in range(300):
+        A = rand_spd(rng, 10 ** rng.uniform(-8, 2))
+        if t % 3 == 0:  # strongly anisotropic
+            R = Rotation.random(random_state=t).as_matrix()
+            A = R @ np.diag([1.0, 10 ** rng.uniform(-4, 0), 10 ** rng.uniform(-9, -5)]) @ R.T
+        lam, V, _ = O.eig3(A)
+        nrm = np.linalg.norm(A)
+        assert np.linalg.norm(V @ np.diag(lam) @ V.T - A) <= 1e-13 * nrm
+        assert np.allclose(V.T @ V, np.eye(3), atol=1e-13)
+        assert abs(np.linalg.det(V) - 1) < 1e-12
+        assert lam[0] >= lam[1] >= lam[2]
+        ref = np.linalg.eigvalsh(A)[::-1]          # LAPACK, independent
+        assert np.allclose(lam, ref, rtol=0, atol=1e-13 * nrm)
+        for c in range(2):  # canonical sign (column 3 may be flipped for det=+1)
+            col = V[:, c]
+            assert col[np.argmax(np.abs(col))] > 0
+
+
+def test_R_to_quat_roundtrip_scipy():
+    for t in range(100):
+        R = Rotation.random(random_state=100 + t).as_matrix()
+        q = O.R_to_quat(R)
+        assert q[0] >= 0 and abs(np.linalg.norm(q) - 1) < 1e-14
+        back = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        assert np.allclose(back, R, atol=1e-13)
+
+
+# ---------------------------------------------------------------- MPMM (A5, A9, A10)
+
+def test_mpmm_exact_rational():
+    """Sec. 3.3 equations evaluated in exact rational arithmetic."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        wi, wj = (Fraction(int(x), 7) for x in rng.integers(1, 50, 2))
+        mui = [Fraction(int(x), 3) for x in rng.integers(-9, 9, 3)]
+        muj = [Fraction(int(x), 5) for x in rng.integers(-9, 9, 3)]
+        Si = [[Fraction(0)] * 3 for _ in range(3)]
+        Sj = [[Fraction(0)] * 3 for _ in range(3)]
+        for r in range(3):
+            for c in range(r, 3):
+                Si[r][c] = Si[c][r] = Fraction(int(rng.integers(-5, 5)), 4) + (3 if r == c else 0)
+                Sj[r][c] = Sj[c][r] = Fraction(int(rng.integers(-5, 5)), 8) + (2 if r == c else 0)
+        W = wi + wj
+        mum = [(wi * a + wj * b) / W for a, b in zip(mui, muj)]
+        Sm = [[(wi * (Si[r][c] + (mui[r] - mum[r]) * (mui[c] - mum[c])) +
+                wj * (Sj[r][c] + (muj[r] - mum[r]) * (muj[c] - mum[c]))) / W
+               for c in range(3)] for r in range(3)]
+        fi, fj = [Fraction(1, 3), Fraction(-2)], [Fraction(5, 4), Fraction(7, 9)]
+        fm = [(wi * a + wj * b) / W for a, b in zip(fi, fj)]
+        g_mu, g_S, g_f = O.mpmm_moments(float(wi), np.array(mui, float), np.array(Si, float),
+                                        np.array(fi, float), float(wj), np.array(muj, float),
+                                        np.array(Sj, float), np.array(fj, float))
+        assert np.allclose(g_mu, np.array(mum, float), rtol=1e-14, atol=1e-14)
+        assert np.allclose(g_S, np.array(Sm, float), rtol=1e-13, atol=1e-13)
+        assert np.allclose(g_f, np.array(fm, float), rtol=1e-14, atol=1e-14)
+
+
+def _merge_one(si, sj, eig_floor=1e-30):
+    splats = tuple(np.stack([np.asarray(si[k], float), np.asarray(sj[k], float)])
+                   for k in range(5))
+    out = O.merge_compact(splats, [0], [1], eig_floor)
+    return tuple(a[0] for a in out)
+
+
+def _rand_splat(rng, F=48, ls_mean=-4.5):
+    return (rng.normal(size=3) * 0.05, rng.normal(ls_mean, 0.5, 3), rng.normal(size=4),
+            rng.normal(0, 1.5), rng.normal(0, 0.3, F))
+
+
+def test_mpmm_golden_hand_derived():
+    g = json.load(open(os.path.join(GOLDEN, "mpmm_two_unit_gaussians.json")))
+    si = [g["splat_i"][k] for k in ("xyz", "log_scale", "rot", "logit", "sh")]
+    sj = [g["splat_j"][k] for k in ("xyz", "log_scale", "rot", "logit", "sh")]
+    xyz, ls, rot, logit, sh = _merge_one(si, sj)
+    assert np.allclose(xyz, g["merged"]["xyz"], atol=1e-14)
+    assert np.allclose(sigma_of(ls, rot), np.diag(g["merged"]["Sigma_diag"]), atol=1e-13)
+    assert abs(logit - g["merged"]["logit"]) < 1e-13
+    assert np.allclose(sh, g["merged"]["sh"], atol=1e-14)
+
+
+def test_mpmm_moment_identities_and_invariants():
+    """W mu_m = sum w_c mu_c; W (Sigma_m + mu_m mu_m^T) = sum w_c (Sigma_c + mu_c mu_c^T);
+    Sigma_m SPD and above the mass-weighted average (Loewner); symmetric in i<->j;
+    opacity union; identical copy leaves mu, Sigma, f unchanged."""
+    rng = np.random.default_rng(4)
+    for t in range(200):
+        si, sj = _rand_splat(rng), _rand_splat(rng)
+        xyz, ls, rot, logit, sh = _merge_one(si, sj)
+        a_i, a_j = 1 / (1 + math.exp(-si[3])), 1 / (1 + math.exp(-sj[3]))
+        w_i = (2 * math.pi) ** 1.5 * a_i * math.exp(si[1].sum())
+        w_j = (2 * math.pi) ** 1.5 * a_j * math.exp(sj[1].sum())
+        W = w_i + w_j
+        S_i, S_j = sigma_of(si[1], si[2]), sigma_of(sj[1], sj[2])
+        S_m = sigma_of(ls, rot)
+        first = w_i * si[0] + w_j * sj[0]
+        assert np.allclose(W * xyz, first, rtol=1e-12, atol=1e-12 * np.abs(first).max())
+        M2 = w_i * (S_i + np.outer(si[0], si[0])) + w_j * (S_j + np.outer(sj[0], sj[0]))
+        assert np.linalg.norm(W * (S_m + np.outer(xyz, xyz)) - M2) <= 1e-12 * np.linalg.norm(M2)
+        assert np.all(np.linalg.eigvalsh(S_m) > 0)
+        avg = (w_i * S_i + w_j * S_j) / W
+        assert np.linalg.eigvalsh(S_m - avg).min() >= -1e-12 * np.linalg.norm(S_m)
+        assert np.allclose(sh, (w_i * si[4] + w_j * sj[4]) / W, atol=1e-13)
+        a_m = 1 / (1 + math.exp(-logit))
+        assert abs(a_m - (1 - (1 - a_i) * (1 - a_j))) < 1e-13
+        xyz2, ls2, rot2, logit2, sh2 = _merge_one(sj, si)      # swapped order
+        assert np.allclose(xyz2, xyz, atol=1e-15) and abs(logit2 - logit) < 1e-13
+        assert np.linalg.norm(sigma_of(ls2, rot2) - S_m) <= 1e-13 * np.linalg.norm(S_m)
+    si = _rand_splat(rng)
+    xyz, ls, rot, logit, sh = _merge_one(si, si)
+    a = 1 / (1 + math.exp(-si[3]))
+    assert np.allclose(xyz, si[0], atol=1e-15)
+    S = sigma_of(si[1], si[2])
+    assert np.linalg.norm(sigma_of(ls, rot) - S) <= 1e-13 * np.linalg.norm(S)
+    assert np.allclose(sh, si[4], atol=1e-15)
+    assert abs(1 / (1 + math.exp(-logit)) - (2 * a - a * a)) < 1e-13
+
+
+def test_merged_mass_is_not_W():
+    """The merged splat's own mass (2 pi)^{3/2} alpha_m prod s_m differs from W
+    in general (union opacity is sub-additive, the dispersion term inflates
+    the volume): a guard against 'conserving' w_m = W by mistake."""
+    rng = np.random.default_rng(5)
+    si, sj = _rand_splat(rng), _rand_splat(rng)
+    xyz, ls, rot, logit, sh = _merge_one(si, sj)
+    w = lambda l, s: (2 * math.pi) ** 1.5 / (1 + math.exp(-l)) * math.exp(np.sum(s))
+    W = w(si[3], si[1]) + w(sj[3], sj[1])
+    assert abs(w(logit, ls) - W) > 1e-3 * W
+
+
+# ---------------------------------------------------------------- KL helpers (A17)
+
+def test_kl_golden_and_idiv():
+    g = json.load(open(os.path.join(GOLDEN, "kl_closed_form.json")))
+    kl = O.kl_gauss(g["mu_i"], g["Sigma_i"], g["mu_j"], g["Sigma_j"])
+    assert abs(kl - g["kl"]) < 1e-14
+    idv = O.idiv_gauss(g["m_i"], g["mu_i"], g["Sigma_i"], g["m_j"], g["mu_j"], g["Sigma_j"])
+    assert abs(idv - g["idiv"]) < 1e-14
+
+
+def test_kl_closed_form_vs_monte_carlo_scipy():
+    rng = np.random.default_rng(6)
+    for _ in range(3):
+        mi, mj = rng.normal(size=3), rng.normal(size=3)
+        Si, Sj = rand_spd(rng), rand_spd(rng)
+        x = scipy.stats.multivariate_normal(mi, Si).rvs(size=400000, random_state=rng)
+        v = (scipy.stats.multivariate_normal(mi, Si).logpdf(x) -
+             scipy.stats.multivariate_normal(mj, Sj).logpdf(x))
+        se = v.std() / math.sqrt(v.size)
+        assert abs(O.kl_gauss(mi, Si, mj, Sj) - v.mean()) < 5 * se
+
+
+# ---------------------------------------------------------------- D_geo (A6)
+
+def _gh_kl(si, sj, order=40):
+    """KL(p~ || q_m) by Gauss-Hermite quadrature, with q_m the Gaussian of
+    p~'s own mean and covariance (both also by quadrature), scipy densities."""
+    t, w = np.polynomial.hermite.hermgauss(order)
+    T = np.stack(np.meshgrid(t, t, t, indexing="ij"), -1).reshape(-1, 3)
+    Wt = np.einsum("i,j,k->ijk", w, w, w).reshape(-1) / math.pi ** 1.5
+    comps = []
+    for s in (si, sj):
+        S = sigma_of(s[1], s[2])
+        L = np.linalg.cholesky(S)
+        comps.append((np.asarray(s[0], float), S, s[0] + math.sqrt(2) * T @ L.T))
+    a = [1 / (1 + math.exp(-s[3])) for s in (si, sj)]
+    lw = [math.log(a[c]) + float(np.sum((si, sj)[c][1])) for c in range(2)]
+    pi = 1 / (1 + math.exp(lw[1] - lw[0]))
+    wts = (pi, 1 - pi)
+    mean = sum(wts[c] * (Wt[:, None] * comps[c][2]).sum(0) for c in range(2))
+    second = sum(wts[c] * np.einsum("n,ni,nj->ij", Wt, comps[c][2], comps[c][2]) for c in range(2))
+    cov = second - np.outer(mean, mean)
+    q = scipy.stats.multivariate_normal(mean, cov)
+    ni = scipy.stats.multivariate_normal(comps[0][0], comps[0][1])
+    nj = scipy.stats.multivariate_normal(comps[1][0], comps[1][1])
+    total = 0.0
+    for c in range(2):
+        x = comps[c][2]
+        logp = np.logaddexp(math.log(pi) + ni.logpdf(x), math.log(1 - pi) + nj.logpdf(x))
+        total += wts[c] * np.sum(Wt * (logp - q.logpdf(x)))
+    return total
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_dgeo_large_sample_matches_quadrature(mode):
+    rng = np.random.default_rng(7)
+    for t in range(3):
+        si = (rng.normal(size=3) * 0.01, rng.normal(-4.5, 0.4, 3), rng.normal(size=4), rng.normal())
+        sj = (si[0] + rng.normal(size=3) * 0.012, rng.normal(-4.5, 0.4, 3), rng.normal(size=4),
+              rng.normal())
+        ref = _gh_kl(si, sj)
+        blocks = []
+        for b in range(16):
+            z, u = O.mc_draws(1000 + t, b, 20000)
+            blocks.append(O.dgeo_pair(si, sj, z, u, mode))
+        est, se = np.mean(blocks), np.std(blocks) / math.sqrt(len(blocks))
+        assert ref >= 0
+        assert abs(est - ref) < 5 * se + 1e-4, (est, ref, se)
+
+
+def test_dgeo_identical_is_zero_and_symmetric():
+    rng = np.random.default_rng(8)
+    z, u = O.mc_draws(3, 0, 4)
+    for _ in range(50):
+        si = (rng.normal(size=3), rng.normal(-4.5, 0.5, 3), rng.normal(size=4), rng.normal())
+        assert abs(O.dgeo_pair(si, si, z, u, 0)) < 1e-10
+        sj = (si[0] + rng.normal(size=3) * 0.01, rng.normal(-4.5, 0.5, 3), rng.normal(size=4),
+              rng.normal())
+        a, b = O.dgeo_pair(si, sj, z, u, 0), O.dgeo_pair(sj, si, z, u, 0)
+        assert abs(a - b) <= 1e-10 * max(1.0, abs(a))
+
+
+def test_edge_cost_appearance_term_and_weights():
+    rng = np.random.default_rng(9)
+    sc = synth.surfaces_unit_cube(300, seed=9)
+    lo = np.arange(0, 100, dtype=np.int32)
+    hi = lo + 100
+    z, u = O.mc_draws(0, 0, 1)
+    c, dg, da = O.edge_costs(sc, lo, hi, z, u, parts=True)
+    ref_da = np.sum((sc.sh[lo].astype(np.float64) - sc.sh[hi].astype(np.float64)) ** 2, axis=1)
+    assert np.allclose(da, ref_da, rtol=1e-14)
+    assert np.allclose(c, dg + da, rtol=1e-14)
+    c2 = O.edge_costs(sc, lo, hi, z, u, lambda_geo=0.5, lambda_app=2.0)
+    assert np.allclose(c2, 0.5 * dg + 2.0 * da, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- random numbers
+
+def test_mc_draws_distribution_and_determinism():
+    z, u = O.mc_draws(42, 7, 200000)
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+    assert scipy.stats.kstest(z[:, 2].astype(float), "norm").pvalue > 1e-3
+    assert 0 < u.min() and u.max() <= 1 and abs(u.mean() - 0.5) < 0.01
+    z2, u2 = O.mc_draws(42, 7, 200000)
+    assert np.array_equal(z, z2) and np.array_equal(u, u2)
+    z3, _ = O.mc_draws(42, 8, 4)
+    assert not np.array_equal(z[:4], z3)
+
+
+def test_splitmix64_published_vector():
+    """SplitMix64 from seed 0 yields 0xE220A8397B1DCDAF first (published
+    reference output of the generator); the oracle's first uniform must be
+    ((that >> 11) + 1) / 2^53."""
+    z, u = O.mc_draws(0, 0, 1)
+    first = 0xE220A8397B1DCDAF
+    u1 = ((first >> 11) + 1) / 2.0 ** 53
+    # Box-Muller radius of the first normal pair uses u1
+    r = math.sqrt(-2 * math.log(u1))
+    assert abs(math.hypot(float(z[0, 0]), float(z[0, 1])) - r) < 1e-6
+
+
+# ---------------------------------------------------------------- kNN (A3)
+
+def _check_knn_against_ckdtree(xyz, nbr, k):
+    tree = scipy.spatial.cKDTree(xyz.astype(np.float64))
+    d, idx = tree.query(xyz.astype(np.float64), k=k + 1)
+    for i in range(xyz.shape[0]):
+        ref = [j for j in idx[i] if j != i][:k]
+        got = list(nbr[i])
+        if got == ref:
+            continue
+        # only exact distance ties may reorder
+        dg = np.sum((xyz[got] - xyz[i]) ** 2, 1)
+        dr = np.sum((xyz[ref] - xyz[i]) ** 2, 1)
+        assert np.allclose(np.sort(dg), np.sort(dr), rtol=0, atol=0), i
+
+
+def test_knn_brute_vs_ckdtree():
+    sc = synth.surfaces_unit_cube(3000, seed=11)
+    nbr = O.knn(sc.xyz, 16, "brute")
+    _check_knn_against_ckdtree(sc.xyz.astype(np.float64), nbr, 16)
+
+
+def test_knn_order_ties_and_small_n():
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, 0, 0]], float)
+    nbr = O.knn(xyz, 3, "brute")
+    assert list(nbr[0]) == [4, 1, 2]      # d=0 duplicate first, then ties by index
+    assert list(nbr[4]) == [0, 1, 2]
+    assert O.knn(xyz[:2], 16).shape == (2, 1)
+    assert O.knn(xyz[:1], 16).shape[1] == 0
+    assert O.k_effective(5, 0) == 1 and O.k_effective(5, 16) == 4
+
+
+def test_knn_grid_equals_brute():
+    rng = np.random.default_rng(12)
+    cases = [synth.surfaces_unit_cube(4000, seed=12).xyz,
+             synth.patches_cube(5000, seed=13, frac_duplicate=0.05).xyz,
+             rng.uniform(size=(3000, 3)), np.repeat(rng.uniform(size=(300, 3)), 3, axis=0)]
+    for xyz in cases:
+        for k in (1, 5, 16):
+            assert np.array_equal(O.knn(xyz, k, "brute"), O.knn(xyz, k, "grid"))
+    q = np.array([0, 17, 999], dtype=np.int64)
+    full = O.knn(cases[0], 16, "brute")
+    assert np.array_equal(O.knn(cases[0], 16, queries=q), full[q])
+
+
+def test_union_edges_vs_python_sets():
+    sc = synth.surfaces_unit_cube(2000, seed=14)
+    nbr = O.knn(sc.xyz, 16, "grid")
+    lo, hi = O.union_edges(nbr)
+    ref = sorted({(min(i, int(j)), max(i, int(j))) for i in range(nbr.shape[0]) for j in nbr[i]})
+    assert list(zip(lo.tolist(), hi.tolist())) == ref
+    assert nbr.shape[0] * 16 / 2 <= len(ref) <= nbr.shape[0] * 16
+
+
+# ---------------------------------------------------------------- greedy (A12)
+
+def _all_matchings(edges):
+    for r in range(len(edges) + 1):
+        for sub in itertools.combinations(range(len(edges)), r):
+            used = set()
+            ok = True
+            for e in sub:
+                a, b = edges[e]
+                if a in used or b in used:
+                    ok = False
+                    break
+                used |= {a, b}
+            if ok:
+                yield set(sub)
+
+
+def test_greedy_exhaustive_characterisation():
+    """Greedy under a strict order is the unique matching in which every
+    non-member edge meets a member edge ranked before it."""
+    rng = np.random.default_rng(15)
+    for trial in range(25):
+        n = int(rng.integers(3, 8))
+        all_e = [(a, b) for a in range(n) for b in range(a + 1, n)]
+        m = int(rng.integers(1, min(9, len(all_e)) + 1))
+        edges = [all_e[i] for i in sorted(rng.choice(len(all_e), m, replace=False))]
+        lo = np.array([e[0] for e in edges], np.int32)
+        hi = np.array([e[1] for e in edges], np.int32)
+        for perm in itertools.islice(itertools.permutations(range(m)), 40):
+            cost = np.array(perm, float)
+            plo, phi = O.greedy(n, lo, hi, cost, n)
+            got = {edges.index((a, b)) for a, b in zip(plo.tolist(), phi.tolist())}
+            rank = {e: cost[e] for e in range(m)}
+            cert = [M for M in _all_matchings(edges)
+                    if all(any(rank[f] < rank[e] and set(edges[f]) & set(edges[e]) for f in M)
+                           for e in range(m) if e not in M)]
+            assert cert == [got]
+            # cap: first P picks are the P smallest members
+            for P in range(len(got) + 1):
+                clo, chi = O.greedy(n, lo, hi, cost, P)
+                sub = [edges.index((a, b)) for a, b in zip(clo.tolist(), chi.tolist())]
+                assert sorted(sub) == sorted(sorted(got, key=lambda e: rank[e])[:P])
+
+
+def test_greedy_ties_nan_negzero():
+    lo = np.array([0, 1, 0, 2], np.int32)
+    hi = np.array([1, 2, 3, 3], np.int32)
+    cost = np.array([1.0, 1.0, np.nan, -0.0])
+    plo, phi = O.greedy(4, lo, hi, cost, 4)
+    assert list(zip(plo, phi)) == [(2, 3), (0, 1)]
+    cost = np.array([np.nan, 5.0, np.inf, np.nan])
+    plo, phi = O.greedy(4, lo, hi, cost, 4)
+    assert list(zip(plo, phi)) == [(1, 2), (0, 3)]  # NaN ranks with +inf, then (lo,hi)
+
+
+# ---------------------------------------------------------------- prefilter (A1, A2)
+
+def test_prefilter_definition():
+    rng = np.random.default_rng(16)
+    for n in (1, 2, 7, 1000, 1001):
+        logit = rng.normal(0, 1.5, n)
+        keep, cnt = O.prefilter(logit, 0.005)
+        alpha = 1 / (1 + np.exp(-logit))
+        med = np.sort(alpha)[(n - 1) // 2]
+        ref = alpha >= min(0.005, med)
+        assert np.array_equal(keep, ref) and cnt == ref.sum()
+    logit = np.array([-9.0, -8.0, -7.0, -6.5, 3.0, -10.0])   # median alpha below tau
+    keep, cnt = O.prefilter(logit, 0.005)
+    alpha = 1 / (1 + np.exp(-logit))
+    assert cnt == np.sum(alpha >= np.sort(alpha)[2]) == 4
+
+
+def test_target_count():
+    assert O.target_count(20000, 0.5) == 10000
+    assert O.target_count(6_000_000, 0.1) == 600000
+    assert O.target_count(6_000_000, 0.01) == 60000
+    assert O.target_count(3, 0.1) == 1 and O.target_count(0, 0.5) == 1
+
+
+# ---------------------------------------------------------------- merge/compact order (A13)
+
+def test_merge_compact_slot_and_order():
+    sc = synth.surfaces_unit_cube(10, seed=17)
+    out = O.merge_compact(sc, [1, 4], [7, 5])
+    assert out[0].shape[0] == 8
+    keep = [0, 1, 2, 3, 4, 6, 8, 9]
+    for o, i in enumerate(keep):
+        if i in (1, 4):
+            continue
+        assert np.array_equal(out[0][o], sc.xyz[i].astype(np.float64))
+        assert np.array_equal(out[4][o], sc.sh[i].astype(np.float64))
+    with pytest.raises(ValueError):
+        O.merge_compact(sc, [1, 1], [7, 5])
+
+
+# ---------------------------------------------------------------- loop (A7, A13)
+
+def test_simplify_counts_and_loop_rules():
+    sc = synth.surfaces_unit_cube(3000, seed=18)
+    out, st = O.simplify(sc, 1500, use_grid=True)
+    keep, kept = O.prefilter(sc.logit)
+    assert st["n"][0] == kept
+    assert out[0].shape[0] == 1500
+    for a, b in zip(st["n"], st["n"][1:]):
+        assert b < a
+    for p in range(st["passes"]):
+        n = st["n"][p]
+        assert st["pairs"][p] <= min(n - 1500, n // 2)
+    out2, st2 = O.simplify(sc, 1500, use_grid=False)
+    assert all(np.array_equal(a, b) for a, b in zip(out, out2))
+    out3, st3 = O.simplify(sc, 5000)
+    assert st3["passes"] == 0 and out3[0].shape[0] == kept
+    out4, st4 = O.simplify(sc.subset(np.arange(1)), 1)
+    assert out4[0].shape[0] == 1 and st4["passes"] == 0
+    out5, st5 = O.simplify(sc, 1, max_passes=64)
+    assert out5[0].shape[0] == 1          # a graph exists until one splat is left
