@@ -1,0 +1,229 @@
+/*
+ * ngs.h -- C ABI of the GB300 (sm_103a) NanoGS simplification library.
+ *
+ * The library runs the simplification pass of NanoGS (Sec. 3, Algorithm 1):
+ * kNN merge graph -> per-edge merge cost -> disjoint pair selection -> MPMM
+ * merge + compaction, repeated until a target count is reached.  Every step
+ * runs in the library's own CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * General rules
+ *   - Every pointer inside ngs_splats and every array argument documented as
+ *     "device" is CUDA device memory owned by the caller, unless the field is
+ *     documented as ctx-owned.  Host pointers are documented as such.
+ *   - All work is enqueued on the stream given to ngs_create; calls that
+ *     return a count on the host synchronise that stream before returning.
+ *   - Functions return NGS_OK (0) or a negative NGS_ERR_* code and never
+ *     throw; ngs_last_error() returns a thread-local message for the last
+ *     failure on the calling thread.
+ *   - A ctx is not thread safe; use one ctx per host thread (or lock).
+ *   - Splat arrays are FP32, structure of arrays, row-major per splat:
+ *       xyz[n*3]            centre mu
+ *       log_scale[n*3]      log of the per-axis standard deviation s
+ *       rot[n*4]            quaternion (w, x, y, z); need not be unit
+ *       opacity_logit[n]    alpha = 1 / (1 + exp(-logit))
+ *       sh[n*sh_dim]        appearance feature f (SH coefficients)
+ *     Row i of every array belongs to splat i ("canonical index" i); every
+ *     tie-break in the method uses canonical indices.
+ */
+#ifndef NGS_H
+#define NGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define NGS_OK               0
+#define NGS_ERR_INVALID_ARG (-1) /* bad pointer, size, parameter or layout      */
+#define NGS_ERR_OOM         (-2) /* device or host allocation failed            */
+#define NGS_ERR_CUDA        (-3) /* a CUDA runtime call or launch failed        */
+#define NGS_ERR_TIMEOUT     (-4) /* a bounded device-side wait gave up          */
+#define NGS_ERR_BUDGET      (-5) /* the request does not fit the memory budget  */
+#define NGS_ERR_STATE       (-6) /* call order violated (e.g. no graph built)   */
+
+#define NGS_MAX_K   32   /* largest supported kNN size k                       */
+#define NGS_MAX_S   128  /* largest supported Monte Carlo sample count S       */
+
+typedef struct ngs_ctx ngs_ctx;
+
+/* A splat set in caller-owned device memory (see the layout above).
+ * n = live rows, cap = allocated rows (cap >= n), sh_dim = F (1..64). */
+typedef struct {
+    float  *xyz;
+    float  *log_scale;
+    float  *rot;
+    float  *opacity_logit;
+    float  *sh;
+    int64_t n;
+    int64_t cap;
+    int32_t sh_dim;
+} ngs_splats;
+
+/* Method parameters (Algorithm 1 inputs r, k, tau, cp; Sec. 4 defaults).
+ *   k           kNN size (Sec. 3.1; default 16; 1..NGS_MAX_K)
+ *   mc_samples  S, Monte Carlo samples per edge (App. A; default 1)
+ *   cost_mode   0: component-stratified common-random-number estimator
+ *               (pi g(x_i) + (1-pi) g(x_j)); 1: the literal mixture draw
+ *               (component i when u < pi).  Default 0.
+ *   tau         opacity pre-filter threshold (Algorithm 1; default 0.005)
+ *   lambda_geo, lambda_app  weights of D_geo and D_app in the cost
+ *               (Eq. Equ:cost has both at 1; default 1, 1)
+ *   seed        seed of the per-pass common random numbers
+ *   max_passes  upper bound on simplification passes (default 64)
+ *   fp64_policy 0: merged covariance eigendecomposition in FP64 and FP64
+ *               log-det for near-degenerate merged covariances (default);
+ *               1: additionally FP64 cost terms for edges with a
+ *               near-degenerate endpoint
+ *   prefilter   1: ngs_simplify first applies the opacity pre-filter
+ *   eig_floor   lower bound on merged covariance eigenvalues (default 1e-30)
+ */
+typedef struct {
+    int32_t  k;
+    int32_t  mc_samples;
+    int32_t  cost_mode;
+    double   tau;
+    float    lambda_geo;
+    float    lambda_app;
+    uint64_t seed;
+    int32_t  max_passes;
+    int32_t  fp64_policy;
+    int32_t  prefilter;
+    double   eig_floor;
+} ngs_params;
+
+/* The merge graph of one pass (Sec. 3.1, Algorithm 1 KNN and
+ * UndirectedUnionEdges).  All arrays are device memory owned by the ctx and
+ * stay valid until the next ngs_build_graph / ngs_simplify on that ctx.
+ *   n        vertex count
+ *   k_eff    min(max(1,k), n-1)
+ *   nbr      n*k_eff directed neighbours, row i sorted by (d^2, index)
+ *   n_edges  |E| (host value)
+ *   edge_lo, edge_hi  |E| undirected edges, edge_lo < edge_hi, sorted
+ *            lexicographically; the edge id is the position in this list
+ */
+typedef struct {
+    int64_t        n;
+    int32_t        k_eff;
+    int64_t        n_edges;
+    const int32_t *nbr;
+    const int32_t *edge_lo;
+    const int32_t *edge_hi;
+} ngs_graph;
+
+/* Per-call statistics (host struct, filled when a pointer is passed). */
+#define NGS_STATS_MAX_PASSES 64
+typedef struct {
+    int64_t n_input;        /* splats before the pre-filter                  */
+    int64_t n_filtered;     /* splats after the pre-filter                   */
+    int64_t n_output;       /* splats returned                               */
+    int32_t passes;         /* passes run                                    */
+    int32_t matching_rounds;/* locally-dominant rounds, summed over passes   */
+    int64_t pass_n[NGS_STATS_MAX_PASSES];     /* N at the start of pass p   */
+    int64_t pass_edges[NGS_STATS_MAX_PASSES]; /* |E| of pass p              */
+    int64_t pass_pairs[NGS_STATS_MAX_PASSES]; /* merged pairs of pass p     */
+    int64_t fp64_cost_edges;/* edges whose cost took the FP64 path           */
+    int64_t eig_floor_hits; /* merged eigenvalues raised to eig_floor        */
+    int64_t gpu_launches;   /* kernels the library launched for this call    */
+} ngs_stats;
+
+/* ---- lifecycle ---- */
+
+/* Fill *p with the defaults listed above.  Never fails. */
+void ngs_default_params(ngs_params *p);
+
+/* Create a context bound to the current CUDA device and `stream` (a
+ * cudaStream_t passed as void*; NULL = the legacy default stream).  The ctx
+ * owns every workspace; workspaces grow on demand and are reused.  p may be
+ * NULL for defaults.  Errors: INVALID_ARG (out of range parameter), OOM. */
+int ngs_create(ngs_ctx **ctx, const ngs_params *p, void *stream);
+
+/* Free the ctx and all its device workspaces (synchronises its stream). */
+int ngs_destroy(ngs_ctx *ctx);
+
+/* Replace the ctx's parameters (same validation as ngs_create). */
+int ngs_set_params(ngs_ctx *ctx, const ngs_params *p);
+
+/* Thread-local message describing the last failure ("" if none). */
+const char *ngs_last_error(void);
+
+/* ---- the pass, step by step ---- */
+
+/* Opacity pre-filter (Algorithm 1): tau' = min(tau, lower median alpha),
+ * keep splats with alpha >= tau' in their original order.  In place on
+ * *inout; sets inout->n to the kept count (host, synchronises).
+ * Errors: INVALID_ARG, CUDA. */
+int ngs_prefilter(ngs_ctx *ctx, ngs_splats *inout);
+
+/* kNN merge graph (Sec. 3.1, Algorithm 1 KNN + UndirectedUnionEdges): the
+ * k_eff nearest other centres by squared Euclidean distance (ties by
+ * canonical index), then the lexicographically sorted unique undirected
+ * edge list.  *out receives a ctx-owned view (see ngs_graph).  n <= 1 gives
+ * an empty graph.  Synchronises (n_edges is a host value).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int ngs_build_graph(ngs_ctx *ctx, const ngs_splats *splats, ngs_graph *out);
+
+/* Merge cost of every edge of `graph` (Sec. 3.2, Eq. Equ:cost; Monte Carlo
+ * estimator of App. A with the common random numbers of pass `pass`):
+ * cost[e] = lambda_geo * D_geo(e) + lambda_app * D_app(e), FP32, device
+ * array of graph->n_edges entries (caller-owned).  `graph` must be the
+ * current graph of this ctx built on the same splats.
+ * Errors: INVALID_ARG, STATE, CUDA. */
+int ngs_edge_costs(ngs_ctx *ctx, const ngs_splats *splats, const ngs_graph *graph,
+                   uint32_t pass, float *cost);
+
+/* Disjoint pair selection (Sec. 3.4, Algorithm 1 GreedyDisjointPairs): the
+ * greedy matching of `graph` under the strict order (cost, edge id) -- cost
+ * ascending, NaN ranked as +inf, -0 as +0 -- keeping its max_pairs smallest
+ * members.  Computed as a locally-dominant matching, which yields exactly
+ * that set.  pairs_out (device, caller-owned, 2*max_pairs int32) receives
+ * (lo, hi) rows sorted by lo; *n_pairs (host) the count.  Synchronises.
+ * Errors: INVALID_ARG, STATE, CUDA, TIMEOUT. */
+int ngs_select_pairs(ngs_ctx *ctx, const ngs_graph *graph, const float *cost,
+                     int64_t max_pairs, int32_t *pairs_out, int64_t *n_pairs);
+
+/* MPMM merge of each (lo, hi) pair (Sec. 3.3, Eqs. vm_weights, vm_cov,
+ * vm_alpha) followed by stream compaction: the merged splat takes row lo,
+ * row hi is removed, every other row keeps its relative order.  pairs is a
+ * device array of 2*n_pairs int32, vertex-disjoint, lo < hi (checked on the
+ * device; a violation returns INVALID_ARG and leaves *inout unchanged).
+ * In place; sets inout->n (host, synchronises).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int ngs_merge_compact(ngs_ctx *ctx, ngs_splats *inout, const int32_t *pairs, int64_t n_pairs);
+
+/* Algorithm 1 end to end on device-resident splats: optional pre-filter,
+ * then passes of graph -> costs -> pairs (at most n - target_count) ->
+ * merge + compaction while n > target_count, stopping early when a pass
+ * finds no pair.  In place; inout->n receives the final count.  The output
+ * equals running the four calls above pass by pass (pass index p for the
+ * random numbers).  stats may be NULL.
+ * Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
+int ngs_simplify(ngs_ctx *ctx, ngs_splats *inout, int64_t target_count, ngs_stats *stats);
+
+/* ngs_simplify for host-resident splats: copies the n rows of the host
+ * arrays (pinned or pageable) to ctx-owned device memory, simplifies, and
+ * copies the result rows back into the same host arrays (n updated).
+ * Errors: as ngs_simplify. */
+int ngs_simplify_host(ngs_ctx *ctx, ngs_splats *host_inout, int64_t target_count,
+                      ngs_stats *stats);
+
+/* ---- instrumentation ---- */
+
+/* When enabled, every kernel launch of the ctx is bracketed by CUDA events on
+ * the ctx stream and its device time is accumulated per kernel name. */
+int ngs_profile_enable(ngs_ctx *ctx, int enable);
+/* Number of distinct kernels profiled so far. */
+int ngs_profile_count(ngs_ctx *ctx);
+/* Kernel i: name (static string), launch count and summed milliseconds.
+ * Synchronises the ctx stream. */
+int ngs_profile_get(ngs_ctx *ctx, int i, const char **name, int64_t *launches, double *ms);
+int ngs_profile_reset(ngs_ctx *ctx);
+/* Total kernels launched by the ctx since creation (all calls). */
+int64_t ngs_launch_count(ngs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NGS_H */

@@ -1,0 +1,363 @@
+// Merge cost of every candidate edge (Sec. 3.2, Eq. Equ:cost; App. A).
+//
+// C(i,j) = lambda_geo * D_geo + lambda_app * D_app with
+//   D_app = || f_i - f_j ||^2 over all SH coefficients,
+//   D_geo = KL( pi N_i + (1-pi) N_j || N(mu_m, Sigma_m) ) estimated with S
+//           common standard-normal draws z_s shared by all edges of a pass,
+//   pi = w_i / (w_i + w_j), w = (2 pi)^{3/2} alpha prod s (Eq. vm_weights),
+//   (mu_m, Sigma_m) the MPMM moments (Eq. vm_cov).
+// Sample points use the symmetric square root, x_c = mu_c + Sigma_c^{1/2} z.
+// Writing every log-density relative to the merged Gaussian,
+//   g(x) = logsumexp(log pi + a_i - q_i(x)/2, log(1-pi) + a_j - q_j(x)/2) + q_m(x)/2,
+//   a_c  = log sqrt(det Sigma_m / det Sigma_c),  q_c = Mahalanobis^2 under c,
+// keeps FP32 cancellation small; q_c(x_c) = |z|^2 exactly.
+// Mode 0 averages pi g(x_i) + (1-pi) g(x_j) (the component draw integrated
+// out); mode 1 takes g(x_i) if u_s < pi else g(x_j).
+// A merged covariance whose FP32 Cholesky pivots are tiny relative to its
+// diagonal (near-degenerate) is redone entirely in FP64.
+#include "ngs_device.cuh"
+#include "ngs_internal.h"
+
+namespace {
+
+constexpr float LOG_2PI_F = 1.8378770664093453f;
+constexpr int REC = 32;  // floats per per-splat record
+
+// record layout
+enum {
+    R_MU = 0, R_LW = 3, R_R = 4, R_INVS = 13, R_SIG = 16, R_SUMLS = 22, R_SRATIO = 23,
+    R_Y0 = 24, R_S = 28
+};
+
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float *R) {
+    float inv = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// y = R diag(s) R^T z
+__device__ __forceinline__ void sym_sqrt_apply(const float *R, const float *s, const float *z,
+                                               float *y) {
+    float t[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) t[k] = s[k] * (R[k] * z[0] + R[3 + k] * z[1] + R[6 + k] * z[2]);
+#pragma unroll
+    for (int a = 0; a < 3; a++) y[a] = R[3 * a] * t[0] + R[3 * a + 1] * t[1] + R[3 * a + 2] * t[2];
+}
+
+__global__ void k_prep(const float *__restrict__ xyz, const float *__restrict__ ls,
+                       const float *__restrict__ rot, const float *__restrict__ logit, int64_t n,
+                       const float *__restrict__ zs, float *__restrict__ rec) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        float r[REC];
+        float R[9], s[3], l[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            r[R_MU + a] = xyz[3 * v + a];
+            l[a] = ls[3 * v + a];
+            s[a] = expf(l[a]);
+        }
+        quat_rot(rot[4 * v], rot[4 * v + 1], rot[4 * v + 2], rot[4 * v + 3], R);
+        float sum_ls = l[0] + l[1] + l[2];
+        r[R_LW] = 1.5f * LOG_2PI_F - softplusf(-logit[v]) + sum_ls;
+#pragma unroll
+        for (int k = 0; k < 9; k++) r[R_R + k] = R[k];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            r[R_INVS + a] = 1.0f / s[a];
+            r[R_S + a] = s[a];
+        }
+        float s2[3] = {s[0] * s[0], s[1] * s[1], s[2] * s[2]};
+        int idx = 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = a; b < 3; b++)
+                r[R_SIG + idx++] = R[3 * a] * s2[0] * R[3 * b] + R[3 * a + 1] * s2[1] * R[3 * b + 1] +
+                                   R[3 * a + 2] * s2[2] * R[3 * b + 2];
+        r[R_SUMLS] = sum_ls;
+        r[R_SRATIO] = fminf(fminf(s[0], s[1]), s[2]) / fmaxf(fmaxf(s[0], s[1]), s[2]);
+        float y[3];
+        sym_sqrt_apply(R, s, zs, y);
+        r[R_Y0] = y[0]; r[R_Y0 + 1] = y[1]; r[R_Y0 + 2] = y[2];
+        r[27] = 0.f;
+        r[31] = 0.f;
+        float4 *dst = (float4 *)(rec + (int64_t)v * REC);
+#pragma unroll
+        for (int k = 0; k < REC / 4; k++) dst[k] = make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
+    }
+}
+
+__device__ __forceinline__ float lse2(float a, float b) {
+    float m = fmaxf(a, b);
+    return m + log1pf(__expf(-fabsf(a - b)));
+}
+
+// |diag(inv_s) R^T v|^2
+__device__ __forceinline__ float maha_splat(const float *R, const float *invs, const float *v) {
+    float q = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float t = (R[k] * v[0] + R[3 + k] * v[1] + R[6 + k] * v[2]) * invs[k];
+        q += t * t;
+    }
+    return q;
+}
+
+// |L^{-1} v|^2 with L lower (l00, l10, l11, l20, l21, l22) and inverse diagonal
+__device__ __forceinline__ float maha_chol(const float *L, const float *il, const float *v) {
+    float y0 = v[0] * il[0];
+    float y1 = (v[1] - L[1] * y0) * il[1];
+    float y2 = (v[2] - L[3] * y0 - L[4] * y1) * il[2];
+    return y0 * y0 + y1 * y1 + y2 * y2;
+}
+
+// ---------------------------------------------------------------- FP64 path
+struct G64 {
+    double mu[3], R[9], s[3], Sig[6], sum_ls, lw;
+};
+
+__device__ void splat64(const float *xyz, const float *ls, const float *rot, const float *logit,
+                        int64_t v, G64 &g) {
+    double w = rot[4 * v], x = rot[4 * v + 1], y = rot[4 * v + 2], z = rot[4 * v + 3];
+    double nn = w * w + x * x + y * y + z * z;
+    double inv = 1.0 / sqrt(nn);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    double *R = g.R;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+    g.sum_ls = 0;
+    for (int a = 0; a < 3; a++) {
+        g.mu[a] = xyz[3 * v + a];
+        g.s[a] = exp((double)ls[3 * v + a]);
+        g.sum_ls += (double)ls[3 * v + a];
+    }
+    int idx = 0;
+    for (int a = 0; a < 3; a++)
+        for (int b = a; b < 3; b++) {
+            double acc = 0;
+            for (int k = 0; k < 3; k++) acc += R[3 * a + k] * g.s[k] * g.s[k] * R[3 * b + k];
+            g.Sig[idx++] = acc;
+        }
+    g.lw = 1.5 * 1.8378770664093454835606594728112 - softplus_d(-(double)logit[v]) + g.sum_ls;
+}
+
+__device__ double maha64_splat(const G64 &g, const double *v) {
+    double q = 0;
+    for (int k = 0; k < 3; k++) {
+        double t = (g.R[k] * v[0] + g.R[3 + k] * v[1] + g.R[6 + k] * v[2]) / g.s[k];
+        q += t * t;
+    }
+    return q;
+}
+
+__device__ double lse2_d(double a, double b) {
+    double m = fmax(a, b);
+    return m + log1p(exp(-fabs(a - b)));
+}
+
+__device__ double dgeo_fp64(const float *xyz, const float *ls, const float *rot,
+                            const float *logit, int64_t i, int64_t j, int S,
+                            const float *__restrict__ zs, const float *__restrict__ us, int mode) {
+    G64 gi, gj;
+    splat64(xyz, ls, rot, logit, i, gi);
+    splat64(xyz, ls, rot, logit, j, gj);
+    double ld = gi.lw - gj.lw;
+    double lpi = -softplus_d(-ld), lpj = -softplus_d(ld);
+    double pi = exp(lpi), pj = exp(lpj);
+    double d[3] = {gi.mu[0] - gj.mu[0], gi.mu[1] - gj.mu[1], gi.mu[2] - gj.mu[2]};
+    double Sm[6];
+    int idx = 0;
+    for (int a = 0; a < 3; a++)
+        for (int b = a; b < 3; b++, idx++) Sm[idx] = pi * gi.Sig[idx] + pj * gj.Sig[idx] + pi * pj * d[a] * d[b];
+    // Sm = (00 01 02 11 12 22)
+    double l00 = sqrt(Sm[0]);
+    double l10 = Sm[1] / l00, l20 = Sm[2] / l00;
+    double t11 = Sm[3] - l10 * l10;
+    if (!(t11 > 0)) return INFINITY;
+    double l11 = sqrt(t11);
+    double l21 = (Sm[4] - l20 * l10) / l11;
+    double t22 = Sm[5] - l20 * l20 - l21 * l21;
+    if (!(t22 > 0)) return INFINITY;
+    double l22 = sqrt(t22);
+    double half_ldm = log(l00) + log(l11) + log(l22);
+    double ai = half_ldm - gi.sum_ls, aj = half_ldm - gj.sum_ls;
+    double acc = 0;
+    for (int s = 0; s < S; s++) {
+        double z[3] = {zs[3 * s], zs[3 * s + 1], zs[3 * s + 2]};
+        double zz = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
+        double yi[3], yj[3];
+        for (int pass = 0; pass < 2; pass++) {
+            const G64 &g = pass == 0 ? gi : gj;
+            double *y = pass == 0 ? yi : yj;
+            double t[3];
+            for (int k = 0; k < 3; k++) t[k] = g.s[k] * (g.R[k] * z[0] + g.R[3 + k] * z[1] + g.R[6 + k] * z[2]);
+            for (int a = 0; a < 3; a++) y[a] = g.R[3 * a] * t[0] + g.R[3 * a + 1] * t[1] + g.R[3 * a + 2] * t[2];
+        }
+        double gvals[2];
+        for (int side = 0; side < 2; side++) {
+            // side 0: x = x_i, side 1: x = x_j ; offsets from each mean
+            double vi[3], vj[3], vm[3];
+            for (int a = 0; a < 3; a++) {
+                if (side == 0) {
+                    vi[a] = yi[a];
+                    vj[a] = d[a] + yi[a];
+                    vm[a] = pj * d[a] + yi[a];
+                } else {
+                    vi[a] = yj[a] - d[a];
+                    vj[a] = yj[a];
+                    vm[a] = yj[a] - pi * d[a];
+                }
+            }
+            double qi = side == 0 ? zz : maha64_splat(gi, vi);
+            double qj = side == 1 ? zz : maha64_splat(gj, vj);
+            double y0 = vm[0] / l00, y1 = (vm[1] - l10 * y0) / l11, y2 = (vm[2] - l20 * y0 - l21 * y1) / l22;
+            double qm = y0 * y0 + y1 * y1 + y2 * y2;
+            gvals[side] = lse2_d(lpi + ai - 0.5 * qi, lpj + aj - 0.5 * qj) + 0.5 * qm;
+        }
+        if (mode == 0) acc += pi * gvals[0] + pj * gvals[1];
+        else acc += ((double)us[s] < pi) ? gvals[0] : gvals[1];
+    }
+    return acc / S;
+}
+
+// ---------------------------------------------------------------- edge kernel
+__global__ void __launch_bounds__(256)
+    k_edge_cost(const int32_t *__restrict__ elo, const int32_t *__restrict__ ehi, int64_t m,
+                const float *__restrict__ rec, const float *__restrict__ sh, int F,
+                const float *__restrict__ zs, const float *__restrict__ us, int S, int mode,
+                float lg, float la, int policy, const float *__restrict__ xyz,
+                const float *__restrict__ ls, const float *__restrict__ rot,
+                const float *__restrict__ logit, float *__restrict__ cost,
+                unsigned long long *fp64_count) {
+    const float zz0 = zs[0] * zs[0] + zs[1] * zs[1] + zs[2] * zs[2];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = elo[e], j = ehi[e];
+        float ri[REC], rj[REC];
+        const float4 *pi4 = (const float4 *)(rec + i * REC), *pj4 = (const float4 *)(rec + j * REC);
+#pragma unroll
+        for (int k = 0; k < REC / 4; k++) {
+            float4 a = __ldg(pi4 + k), b = __ldg(pj4 + k);
+            ri[4 * k] = a.x; ri[4 * k + 1] = a.y; ri[4 * k + 2] = a.z; ri[4 * k + 3] = a.w;
+            rj[4 * k] = b.x; rj[4 * k + 1] = b.y; rj[4 * k + 2] = b.z; rj[4 * k + 3] = b.w;
+        }
+        // ---- appearance term
+        float dapp = 0.f;
+        if ((F & 3) == 0) {
+            const float4 *fi = (const float4 *)(sh + i * F), *fj = (const float4 *)(sh + j * F);
+            for (int t = 0; t < F / 4; t++) {
+                float4 a = __ldg(fi + t), b = __ldg(fj + t);
+                float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+                dapp += dx * dx + dy * dy + dz * dz + dw * dw;
+            }
+        } else {
+            for (int t = 0; t < F; t++) {
+                float df = sh[i * F + t] - sh[j * F + t];
+                dapp += df * df;
+            }
+        }
+        // ---- MPMM moments (Eqs. vm_weights, vm_cov)
+        const float ld = ri[R_LW] - rj[R_LW];
+        const float lpi = -softplusf(-ld), lpj = -softplusf(ld);
+        const float pi = __expf(lpi), pj = __expf(lpj);
+        float d[3] = {ri[R_MU] - rj[R_MU], ri[R_MU + 1] - rj[R_MU + 1], ri[R_MU + 2] - rj[R_MU + 2]};
+        const float ppd = pi * pj;
+        float Sm[6];
+        {
+            int idx = 0;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int b = a; b < 3; b++, idx++)
+                    Sm[idx] = pi * ri[R_SIG + idx] + pj * rj[R_SIG + idx] + ppd * d[a] * d[b];
+        }
+        // ---- Cholesky of Sigma_m (00 01 02 11 12 22)
+        float L[6], il[3];
+        L[0] = sqrtf(Sm[0]);
+        il[0] = 1.0f / L[0];
+        L[1] = Sm[1] * il[0];
+        L[3] = Sm[2] * il[0];
+        float t11 = Sm[3] - L[1] * L[1];
+        L[2] = sqrtf(fmaxf(t11, 0.f));
+        il[1] = 1.0f / L[2];
+        L[4] = (Sm[4] - L[3] * L[1]) * il[1];
+        float t22 = Sm[5] - L[3] * L[3] - L[4] * L[4];
+        L[5] = sqrtf(fmaxf(t22, 0.f));
+        il[2] = 1.0f / L[5];
+        bool flag = !(Sm[0] > 0.f) || !(t11 > 1e-5f * Sm[3]) || !(t22 > 1e-5f * Sm[5]);
+        if (policy == 1) flag = flag || ri[R_SRATIO] < 1e-3f || rj[R_SRATIO] < 1e-3f;
+        float dgeo;
+        if (!flag) {
+            // a_c = log sqrt(det Sm / det Sigma_c) as a product of O(1) ratios
+            const float ai = logf((L[0] * ri[R_INVS]) * (L[2] * ri[R_INVS + 1]) * (L[5] * ri[R_INVS + 2]));
+            const float aj = logf((L[0] * rj[R_INVS]) * (L[2] * rj[R_INVS + 1]) * (L[5] * rj[R_INVS + 2]));
+            const float ci = lpi + ai, cj = lpj + aj;
+            float acc = 0.f;
+            for (int s = 0; s < S; s++) {
+                float yi[3], yj[3], zz;
+                if (s == 0) {
+                    yi[0] = ri[R_Y0]; yi[1] = ri[R_Y0 + 1]; yi[2] = ri[R_Y0 + 2];
+                    yj[0] = rj[R_Y0]; yj[1] = rj[R_Y0 + 1]; yj[2] = rj[R_Y0 + 2];
+                    zz = zz0;
+                } else {
+                    const float z[3] = {zs[3 * s], zs[3 * s + 1], zs[3 * s + 2]};
+                    sym_sqrt_apply(ri + R_R, ri + R_S, z, yi);
+                    sym_sqrt_apply(rj + R_R, rj + R_S, z, yj);
+                    zz = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
+                }
+                // x = x_i
+                float v1[3] = {d[0] + yi[0], d[1] + yi[1], d[2] + yi[2]};
+                float v2[3] = {pj * d[0] + yi[0], pj * d[1] + yi[1], pj * d[2] + yi[2]};
+                float qj = maha_splat(rj + R_R, rj + R_INVS, v1);
+                float qm = maha_chol(L, il, v2);
+                const float gi = lse2(ci - 0.5f * zz, cj - 0.5f * qj) + 0.5f * qm;
+                // x = x_j
+                float w1[3] = {yj[0] - d[0], yj[1] - d[1], yj[2] - d[2]};
+                float w2[3] = {yj[0] - pi * d[0], yj[1] - pi * d[1], yj[2] - pi * d[2]};
+                float qi = maha_splat(ri + R_R, ri + R_INVS, w1);
+                float qm2 = maha_chol(L, il, w2);
+                const float gj = lse2(ci - 0.5f * qi, cj - 0.5f * zz) + 0.5f * qm2;
+                acc += mode == 0 ? (pi * gi + pj * gj) : (us[s] < pi ? gi : gj);
+            }
+            dgeo = acc / (float)S;
+        } else {
+            dgeo = (float)dgeo_fp64(xyz, ls, rot, logit, i, j, S, zs, us, mode);
+        }
+        unsigned fm = __ballot_sync(__activemask(), flag);
+        if (fm && (threadIdx.x & 31) == __ffs(fm) - 1) atomicAdd(fp64_count, (unsigned long long)__popc(fm));
+        cost[e] = lg * dgeo + la * dapp;
+    }
+}
+
+}  // namespace
+
+void edge_costs(ngs_ctx *c, const SplatView &s, const GraphDev &g, uint32_t pass, float *cost) {
+    const int64_t m = g.n_edges;
+    const int S = c->prm.mc_samples;
+    c->h_pin[1] = 0;  // FP64-path edge count of this call (filled below)
+    if (m <= 0) return;
+    // common random numbers of this pass
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    std::vector<float> h(4 * (size_t)S);
+    host_mc_draws(c->prm.seed, pass, S, h.data(), h.data() + 3 * S);
+    float *zs = ws<float>(c->b_rng, 4 * S);
+    NGS_CHECK_CUDA(cudaMemcpyAsync(zs, h.data(), sizeof(float) * 4 * S, cudaMemcpyHostToDevice,
+                                   c->st));
+    float *rec = ws<float>(c->b_rec, s.n * REC);
+    launch(c, "cost_prep", dim3(grid_stride_blocks(c, s.n, 256, 8)), dim3(256), 0, k_prep, s.xyz,
+           s.ls, s.rot, s.logit, s.n, (const float *)zs, rec);
+    unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c->b_status, 64);
+    NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, c->st));
+    launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0, k_edge_cost,
+           (const int32_t *)g.elo, (const int32_t *)g.ehi, m, (const float *)rec,
+           (const float *)s.sh, s.F, (const float *)zs, (const float *)(zs + 3 * S), S,
+           c->prm.cost_mode, c->prm.lambda_geo, c->prm.lambda_app, c->prm.fp64_policy,
+           (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
+           (const float *)s.logit, cost, cnt);
+    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin + 1, cnt, 8, cudaMemcpyDeviceToHost, c->st));
+}

@@ -1,0 +1,216 @@
+// Disjoint pair selection (Sec. 3.4, Algorithm 1 GreedyDisjointPairs).
+//
+// The greedy rule -- sort edges by cost, scan, take an edge when both
+// endpoints are free, stop after P picks -- is computed as a locally-dominant
+// matching under the same strict order (cost, lo canonical id, hi canonical
+// id), NaN ranked as +inf and -0 as +0:
+//   * every free vertex points at its best edge to a free neighbour;
+//   * mutual pointers are matched (such an edge is the minimum of all edges
+//     touching either endpoint, so greedy would take it too);
+//   * a vertex re-scans only when its target was matched elsewhere.
+// Under a strict total order this reaches exactly the greedy matching.  The
+// cap keeps the P smallest matched edges, which are the greedy's first P
+// picks, found by a radix select on (cost bits, lo canonical id).
+#include "ngs_device.cuh"
+#include "ngs_internal.h"
+
+namespace {
+
+__device__ __forceinline__ uint32_t cid_of(const int32_t *cid, int32_t v) {
+    return cid ? (uint32_t)cid[v] : (uint32_t)v;
+}
+
+__global__ void k_match_init(int64_t n, int32_t *mate, int32_t *cand) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        mate[v] = -1;
+        cand[v] = -2;  // unknown
+    }
+}
+
+// Re-scan the rows of free vertices whose pointer is unknown or stale.
+__global__ void k_match_scan(int64_t n, const int32_t *__restrict__ rstart,
+                             const int32_t *__restrict__ deg, const int32_t *__restrict__ adj,
+                             const int32_t *__restrict__ adj_eid, const float *__restrict__ cost,
+                             const int32_t *__restrict__ cid, const int32_t *__restrict__ mate,
+                             int32_t *cand, uint32_t *candkey) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (mate[v] != -1) continue;
+        int32_t c = cand[v];
+        if (c == -1) continue;                  // no free neighbour: stays single
+        if (c >= 0 && mate[c] == -1) continue;  // target still free: still the best
+        const uint32_t cv = cid_of(cid, (int32_t)v);
+        const int32_t rs = rstart[v];
+        const int d = deg[v];
+        int32_t best = -1;
+        uint32_t bk = 0xffffffffu, blo = 0xffffffffu, bhi = 0xffffffffu;
+        for (int t = 0; t < d; t++) {
+            int32_t u = adj[rs + t];
+            if (mate[u] != -1) continue;
+            uint32_t k = cost_order_bits(cost[adj_eid[rs + t]]);
+            uint32_t cu = cid_of(cid, u);
+            uint32_t lo = cv < cu ? cv : cu, hi = cv < cu ? cu : cv;
+            bool better = best < 0 || k < bk || (k == bk && (lo < blo || (lo == blo && hi < bhi)));
+            if (better) {
+                best = u;
+                bk = k;
+                blo = lo;
+                bhi = hi;
+            }
+        }
+        cand[v] = best;
+        candkey[v] = bk;
+    }
+}
+
+// Match mutual pointers; count new pairs of this round.
+__global__ void k_match_pair(int64_t n, const int32_t *__restrict__ cand, int32_t *mate,
+                             int32_t *round_count) {
+    int found = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (mate[v] != -1) continue;
+        int32_t u = cand[v];
+        if (u < 0) continue;
+        if (cand[u] == (int32_t)v) {
+            mate[v] = u;
+            if (v < u) found++;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(FULL_MASK, found, o);
+    if ((threadIdx.x & 31) == 0 && found) atomicAdd(round_count, found);
+}
+
+// 64-bit selection key of each matched pair at its lower-cid endpoint:
+// (cost bits << 32) | lo cid; other vertices get UINT64_MAX.
+__global__ void k_pair_keys(int64_t n, const int32_t *__restrict__ mate,
+                            const uint32_t *__restrict__ candkey, const int32_t *__restrict__ cid,
+                            uint64_t *keys) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = mate[v];
+        uint64_t k = ~0ull;
+        if (u >= 0) {
+            uint32_t cv = cid_of(cid, (int32_t)v), cu = cid_of(cid, u);
+            if (cv < cu) k = ((uint64_t)candkey[v] << 32) | cv;
+        }
+        keys[v] = k;
+    }
+}
+
+// partner[v] = mate[v] if the pair's key <= threshold (or no cap), else -1.
+__global__ void k_apply_cap(int64_t n, const int32_t *__restrict__ mate,
+                            const uint32_t *__restrict__ candkey, const int32_t *__restrict__ cid,
+                            const uint64_t *__restrict__ thr, int capped, int32_t *partner) {
+    const uint64_t T = capped ? *thr : ~0ull;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = mate[v];
+        int32_t p = -1;
+        if (u >= 0) {
+            uint32_t cv = cid_of(cid, (int32_t)v), cu = cid_of(cid, u);
+            uint64_t k = ((uint64_t)candkey[v] << 32) | (cv < cu ? cv : cu);
+            if (k <= T) p = u;
+        }
+        partner[v] = p;
+    }
+}
+
+__global__ void k_lo_flags(int64_t n, const int32_t *__restrict__ partner,
+                           const int32_t *__restrict__ cid, int32_t *flag) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = partner[v];
+        flag[v] = (u >= 0 && cid_of(cid, (int32_t)v) < cid_of(cid, u)) ? 1 : 0;
+    }
+}
+
+__global__ void k_write_pairs(int64_t n, const int32_t *__restrict__ partner,
+                              const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
+                              int32_t *pairs) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (flag[v]) {
+            int32_t p = pos[v];
+            pairs[2 * p] = (int32_t)v;
+            pairs[2 * p + 1] = partner[v];
+        }
+    }
+}
+
+}  // namespace
+
+int64_t select_pairs(ngs_ctx *c, const GraphDev &g, const float *cost, int64_t max_pairs,
+                     int32_t *partner) {
+    const int64_t n = g.n;
+    c->rounds = 0;
+    if (n <= 0) return 0;
+    int32_t *mate = ws<int32_t>(c->b_mate, n);
+    int32_t *cand = ws<int32_t>(c->b_cand, n);
+    uint32_t *candkey = ws<uint32_t>(c->b_candkey, n);
+    const int max_rounds = 4096;
+    int32_t *counts = ws<int32_t>(c->b_counts, max_rounds);
+    NGS_CHECK_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * max_rounds, c->st));
+    const unsigned grid = grid_stride_blocks(c, n, 256, 8);
+    launch(c, "match_init", dim3(grid), dim3(256), 0, k_match_init, n, mate, cand);
+    int64_t matched = 0;
+    int r = 0;
+    if (g.n_edges > 0 && max_pairs > 0) {
+        // rounds are launched in batches; a batch is checked once on the host
+        int batch = 4;
+        bool done = false;
+        while (!done) {
+            if (r + batch > max_rounds)
+                NGS_FAIL(NGS_ERR_TIMEOUT, "matching did not converge in %d rounds", max_rounds);
+            for (int b = 0; b < batch; b++, r++) {
+                launch(c, "match_scan", dim3(grid), dim3(256), 0, k_match_scan, n,
+                       (const int32_t *)g.rstart, (const int32_t *)g.deg, (const int32_t *)g.adj,
+                       (const int32_t *)g.adj_eid, cost, g.cid, (const int32_t *)mate, cand,
+                       candkey);
+                launch(c, "match_pair", dim3(grid), dim3(256), 0, k_match_pair, n,
+                       (const int32_t *)cand, mate, counts + r);
+            }
+            int32_t *hc = (int32_t *)(c->h_pin + 32);
+            NGS_CHECK_CUDA(cudaMemcpyAsync(hc, counts + r - batch, sizeof(int32_t) * batch,
+                                           cudaMemcpyDeviceToHost, c->st));
+            sync_stream(c);
+            for (int b = 0; b < batch; b++) {
+                matched += hc[b];
+                if (hc[b] == 0) {
+                    done = true;
+                    c->rounds = r - batch + b + 1;
+                    break;
+                }
+            }
+            batch = batch < 16 ? batch * 2 : 16;
+        }
+    }
+    const bool capped = matched > max_pairs;
+    uint64_t *thr = (uint64_t *)ws<uint8_t>(c->b_sel, 64);
+    if (capped) {
+        uint64_t *keys = (uint64_t *)ws<uint8_t>(c->b_flag, sizeof(uint64_t) * n);
+        launch(c, "pair_keys", dim3(grid), dim3(256), 0, k_pair_keys, n, (const int32_t *)mate,
+               (const uint32_t *)candkey, g.cid, keys);
+        radix_select_u64(c, keys, n, max_pairs - 1, thr);
+    }
+    launch(c, "apply_cap", dim3(grid), dim3(256), 0, k_apply_cap, n, (const int32_t *)mate,
+           (const uint32_t *)candkey, g.cid, (const uint64_t *)thr, capped ? 1 : 0, partner);
+    return capped ? max_pairs : matched;
+}
+
+int64_t partner_to_pairs(ngs_ctx *c, const int32_t *partner, const int32_t *cid, int64_t n,
+                         int32_t *pairs_out) {
+    if (n <= 0) return 0;
+    int32_t *flag = ws<int32_t>(c->b_keep, n + 1);
+    int32_t *pos = ws<int32_t>(c->b_pos, n + 1);
+    const unsigned grid = grid_stride_blocks(c, n, 256, 8);
+    launch(c, "lo_flags", dim3(grid), dim3(256), 0, k_lo_flags, n, partner, cid, flag);
+    scan_i32(c, flag, pos, n);
+    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin, pos + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+    launch(c, "write_pairs", dim3(grid), dim3(256), 0, k_write_pairs, n, partner,
+           (const int32_t *)flag, (const int32_t *)pos, pairs_out);
+    sync_stream(c);
+    return *(int32_t *)c->h_pin;
+}

@@ -1,0 +1,271 @@
+// Device-wide primitives: exclusive scan, stable LSD radix sort and radix
+// select.  Deterministic three-phase designs (no inter-block waiting).
+#include "ngs_device.cuh"
+#include "ngs_internal.h"
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Block-wide exclusive scan of one int per thread; returns the prefix and
+// the block total in *total.
+__device__ int block_excl_scan(int v, int *total) {
+    __shared__ int wsum[32];
+    __shared__ int wtot;
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = warp_incl_scan(v, lane);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    if (warp == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
+        int wi = warp_incl_scan(w, lane);
+        if (lane < nw) wsum[lane] = wi - w;
+        if (lane == nw - 1) wtot = wi;
+    }
+    __syncthreads();
+    int res = incl - v + wsum[warp];
+    *total = wtot;
+    __syncthreads();
+    return res;
+}
+
+__global__ void k_scan_reduce(const int32_t *__restrict__ in, int64_t n, int32_t *part) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int s = 0;
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; r++) {
+        int64_t i = base + r * SCAN_THREADS + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    int tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_partials(int32_t *part, int64_t nb) {
+    // single block: exclusive scan of part[0..nb) in chunks
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int v = i < nb ? part[i] : 0;
+        int tot;
+        int ex = block_excl_scan(v, &tot);
+        if (i < nb) part[i] = ex + carry;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[nb] = carry;
+}
+
+__global__ void k_scan_apply(const int32_t *in, int32_t *out, int64_t n, const int32_t *part) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int s = 0;
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; r++) {
+        int64_t i = base + r;
+        v[r] = i < n ? in[i] : 0;
+        s += v[r];
+    }
+    int tot;
+    int ex = block_excl_scan(s, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; r++) {
+        int64_t i = base + r;
+        if (i < n) out[i] = ex;
+        ex += v[r];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = part[gridDim.x];
+}
+
+// ---------------------------------------------------------------- radix sort
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+__global__ void k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
+                          int32_t *hist, int64_t ntiles) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        int64_t i = base + r * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: items of a tile are ranked in index order (round-major,
+// then thread) using warp match + per-warp digit counts.
+__global__ void k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
+                             int shift, const int32_t *__restrict__ offs, int64_t ntiles) {
+    __shared__ int run[256];
+    __shared__ int wc[RS_THREADS / 32][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    run[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ITEMS; r++) {
+#pragma unroll
+        for (int w = 0; w < RS_THREADS / 32; w++) wc[w][tid] = 0;
+        __syncthreads();
+        int64_t i = base + r * RS_THREADS + tid;
+        bool valid = i < n;
+        uint32_t key = valid ? kin[i] : 0u;
+        uint32_t val = valid ? vin[i] : 0u;
+        int d = valid ? (int)((key >> shift) & 255u) : 256 + lane;  // invalid: own group
+        unsigned peers = __match_any_sync(FULL_MASK, d);
+        int rank = __popc(peers & lt_mask);
+        int leader = __ffs(peers) - 1;
+        if (valid && lane == leader) wc[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            int p = run[tid];
+#pragma unroll
+            for (int w = 0; w < RS_THREADS / 32; w++) {
+                int t = wc[w][tid];
+                wc[w][tid] = p;
+                p += t;
+            }
+            run[tid] = p;
+        }
+        __syncthreads();
+        if (valid) {
+            int pos = wc[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- radix select
+// state: [0] prefix lo32, [1] prefix hi32, [2] mask lo, [3] mask hi, [4..5] rank (int64)
+struct SelState {
+    uint64_t prefix;
+    uint64_t mask;
+    int64_t rank;
+};
+
+__global__ void k_sel_init(SelState *s, int64_t k, int32_t *hist) {
+    if (threadIdx.x == 0) {
+        s->prefix = 0;
+        s->mask = 0;
+        s->rank = k;
+    }
+    hist[threadIdx.x] = 0;
+}
+
+template <class K>
+__global__ void k_sel_hist(const K *__restrict__ keys, int64_t n, const SelState *s, int shift,
+                           int32_t *hist, bool skip_max) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    uint64_t prefix = s->prefix, mask = s->mask;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = (uint64_t)keys[i];
+        if (skip_max && k == (uint64_t)(K)(~(K)0)) continue;
+        if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_sel_decide(SelState *s, int32_t *hist, int shift) {
+    __shared__ int h[256];
+    h[threadIdx.x] = hist[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t r = s->rank, cum = 0;
+        int d = 255;
+        for (int b = 0; b < 256; b++) {
+            if (r < cum + h[b]) {
+                d = b;
+                break;
+            }
+            cum += h[b];
+        }
+        s->rank = r - cum;
+        s->prefix |= (uint64_t)d << shift;
+        s->mask |= (uint64_t)255u << shift;
+    }
+    __syncthreads();
+    hist[threadIdx.x] = 0;
+}
+
+template <class K>
+__global__ void k_sel_out(const SelState *s, K *out) {
+    *out = (K)s->prefix;
+}
+
+}  // namespace
+
+void scan_i32(ngs_ctx *c, const int32_t *in, int32_t *out, int64_t n) {
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb < 1) nb = 1;
+    int32_t *part = ws<int32_t>(c->b_scan_part, nb + 1);
+    launch(c, "scan_reduce", dim3((unsigned)nb), dim3(SCAN_THREADS), 0, k_scan_reduce, in, n, part);
+    launch(c, "scan_partials", dim3(1), dim3(1024), 0, k_scan_partials, part, nb);
+    launch(c, "scan_apply", dim3((unsigned)nb), dim3(SCAN_THREADS), 0, k_scan_apply, in, out, n,
+           (const int32_t *)part);
+}
+
+void radix_sort_u32(ngs_ctx *c, uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp,
+                    uint32_t *vals_tmp, int64_t n, int bits) {
+    if (n <= 1) return;
+    int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    int32_t *hist = ws<int32_t>(c->b_hist, 256 * ntiles + 1);
+    uint32_t *ka = keys, *va = vals, *kb = keys_tmp, *vb = vals_tmp;
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; p++) {
+        int shift = 8 * p;
+        launch(c, "rs_hist", dim3((unsigned)ntiles), dim3(RS_THREADS), 0, k_rs_hist,
+               (const uint32_t *)ka, n, shift, hist, ntiles);
+        scan_i32(c, hist, hist, 256 * ntiles);
+        launch(c, "rs_scatter", dim3((unsigned)ntiles), dim3(RS_THREADS), 0, k_rs_scatter,
+               (const uint32_t *)ka, (const uint32_t *)va, kb, vb, n, shift,
+               (const int32_t *)hist, ntiles);
+        uint32_t *t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+    if (ka != keys) {
+        NGS_CHECK_CUDA(cudaMemcpyAsync(keys, ka, n * 4, cudaMemcpyDeviceToDevice, c->st));
+        NGS_CHECK_CUDA(cudaMemcpyAsync(vals, va, n * 4, cudaMemcpyDeviceToDevice, c->st));
+    }
+}
+
+template <class K>
+static void radix_select_impl(ngs_ctx *c, const K *keys, int64_t n, int64_t k, K *d_out,
+                              bool skip_max) {
+    uint8_t *misc = ws<uint8_t>(c->b_misc, 4096);
+    SelState *st = (SelState *)misc;
+    int32_t *hist = (int32_t *)(misc + 256);
+    launch(c, "sel_init", dim3(1), dim3(256), 0, k_sel_init, st, k, hist);
+    unsigned grid = grid_stride_blocks(c, n, 256, 4);
+    for (int shift = (int)(8 * sizeof(K)) - 8; shift >= 0; shift -= 8) {
+        launch(c, "sel_hist", dim3(grid), dim3(256), 0, k_sel_hist<K>, keys, n,
+               (const SelState *)st, shift, hist, skip_max);
+        launch(c, "sel_decide", dim3(1), dim3(256), 0, k_sel_decide, st, hist, shift);
+    }
+    launch(c, "sel_out", dim3(1), dim3(1), 0, k_sel_out<K>, (const SelState *)st, d_out);
+}
+
+void radix_select_u32(ngs_ctx *c, const uint32_t *keys, int64_t n, int64_t k, uint32_t *d_out) {
+    radix_select_impl<uint32_t>(c, keys, n, k, d_out, false);
+}
+
+void radix_select_u64(ngs_ctx *c, const uint64_t *keys, int64_t n, int64_t k, uint64_t *d_out) {
+    radix_select_impl<uint64_t>(c, keys, n, k, d_out, true);
+}

@@ -1,0 +1,603 @@
+// C ABI of the library (include/ngs.h): context, workspaces, instrumentation
+// and the host orchestration of the simplification pass (Algorithm 1).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <utility>
+
+#include "ngs_internal.h"
+
+// ---------------------------------------------------------------- errors
+static thread_local char g_err[512] = "";
+
+void ngs_set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+extern "C" const char *ngs_last_error(void) { return g_err; }
+
+#define API_BEGIN try {
+#define API_END                                         \
+    }                                                   \
+    catch (const NgsError &e) {                         \
+        return e.code;                                  \
+    }                                                   \
+    catch (...) {                                       \
+        ngs_set_error("unexpected host exception");     \
+        return NGS_ERR_CUDA;                            \
+    }                                                   \
+    return NGS_OK;
+
+// ---------------------------------------------------------------- workspace
+void *ws_get(DevBuf &b, size_t bytes) {
+    if (bytes <= b.bytes) return b.p;
+    if (b.p) {
+        NGS_CHECK_CUDA(cudaFree(b.p));  // implicit device sync: safe for in-flight work
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = bytes + bytes / 8 + 256;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        NGS_FAIL(NGS_ERR_OOM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    b.p = p;
+    b.bytes = want;
+    return p;
+}
+
+static void ws_free(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+void sync_stream(ngs_ctx *c) { NGS_CHECK_CUDA(cudaStreamSynchronize(c->st)); }
+
+// ---------------------------------------------------------------- profiling
+int prof_slot(ngs_ctx *c, const char *name) {
+    for (size_t i = 0; i < c->kstats.size(); i++)
+        if (strcmp(c->kstats[i].name, name) == 0) return (int)i;
+    c->kstats.push_back(KStat{name, 0, 0.0});
+    return (int)c->kstats.size() - 1;
+}
+
+static cudaEvent_t ev_get(ngs_ctx *c) {
+    if (!c->ev_free.empty()) {
+        cudaEvent_t e = c->ev_free.back();
+        c->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    NGS_CHECK_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+void prof_begin(ngs_ctx *c, int slot, cudaEvent_t *a) {
+    (void)slot;
+    *a = ev_get(c);
+    NGS_CHECK_CUDA(cudaEventRecord(*a, c->st));
+}
+
+static void prof_resolve(ngs_ctx *c) {
+    if (c->pending.empty()) return;
+    NGS_CHECK_CUDA(cudaStreamSynchronize(c->st));
+    for (auto &p : c->pending) {
+        float ms = 0.f;
+        NGS_CHECK_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+        c->kstats[p.stat].launches++;
+        c->kstats[p.stat].ms += ms;
+        c->ev_free.push_back(p.a);
+        c->ev_free.push_back(p.b);
+    }
+    c->pending.clear();
+}
+
+void prof_end(ngs_ctx *c, int slot, cudaEvent_t a) {
+    cudaEvent_t b = ev_get(c);
+    NGS_CHECK_CUDA(cudaEventRecord(b, c->st));
+    c->pending.push_back(PendingEv{slot, a, b});
+    if (c->pending.size() > 4096) prof_resolve(c);
+}
+
+// ---------------------------------------------------------------- random numbers
+// SplitMix64 (Steele, Lea & Flood, 2014): a Weyl sequence with increment
+// 0x9E3779B97F4A7C15 passed through a 64-bit finaliser.  Pass p starts from
+// seed XOR (p * 0xD1B54A32D192ED03).  Uniforms take the top 53 bits, (0, 1].
+// Normals use the Box-Muller transform (Box & Muller, 1958) in FP64.
+namespace {
+struct SplitMix {
+    uint64_t x;
+    uint64_t next() {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t r = x;
+        r ^= r >> 30;
+        r *= 0xBF58476D1CE4E5B9ull;
+        r ^= r >> 27;
+        r *= 0x94D049BB133111EBull;
+        r ^= r >> 31;
+        return r;
+    }
+    double unit() { return (double)((next() >> 11) + 1) / 9007199254740992.0; }
+};
+}  // namespace
+
+void host_mc_draws(uint64_t seed, uint32_t pass, int S, float *z, float *u) {
+    SplitMix g{seed ^ ((uint64_t)pass * 0xD1B54A32D192ED03ull)};
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int s = 0; s < S; s++) {
+        double a = g.unit(), b = g.unit(), cc = g.unit(), dd = g.unit();
+        double ra = sqrt(-2.0 * log(a)), rc = sqrt(-2.0 * log(cc));
+        z[3 * s] = (float)(ra * cos(two_pi * b));
+        z[3 * s + 1] = (float)(ra * sin(two_pi * b));
+        z[3 * s + 2] = (float)(rc * cos(two_pi * dd));
+        u[s] = (float)g.unit();
+    }
+}
+
+// ---------------------------------------------------------------- params
+extern "C" void ngs_default_params(ngs_params *p) {
+    memset(p, 0, sizeof(*p));
+    p->k = 16;
+    p->mc_samples = 1;
+    p->cost_mode = 0;
+    p->tau = 0.005;
+    p->lambda_geo = 1.0f;
+    p->lambda_app = 1.0f;
+    p->seed = 0;
+    p->max_passes = 64;
+    p->fp64_policy = 0;
+    p->prefilter = 1;
+    p->eig_floor = 1e-30;
+}
+
+static int check_params(const ngs_params *p) {
+    if (p->k < 1 || p->k > NGS_MAX_K) return 0;
+    if (p->mc_samples < 1 || p->mc_samples > NGS_MAX_S) return 0;
+    if (p->cost_mode < 0 || p->cost_mode > 1) return 0;
+    if (!(p->tau >= 0.0 && p->tau < 1.0)) return 0;
+    if (p->max_passes < 0 || p->max_passes > NGS_STATS_MAX_PASSES) return 0;
+    if (p->fp64_policy < 0 || p->fp64_policy > 2) return 0;
+    if (!(p->eig_floor > 0.0)) return 0;
+    return 1;
+}
+
+extern "C" int ngs_create(ngs_ctx **out, const ngs_params *p, void *stream) {
+    if (!out) {
+        ngs_set_error("ngs_create: ctx pointer is NULL");
+        return NGS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    ngs_params prm;
+    if (p) prm = *p;
+    else ngs_default_params(&prm);
+    if (!check_params(&prm)) {
+        ngs_set_error("ngs_create: parameter out of range");
+        return NGS_ERR_INVALID_ARG;
+    }
+    ngs_ctx *c = new (std::nothrow) ngs_ctx();
+    if (!c) return NGS_ERR_OOM;
+    API_BEGIN
+    c->prm = prm;
+    c->st = (cudaStream_t)stream;
+    NGS_CHECK_CUDA(cudaGetDevice(&c->device));
+    NGS_CHECK_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    NGS_CHECK_CUDA(cudaMallocHost(&c->h_pin, 1 << 16));
+    memset(c->h_pin, 0, 1 << 16);
+    *out = c;
+    }
+    catch (const NgsError &e) {
+        delete c;
+        return e.code;
+    }
+    return NGS_OK;
+}
+
+extern "C" int ngs_destroy(ngs_ctx *c) {
+    if (!c) return NGS_OK;
+    cudaStreamSynchronize(c->st);
+    DevBuf *bufs[] = {&c->b_pts, &c->b_codes, &c->b_codes2, &c->b_vals, &c->b_vals2, &c->b_hist,
+                      &c->b_bbox, &c->b_frame, &c->b_nodes, &c->b_nbr, &c->b_deg, &c->b_cap,
+                      &c->b_rstart, &c->b_adj, &c->b_adjeid, &c->b_fill, &c->b_upc, &c->b_eptr,
+                      &c->b_elo, &c->b_ehi, &c->b_rec, &c->b_cost, &c->b_rng, &c->b_mate,
+                      &c->b_cand, &c->b_candkey, &c->b_counts, &c->b_sel, &c->b_role, &c->b_keep,
+                      &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
+                      &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2};
+    for (DevBuf *b : bufs) ws_free(*b);
+    for (int k = 0; k < 5; k++) {
+        ws_free(c->b_sA[k]);
+        ws_free(c->b_sB[k]);
+        ws_free(c->b_host_dev[k]);
+    }
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->ev_free) cudaEventDestroy(e);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    delete c;
+    return NGS_OK;
+}
+
+extern "C" int ngs_set_params(ngs_ctx *c, const ngs_params *p) {
+    if (!c || !p || !check_params(p)) {
+        ngs_set_error("ngs_set_params: invalid argument");
+        return NGS_ERR_INVALID_ARG;
+    }
+    c->prm = *p;
+    c->g_valid = false;
+    return NGS_OK;
+}
+
+// ---------------------------------------------------------------- helpers
+static void check_splats(const ngs_splats *s, const char *fn) {
+    if (!s) NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: splats is NULL", fn);
+    if (s->n < 0 || s->n > s->cap || s->n > NGS_MAX_N)
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: bad n=%lld cap=%lld (max %lld)", fn, (long long)s->n,
+                 (long long)s->cap, (long long)NGS_MAX_N);
+    if (s->sh_dim < 1 || s->sh_dim > 64) NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: sh_dim out of range", fn);
+    if (s->n > 0 && (!s->xyz || !s->log_scale || !s->rot || !s->opacity_logit || !s->sh))
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: NULL array", fn);
+    if ((s->sh_dim & 3) == 0 && ((uintptr_t)s->sh & 15))
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: sh must be 16-byte aligned", fn);
+}
+
+static SplatView view_of(const ngs_splats *s) {
+    return SplatView{s->xyz, s->log_scale, s->rot, s->opacity_logit, s->sh, s->n, s->sh_dim};
+}
+
+static SplatView scratch_view(ngs_ctx *c, DevBuf *b, int64_t n, int F) {
+    SplatView v;
+    v.xyz = ws<float>(b[0], 3 * n);
+    v.ls = ws<float>(b[1], 3 * n);
+    v.rot = ws<float>(b[2], 4 * n);
+    v.logit = ws<float>(b[3], n);
+    v.sh = ws<float>(b[4], (int64_t)F * n);
+    v.n = n;
+    v.F = F;
+    (void)c;
+    return v;
+}
+
+static void copy_rows_d2d(ngs_ctx *c, const SplatView &src, SplatView &dst, int64_t n) {
+    if (n <= 0) return;
+    const int F = src.F;
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dst.xyz, src.xyz, 12 * n, cudaMemcpyDeviceToDevice, c->st));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dst.ls, src.ls, 12 * n, cudaMemcpyDeviceToDevice, c->st));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dst.rot, src.rot, 16 * n, cudaMemcpyDeviceToDevice, c->st));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dst.logit, src.logit, 4 * n, cudaMemcpyDeviceToDevice, c->st));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dst.sh, src.sh, 4 * (size_t)F * n, cudaMemcpyDeviceToDevice, c->st));
+}
+
+static int k_eff_of(int64_t n, int k) {
+    int ke = k < 1 ? 1 : k;
+    if ((int64_t)ke > n - 1) ke = (int)(n - 1);
+    return ke;
+}
+
+static void check_finite_frame(ngs_ctx *c, const float *frame) {
+    NGS_CHECK_CUDA(cudaMemcpyAsync((float *)(c->h_pin + 4), frame + 4, 4, cudaMemcpyDeviceToHost, c->st));
+    sync_stream(c);
+    uint32_t bad = *(uint32_t *)(c->h_pin + 4);
+    if (bad) NGS_FAIL(NGS_ERR_INVALID_ARG, "%u non-finite centre coordinates", bad);
+}
+
+// ---------------------------------------------------------------- step by step
+extern "C" int ngs_prefilter(ngs_ctx *c, ngs_splats *s) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    check_splats(s, "ngs_prefilter");
+    const int64_t n = s->n;
+    if (n <= 0) return NGS_OK;
+    int32_t *keep = ws<int32_t>(c->b_role, n + 1);
+    int64_t kept = prefilter_flags(c, s->opacity_logit, n, c->prm.tau, keep);
+    if (kept < n) {
+        SplatView in = view_of(s);
+        SplatView tmp = scratch_view(c, c->b_sB, n, s->sh_dim);
+        compact_rows(c, in, keep, (const int32_t *)c->b_pos.p, tmp);
+        copy_rows_d2d(c, tmp, in, kept);
+        sync_stream(c);
+    }
+    s->n = kept;
+    c->g_valid = false;
+    API_END
+}
+
+// canonical-mode graph of `s` into c->g
+static void graph_canonical(ngs_ctx *c, const ngs_splats *s) {
+    const int64_t n = s->n;
+    GraphDev &g = c->g;
+    g = GraphDev{};
+    g.n = n;
+    g.k_eff = n >= 2 ? k_eff_of(n, c->prm.k) : 0;
+    g.cid = nullptr;
+    if (n >= 2) {
+        float *frame = ws<float>(c->b_frame, 8);
+        morton_frame(c, s->xyz, n, frame);
+        check_finite_frame(c, frame);
+        uint32_t *keys = ws<uint32_t>(c->b_codes, n), *vals = ws<uint32_t>(c->b_vals, n);
+        uint32_t *k2 = ws<uint32_t>(c->b_codes2, n), *v2 = ws<uint32_t>(c->b_vals2, n);
+        morton_keys(c, s->xyz, n, frame, keys, vals);
+        radix_sort_u32(c, keys, vals, k2, v2, n, 30);
+        float4 *pts = ws<float4>(c->b_pts, n);
+        gather_points(c, s->xyz, nullptr, vals, n, pts);
+        int32_t *nbr = ws<int32_t>(c->b_nbr, n * g.k_eff);
+        knn_search(c, KnnInput{pts, n, 1}, g.k_eff, nbr);
+        build_edges(c, nbr, g);
+    }
+    c->g_valid = true;
+    c->g_n = n;
+    c->g_k = g.k_eff;
+    c->g_edges = g.n_edges;
+    c->g_xyz = s->xyz;
+}
+
+extern "C" int ngs_build_graph(ngs_ctx *c, const ngs_splats *s, ngs_graph *out) {
+    if (!c || !out) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    check_splats(s, "ngs_build_graph");
+    graph_canonical(c, s);
+    out->n = s->n;
+    out->k_eff = c->g.k_eff;
+    out->n_edges = c->g.n_edges;
+    out->nbr = (const int32_t *)c->b_nbr.p;
+    out->edge_lo = c->g.n_edges ? c->g.elo : nullptr;
+    out->edge_hi = c->g.n_edges ? c->g.ehi : nullptr;
+    API_END
+}
+
+static void check_graph(ngs_ctx *c, const ngs_graph *g, const char *fn) {
+    if (!g) NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: graph is NULL", fn);
+    if (!c->g_valid || g->n != c->g_n || g->n_edges != c->g_edges)
+        NGS_FAIL(NGS_ERR_STATE, "%s: graph is not the ctx's current graph", fn);
+}
+
+extern "C" int ngs_edge_costs(ngs_ctx *c, const ngs_splats *s, const ngs_graph *g, uint32_t pass,
+                              float *cost) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    check_splats(s, "ngs_edge_costs");
+    check_graph(c, g, "ngs_edge_costs");
+    if (s->n != c->g_n || s->xyz != c->g_xyz)
+        NGS_FAIL(NGS_ERR_STATE, "ngs_edge_costs: splats differ from the graph's");
+    if (g->n_edges > 0 && !cost) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_edge_costs: cost is NULL");
+    c->fp64_edges = 0;
+    edge_costs(c, view_of(s), c->g, pass, cost);
+    API_END
+}
+
+extern "C" int ngs_select_pairs(ngs_ctx *c, const ngs_graph *g, const float *cost,
+                                int64_t max_pairs, int32_t *pairs_out, int64_t *n_pairs) {
+    if (!c || !n_pairs) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    check_graph(c, g, "ngs_select_pairs");
+    *n_pairs = 0;
+    if (max_pairs < 0) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_select_pairs: max_pairs < 0");
+    if (g->n_edges > 0 && (!cost || (max_pairs > 0 && !pairs_out)))
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_select_pairs: NULL array");
+    const int64_t n = c->g.n;
+    if (n <= 1 || g->n_edges == 0 || max_pairs == 0) return NGS_OK;
+    int32_t *partner = ws<int32_t>(c->b_partner, n);
+    select_pairs(c, c->g, cost, max_pairs, partner);
+    *n_pairs = partner_to_pairs(c, partner, nullptr, n, pairs_out);
+    API_END
+}
+
+extern "C" int ngs_merge_compact(ngs_ctx *c, ngs_splats *s, const int32_t *pairs, int64_t n_pairs) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    check_splats(s, "ngs_merge_compact");
+    const int64_t n = s->n;
+    if (n_pairs < 0 || n_pairs > n / 2 || (n_pairs > 0 && !pairs))
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_merge_compact: bad pair list");
+    if (n_pairs == 0) return NGS_OK;
+    int32_t *role = ws<int32_t>(c->b_role, n);
+    if (!pairs_to_role(c, pairs, n_pairs, n, role))
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_merge_compact: pairs out of range, unordered or not disjoint");
+    SplatView in = view_of(s);
+    SplatView tmp = scratch_view(c, c->b_sB, n, s->sh_dim);
+    int64_t nout = merge_compact(c, in, role, tmp, nullptr, nullptr);
+    copy_rows_d2d(c, tmp, in, nout);
+    sync_stream(c);
+    s->n = nout;
+    c->g_valid = false;
+    API_END
+}
+
+// ---------------------------------------------------------------- end to end
+namespace {
+__global__ void k_mark_dropped(uint32_t *keys, const int32_t *__restrict__ keep, int64_t n) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (!keep[v]) keys[v] |= 1u << 30;
+}
+__global__ void k_fill_ones(int32_t *a, int64_t n) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        a[v] = 1;
+}
+__global__ void k_gather_cid(const uint32_t *__restrict__ order, const int32_t *__restrict__ pos,
+                             int64_t n, int32_t *cid) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        cid[p] = pos[order[p]];
+}
+}  // namespace
+
+static void simplify_device(ngs_ctx *c, ngs_splats *s, int64_t target, ngs_stats *st) {
+    const int64_t n0 = s->n;
+    const int F = s->sh_dim;
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->n_input = n0;
+    }
+    const int64_t launches0 = c->launches;
+    c->fp64_edges = 0;
+    c->floor_hits = 0;
+    if (n0 <= 0) return;
+    // pre-filter flags (Algorithm 1) and canonical ids of the survivors
+    int32_t *keep = ws<int32_t>(c->b_role, n0 + 1);
+    int64_t nf;
+    const unsigned g0 = grid_stride_blocks(c, n0, 256, 8);
+    if (c->prm.prefilter) {
+        nf = prefilter_flags(c, s->opacity_logit, n0, c->prm.tau, keep);
+    } else {
+        launch(c, "fill_ones", dim3(g0), dim3(256), 0, k_fill_ones, keep, n0);
+        scan_i32(c, keep, ws<int32_t>(c->b_pos, n0 + 1), n0);
+        nf = n0;
+    }
+    int32_t *pos = (int32_t *)c->b_pos.p;
+    if (st) st->n_filtered = nf;
+    // Morton order of the survivors: the working arrays stay in this order;
+    // canonical ids ride along for every tie-break
+    float *frame = ws<float>(c->b_frame, 8);
+    morton_frame(c, s->xyz, n0, frame);
+    check_finite_frame(c, frame);
+    uint32_t *keys = ws<uint32_t>(c->b_codes, n0), *order = ws<uint32_t>(c->b_vals, n0);
+    uint32_t *k2 = ws<uint32_t>(c->b_codes2, n0), *v2 = ws<uint32_t>(c->b_vals2, n0);
+    morton_keys(c, s->xyz, n0, frame, keys, order);
+    launch(c, "mark_dropped", dim3(g0), dim3(256), 0, k_mark_dropped, keys, (const int32_t *)keep, n0);
+    radix_sort_u32(c, keys, order, k2, v2, n0, 31);
+    SplatView A = scratch_view(c, c->b_sA, nf, F), B = scratch_view(c, c->b_sB, nf, F);
+    int32_t *cidA = ws<int32_t>(c->b_cid, nf + 1), *cidB = ws<int32_t>(c->b_cid2, nf + 1);
+    A.n = nf;
+    gather_rows(c, view_of(s), order, A);
+    launch(c, "gather_cid", dim3(grid_stride_blocks(c, nf, 256, 8)), dim3(256), 0, k_gather_cid,
+           (const uint32_t *)order, (const int32_t *)pos, nf, cidA);
+    int64_t n = nf;
+    int pass = 0;
+    int64_t fp64_total = 0;
+    while (n > target && n > 1 && pass < c->prm.max_passes) {
+        GraphDev &g = c->g;
+        g = GraphDev{};
+        g.n = n;
+        g.k_eff = k_eff_of(n, c->prm.k);
+        g.cid = cidA;
+        float4 *pts = ws<float4>(c->b_pts, n);
+        gather_points(c, A.xyz, cidA, nullptr, n, pts);
+        int32_t *nbr = ws<int32_t>(c->b_nbr, n * g.k_eff);
+        knn_search(c, KnnInput{pts, n, 0}, g.k_eff, nbr);
+        build_edges(c, nbr, g);
+        float *cost = ws<float>(c->b_cost, g.n_edges);
+        edge_costs(c, A, g, (uint32_t)pass, cost);
+        int32_t *partner = ws<int32_t>(c->b_partner, n);
+        int64_t np = select_pairs(c, g, cost, n - target, partner);
+        fp64_total += (int64_t)c->h_pin[1];  // written by edge_costs, synced since
+        if (st && pass < NGS_STATS_MAX_PASSES) {
+            st->pass_n[pass] = n;
+            st->pass_edges[pass] = g.n_edges;
+            st->pass_pairs[pass] = np;
+            st->matching_rounds += c->rounds;
+        }
+        pass++;
+        if (np == 0) break;
+        int32_t *role = ws<int32_t>(c->b_role, n);
+        partner_to_role(c, partner, cidA, n, role);
+        int64_t nn = merge_compact(c, A, role, B, cidA, cidB);
+        std::swap(A, B);
+        std::swap(cidA, cidB);
+        n = nn;
+        A.n = n;
+    }
+    // back to canonical order, in the caller's arrays
+    SplatView dst = view_of(s);
+    scatter_rows(c, A, cidA, dst);
+    sync_stream(c);
+    s->n = n;
+    c->g_valid = false;
+    // keep buffer identities consistent for the next call (A/B may have swapped)
+    if (A.xyz != (float *)c->b_sA[0].p) {
+        std::swap(c->b_sA, c->b_sB);
+    }
+    if (cidA != (int32_t *)c->b_cid.p) std::swap(c->b_cid, c->b_cid2);
+    if (st) {
+        st->n_output = n;
+        st->passes = pass;
+        st->fp64_cost_edges = fp64_total;
+        st->eig_floor_hits = c->floor_hits;
+        st->gpu_launches = c->launches - launches0;
+    }
+}
+
+extern "C" int ngs_simplify(ngs_ctx *c, ngs_splats *s, int64_t target, ngs_stats *st) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    check_splats(s, "ngs_simplify");
+    if (target < 1) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_simplify: target_count < 1");
+    simplify_device(c, s, target, st);
+    API_END
+}
+
+extern "C" int ngs_simplify_host(ngs_ctx *c, ngs_splats *h, int64_t target, ngs_stats *st) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    check_splats(h, "ngs_simplify_host");
+    if (target < 1) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_simplify_host: target_count < 1");
+    const int64_t n = h->n;
+    const int F = h->sh_dim;
+    ngs_splats d = *h;
+    d.xyz = ws<float>(c->b_host_dev[0], 3 * n);
+    d.log_scale = ws<float>(c->b_host_dev[1], 3 * n);
+    d.rot = ws<float>(c->b_host_dev[2], 4 * n);
+    d.opacity_logit = ws<float>(c->b_host_dev[3], n);
+    d.sh = ws<float>(c->b_host_dev[4], (int64_t)F * n);
+    d.cap = n;
+    const size_t sz[5] = {12, 12, 16, 4, 4 * (size_t)F};
+    float *hp[5] = {h->xyz, h->log_scale, h->rot, h->opacity_logit, h->sh};
+    float *dp[5] = {d.xyz, d.log_scale, d.rot, d.opacity_logit, d.sh};
+    for (int k = 0; k < 5; k++)
+        NGS_CHECK_CUDA(cudaMemcpyAsync(dp[k], hp[k], sz[k] * n, cudaMemcpyHostToDevice, c->st));
+    simplify_device(c, &d, target, st);
+    for (int k = 0; k < 5; k++)
+        NGS_CHECK_CUDA(cudaMemcpyAsync(hp[k], dp[k], sz[k] * d.n, cudaMemcpyDeviceToHost, c->st));
+    sync_stream(c);
+    h->n = d.n;
+    API_END
+}
+
+// ---------------------------------------------------------------- instrumentation API
+extern "C" int ngs_profile_enable(ngs_ctx *c, int enable) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    if (!enable) prof_resolve(c);
+    c->prof = enable != 0;
+    API_END
+}
+
+extern "C" int ngs_profile_count(ngs_ctx *c) {
+    if (!c) return 0;
+    try {
+        prof_resolve(c);
+    } catch (...) {
+    }
+    return (int)c->kstats.size();
+}
+
+extern "C" int ngs_profile_get(ngs_ctx *c, int i, const char **name, int64_t *launches, double *ms) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    prof_resolve(c);
+    if (i < 0 || i >= (int)c->kstats.size()) NGS_FAIL(NGS_ERR_INVALID_ARG, "profile index");
+    if (name) *name = c->kstats[i].name;
+    if (launches) *launches = c->kstats[i].launches;
+    if (ms) *ms = c->kstats[i].ms;
+    API_END
+}
+
+extern "C" int ngs_profile_reset(ngs_ctx *c) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    prof_resolve(c);
+    c->kstats.clear();
+    API_END
+}
+
+extern "C" int64_t ngs_launch_count(ngs_ctx *c) { return c ? c->launches : 0; }

@@ -1,0 +1,231 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ngs.h"
+
+#define NGS_MAX_N ((int64_t)1 << 25)  // per-scene splat limit (int32 edge offsets)
+#define NGS_LEAF 32                     // kNN tree leaf = one warp of points
+
+// ---------------------------------------------------------------- errors
+void ngs_set_error(const char *fmt, ...);
+
+struct NgsError {
+    int code;
+};
+
+#define NGS_CHECK_CUDA(call)                                                         \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            ngs_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                 \
+                          cudaGetErrorString(e_));                                   \
+            throw NgsError{e_ == cudaErrorMemoryAllocation ? NGS_ERR_OOM : NGS_ERR_CUDA}; \
+        }                                                                            \
+    } while (0)
+
+#define NGS_FAIL(code, ...)            \
+    do {                               \
+        ngs_set_error(__VA_ARGS__);    \
+        throw NgsError{code};          \
+    } while (0)
+
+// ---------------------------------------------------------------- workspace
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+// Grow-only device buffer (contents are not preserved on growth).
+void *ws_get(DevBuf &b, size_t bytes);
+template <class T>
+T *ws(DevBuf &b, int64_t count) {
+    return (T *)ws_get(b, (size_t)(count > 0 ? count : 1) * sizeof(T));
+}
+
+// ---------------------------------------------------------------- ctx
+struct KStat {
+    const char *name;
+    int64_t launches;
+    double ms;
+};
+
+struct PendingEv {
+    int stat;
+    cudaEvent_t a, b;
+};
+
+// Splat arrays in device memory (SoA).
+struct SplatView {
+    float *xyz, *ls, *rot, *logit, *sh;
+    int64_t n;
+    int F;
+};
+
+struct GraphDev {
+    int64_t n;
+    int k_eff;
+    const int32_t *cid;   // canonical ids (nullptr = identity)
+    int32_t *rstart;      // n+1 adjacency row starts (capacity layout)
+    int32_t *deg;         // unique neighbours per row
+    int32_t *adj;         // neighbour internal indices, sorted by cid
+    int32_t *adj_eid;     // edge id of each adjacency entry
+    int32_t *eptr;        // n+1 edge offsets per row (upper entries)
+    int32_t *elo, *ehi;   // edges
+    int64_t n_edges;      // host copy
+};
+
+struct ngs_ctx {
+    ngs_params prm;
+    cudaStream_t st;
+    int device;
+    int num_sms;
+
+    // graph of the last ngs_build_graph (canonical mode)
+    bool g_valid = false;
+    int64_t g_n = 0;
+    int32_t g_k = 0;
+    int64_t g_edges = 0;
+    const float *g_xyz = nullptr;
+    GraphDev g{};
+
+    // workspaces
+    DevBuf b_pts, b_codes, b_codes2, b_vals, b_vals2, b_hist, b_bbox, b_frame;
+    DevBuf b_nodes, b_nbr, b_deg, b_cap, b_rstart, b_adj, b_adjeid, b_fill, b_upc, b_eptr;
+    DevBuf b_elo, b_ehi, b_rec, b_cost, b_rng;
+    DevBuf b_mate, b_cand, b_candkey, b_counts, b_sel, b_role, b_keep, b_pos, b_flag;
+    DevBuf b_scan_part, b_status, b_misc, b_cid, b_cid2, b_cflag, b_cscan;
+    DevBuf b_sA[5], b_sB[5];     // ping-pong splat arrays
+    DevBuf b_pairs, b_partner, b_nbr2;
+    DevBuf b_host_dev[5];        // device staging for ngs_simplify_host
+
+    // pinned host scratch
+    int64_t *h_pin = nullptr;
+
+    // instrumentation
+    bool prof = false;
+    std::vector<KStat> kstats;
+    std::vector<PendingEv> pending;
+    std::vector<cudaEvent_t> ev_free;
+    int64_t launches = 0;
+
+    // per-call counters
+    int64_t fp64_edges = 0;
+    int64_t floor_hits = 0;
+    int32_t rounds = 0;
+};
+
+// Launch bookkeeping: records events when profiling, counts launches, and
+// converts launch errors into exceptions.
+int prof_slot(ngs_ctx *c, const char *name);
+void prof_begin(ngs_ctx *c, int slot, cudaEvent_t *a);
+void prof_end(ngs_ctx *c, int slot, cudaEvent_t a);
+
+template <class Kernel, class... Args>
+void launch(ngs_ctx *c, const char *name, dim3 grid, dim3 block, size_t smem, Kernel k,
+            Args... args) {
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+    int slot = -1;
+    cudaEvent_t a = nullptr;
+    if (c->prof) {
+        slot = prof_slot(c, name);
+        prof_begin(c, slot, &a);
+    }
+    k<<<grid, block, smem, c->st>>>(args...);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) NGS_FAIL(NGS_ERR_CUDA, "launch %s: %s", name, cudaGetErrorString(e));
+    c->launches++;
+    if (c->prof) prof_end(c, slot, a);
+}
+
+inline unsigned blocks_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+// Grid of a grid-stride kernel: a multiple of the SM count, at most `need`.
+inline unsigned grid_stride_blocks(ngs_ctx *c, int64_t work, int threads, int per_sm) {
+    int64_t need = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)c->num_sms * per_sm;
+    if (need < 1) need = 1;
+    return (unsigned)(need < cap ? need : cap);
+}
+
+void sync_stream(ngs_ctx *c);
+
+// ---------------------------------------------------------------- primitives (k_prim.cu)
+// Exclusive scan of n int32 counts into out[0..n] (out[n] = total).  in may
+// alias out.  Totals must fit in int32.
+void scan_i32(ngs_ctx *c, const int32_t *in, int32_t *out, int64_t n);
+// Stable LSD radix sort of (key, val) pairs by the low `bits` bits of key.
+// Result in (keys, vals); tmp buffers of n entries are provided.
+void radix_sort_u32(ngs_ctx *c, uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp,
+                    uint32_t *vals_tmp, int64_t n, int bits);
+// k-th smallest (0-based) of n 32-bit orderable keys -> *d_out (device).
+void radix_select_u32(ngs_ctx *c, const uint32_t *keys, int64_t n, int64_t k, uint32_t *d_out);
+// k-th smallest (0-based) among the 64-bit keys; entries equal to
+// UINT64_MAX are padding and never selected.  Result -> *d_out (device).
+void radix_select_u64(ngs_ctx *c, const uint64_t *keys, int64_t n, int64_t k, uint64_t *d_out);
+
+// ---------------------------------------------------------------- graph (k_knn.cu, k_graph.cu)
+// Points for the kNN search: float4 (x, y, z, cid bits), in search order.
+// out_by_cid = 1: the search order is a permutation of the rows and cid is
+// the row index (output rows/neighbours by cid); 0: search position = row.
+struct KnnInput {
+    const float4 *pts;
+    int64_t n;
+    int out_by_cid;
+};
+// Compute the Morton frame (lo.xyz, 1/side) of n centres into frame[4].
+void morton_frame(ngs_ctx *c, const float *xyz, int64_t n, float *frame);
+// Morton keys of n centres in `frame`, with vals = 0..n-1 (or given).
+void morton_keys(ngs_ctx *c, const float *xyz, int64_t n, const float *frame, uint32_t *keys,
+                 uint32_t *vals);
+// Gather float4 points (x,y,z,cid) in the order of `order` (nullptr = identity).
+void gather_points(ngs_ctx *c, const float *xyz, const int32_t *cid, const uint32_t *order,
+                   int64_t n, float4 *pts);
+// Directed kNN: nbr[row*k_eff + t] = internal index of the t-th neighbour.
+void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr);
+
+// Build the symmetric adjacency and the undirected edge list from nbr.
+void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g);
+
+// ---------------------------------------------------------------- cost (k_cost.cu)
+void edge_costs(ngs_ctx *c, const SplatView &s, const GraphDev &g, uint32_t pass, float *cost);
+
+// ---------------------------------------------------------------- matching (k_match.cu)
+// Greedy matching under (cost, canonical pair) capped to max_pairs.  Writes
+// partner[v] (selected partner or -1) and returns the pair count (host).
+int64_t select_pairs(ngs_ctx *c, const GraphDev &g, const float *cost, int64_t max_pairs,
+                     int32_t *partner);
+// pairs_out (2*count) sorted by lo from partner[]; returns count.
+int64_t partner_to_pairs(ngs_ctx *c, const int32_t *partner, const int32_t *cid, int64_t n,
+                         int32_t *pairs_out);
+
+// ---------------------------------------------------------------- merge (k_merge.cu)
+// role[v]: >=0 partner (v is the lower-cid member, merged into row v),
+// -2 removed, -1 kept.  Returns the new count; out receives the compacted
+// rows.  If cid != nullptr, cid_out receives the updated canonical ids.
+int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, SplatView &out,
+                      const int32_t *cid, int32_t *cid_out);
+// pairs (lo,hi) -> role[] with validation; returns false on invalid pairs.
+bool pairs_to_role(ngs_ctx *c, const int32_t *pairs, int64_t npairs, int64_t n, int32_t *role);
+// partner[] (from select_pairs) -> role[] using canonical ids.
+void partner_to_role(ngs_ctx *c, const int32_t *partner, const int32_t *cid, int64_t n,
+                     int32_t *role);
+// Opacity pre-filter keep flags (1/0) and the kept count (host).
+int64_t prefilter_flags(ngs_ctx *c, const float *logit, int64_t n, double tau, int32_t *keep);
+// Stable compaction of splat rows by keep flags (exclusive scan in pos).
+void compact_rows(ngs_ctx *c, const SplatView &in, const int32_t *keep, const int32_t *pos,
+                  SplatView &out);
+// Scatter rows: out[dst[v]] = in[v].
+void scatter_rows(ngs_ctx *c, const SplatView &in, const int32_t *dst, SplatView &out);
+// Gather rows: out[v] = in[src[v]].
+void gather_rows(ngs_ctx *c, const SplatView &in, const uint32_t *src, SplatView &out);
+
+// Host-side common random numbers for pass `pass` (SplitMix64 + Box-Muller):
+// z[3*S] normals and u[S] uniforms, rounded to float.
+void host_mc_draws(uint64_t seed, uint32_t pass, int S, float *z, float *u);

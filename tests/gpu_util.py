@@ -1,0 +1,71 @@
+"""Shared checks for the GPU parity tests (compare CUDA results with the oracle)."""
+import math
+
+import numpy as np
+
+from paper_2603_16103_gb300 import synth
+
+
+def d2_fp64(xyz, i, js):
+    x = xyz.astype(np.float64)
+    return np.sum((x[js] - x[i]) ** 2, axis=1)
+
+
+def knn_agreement(xyz, got, ref, rel=1e-6):
+    """Neighbour lists must be identical except where FP64 squared distances
+    are within `rel` of each other (near ties may reorder or swap the last
+    member).  Returns the number of rows that differ (all explained)."""
+    differ = 0
+    for i in np.nonzero(np.any(got != ref, axis=1))[0]:
+        differ += 1
+        dg = d2_fp64(xyz, i, got[i])
+        dr = d2_fp64(xyz, i, ref[i])
+        assert len(set(got[i].tolist())) == got.shape[1], f"row {i}: duplicate neighbours"
+        assert i not in set(got[i].tolist()), f"row {i}: self in list"
+        scale = max(dr.max(), 1e-300)
+        assert np.all(np.abs(np.sort(dg) - np.sort(dr)) <= rel * scale), \
+            f"row {i}: neighbour distances differ beyond near-ties"
+        assert np.all(np.diff(dg) >= -rel * scale), f"row {i}: order not by distance"
+    return differ
+
+
+def sigma_of(ls, rot):
+    q = rot.astype(np.float64)
+    q = q / np.linalg.norm(q, axis=-1, keepdims=True)
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    R = np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
+    s2 = np.exp(2 * ls.astype(np.float64))
+    return np.einsum("...ik,...k,...jk->...ij", R, s2, R)
+
+
+def greedy_certificate(n, lo, hi, cost64, pairs, rel=1e-6):
+    """`pairs` is a matching, and every non-member edge touches a member edge
+    whose FP64 cost is not larger beyond `rel` -- i.e. `pairs` is the greedy
+    matching for some order consistent with the FP64 costs up to near-ties.
+    Also maximal: no edge has two free endpoints."""
+    mate = -np.ones(n, dtype=np.int64)
+    for a, b in pairs:
+        assert mate[a] < 0 and mate[b] < 0, "not a matching"
+        mate[a], mate[b] = b, a
+    pc = {}
+    key = {(int(a), int(b)): float(c) for a, b, c in zip(lo, hi, cost64)}
+    for a, b in pairs:
+        pc[int(a)] = pc[int(b)] = key[(int(min(a, b)), int(max(a, b)))]
+    bad = 0
+    for a, b, c in zip(lo.tolist(), hi.tolist(), cost64.tolist()):
+        if mate[a] == b:
+            continue
+        assert mate[a] >= 0 or mate[b] >= 0, f"edge ({a},{b}) has two free endpoints"
+        best = min(pc.get(a, math.inf), pc.get(b, math.inf))
+        if not (best <= c + rel * max(abs(c), 1.0)):
+            bad += 1
+    return bad
+
+
+def small_scene(n, seed=0, kind="unit"):
+    if kind == "unit":
+        return synth.surfaces_unit_cube(n, seed=seed)
+    return synth.patches_cube(n, seed=seed, frac_degenerate=0.05, frac_duplicate=0.01)
