@@ -1,0 +1,335 @@
+"""Throughput benchmark of the NanoGS simplification path on GB300.
+
+Workload (the headline metric's configuration): a seeded synthetic 3DGS scene
+of 6,000,000 splats on 64 surface patches in a 20 m cube (density varying
+10x, 5% near-degenerate splats, 1% duplicated centres, SH degree 3),
+simplified to 10% (600,000 splats) by ngs_simplify: pre-filter, then passes
+of kNN graph -> edge costs -> pair selection -> merge + compaction.
+
+A step is one full ngs_simplify on a fresh copy of the input.  The input
+(1.42 GB) is larger than L2 and is restored from a pristine device copy
+before each step (outside the timed events), which also flushes L2.
+
+One JSON line is printed by rank 0.  Under torchrun (N>1) every rank runs an
+independent replica on its own GPU (the method does not shard within a
+scene); value = all ranks' Gaussians / max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has; the paper ships no code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gaussians simplified/s (6M->10%)"
+UNIT = "Gaussians/s"
+SPLAT_BYTES = 4 * (3 + 3 + 4 + 1 + 48)   # 236 B per splat, SH degree 3
+
+# Algorithmic bytes of each kernel per launch (one touch of what the method
+# must read and write): n = splats of the pass, e = undirected edges, p = pairs.
+ALGO_BYTES = {
+    "knn_k16": lambda n, e, p: n * (12 + 64),                  # read mu, write 16 ids
+    "edge_cost": lambda n, e, p: n * SPLAT_BYTES + e * 12,     # attributes once, (lo,hi) + cost per edge
+    "merge": lambda n, e, p: p * 3 * SPLAT_BYTES,              # read two rows, write one
+    "copy_kept": lambda n, e, p: (n - 2 * p) * 2 * SPLAT_BYTES,
+    "match_scan": lambda n, e, p: 2 * e * 8 + n * 8,           # adjacency + costs, mate/cand
+    "graph_row_sort": lambda n, e, p: 2 * e * 4 * 2 + n * 8,
+}
+
+# DRAM traffic per launch from ncu captures (bytes per splat of the pass);
+# see profiles/ for the captures.  None until a capture of the current kernel exists.
+NCU_TRAFFIC_PER_SPLAT = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="patches6m")
+    ap.add_argument("--ratio", type=float, default=0.1)
+    ap.add_argument("--fp64-policy", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def reference_arm(args, ws, rank):
+    """FP64 CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2603_16103_gb300 import synth
+    sample = synth.patches_cube(args.cpu_sample, seed=2, frac_degenerate=0.05,
+                                frac_duplicate=0.01)
+    target = O.target_count(sample.n, args.ratio)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        O.simplify(sample, target)
+        dt = time.perf_counter() - t
+        if it >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = sample.n * len(times) / tot
+    desc = (f"oracle (FP64 C, OpenMP) on a {sample.n}-splat scene of the same recipe "
+            f"(64 patches, 5% degenerate, 1% duplicates) -> {args.ratio:g}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"patches6m sample ({sample.n} splats) -> {args.ratio:g}",
+                   "sample_splats": sample.n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(),
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(args):
+    import oracle as O
+    from paper_2603_16103_gb300 import synth
+    sample = synth.patches_cube(args.cpu_sample, seed=2, frac_degenerate=0.05,
+                                frac_duplicate=0.01)
+    target = O.target_count(sample.n, args.ratio)
+    t = time.perf_counter()
+    O.simplify(sample, target)
+    dt = time.perf_counter() - t
+    return {"value": sample.n / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"one oracle simplify of a {sample.n}-splat scene of the same recipe "
+                      f"-> {args.ratio:g} ({dt:.1f} s)"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2603_16103_gb300 import binding as B
+    from paper_2603_16103_gb300 import synth
+
+    torch.cuda.set_device(local)
+    B.load()
+    scene = synth.workload(args.workload)
+    n0 = scene.n
+    target = max(int(math.ceil(args.ratio * n0)), 1)
+    kw = {}
+    if args.fp64_policy is not None:
+        kw["fp64_policy"] = args.fp64_policy
+    ctx = B.Context(**kw)
+    pristine = B.DeviceSplats.from_numpy(scene)
+    work = pristine.clone()
+
+    def restore():
+        for a, b in zip(work.tensors(), pristine.tensors()):
+            a.copy_(b)
+        work.n = n0
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        restore()
+        ctx.simplify(work, target)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs, CUDA events around each step
+    B.ngs_profile_reset(ctx.handle)
+    B.ngs_profile_enable(ctx.handle, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    launches = 0
+    stats = None
+    for _ in range(args.steps):
+        restore()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        stats = ctx.simplify(work, target)
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        launches += stats["gpu_launches"]
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clk = clocks.stop()
+    B.ngs_profile_enable(ctx.handle, False)
+    prof = B.ngs_profile(ctx.handle)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * n0 * args.steps / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (event-timed live above)
+    pk, src = peaks()
+    kern_total = sum(p[2] for p in prof) or 1.0
+    dom = max(prof, key=lambda p: p[2])
+    name, nl, ms = dom
+    per_step = [(stats["pass_n"][i], stats["pass_edges"][i], stats["pass_pairs"][i])
+                 for i in range(stats["passes"])]
+    roof = None
+    if name in ALGO_BYTES and per_step:
+        byts = sum(ALGO_BYTES[name](*x) for x in per_step)          # per step
+        launches_per_step = nl / args.steps
+        avg_launch_ms = ms / nl
+        per_launch = byts / launches_per_step
+        achieved = per_launch / (avg_launch_ms / 1e3) / 1e9
+        traffic = None
+        if name in NCU_TRAFFIC_PER_SPLAT:
+            traffic = NCU_TRAFFIC_PER_SPLAT[name] * sum(x[0] for x in per_step) / launches_per_step
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                "peak_source": src, "share": ms / kern_total}
+    kernels = [{"name": p[0], "launches_per_step": p[1] / args.steps,
+                "ms_per_step": p[2] / args.steps, "share": p[2] / kern_total}
+               for p in sorted(prof, key=lambda p: -p[2])[:12]]
+
+    # ---- end to end through the host API (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        host_src = B.DeviceSplats.from_numpy(scene, device="cpu", pin=True)
+        host = host_src.clone()
+        host = B.DeviceSplats(*(a.pin_memory() for a in host.tensors()))
+        e2e_t = 0.0
+        reps = max(1, min(args.steps, 3))
+        for it in range(reps + 1):
+            for a, b in zip(host.tensors(), host_src.tensors()):
+                a.copy_(b)
+            host.n = n0
+            t = time.perf_counter()
+            st = ctx.simplify_host(host, target)
+            dt = time.perf_counter() - t
+            if it > 0:
+                e2e_t += dt
+        h2d = n0 * SPLAT_BYTES
+        d2h = host.n * SPLAT_BYTES
+        e2e = {"value": ws * n0 * reps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {n0} splats -> {target} ({args.ratio:g})",
+                       "splats": n0, "target": target, "k": 16, "mc_samples": 1,
+                       "fp64_policy": ctx.params.fp64_policy,
+                       "passes": stats["passes"], "pass_n": stats["pass_n"],
+                       "l2": "inputs (1.42 GB) larger than L2, restored from a pristine "
+                             "device copy before every step",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

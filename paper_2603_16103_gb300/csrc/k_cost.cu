@@ -227,17 +227,23 @@ __device__ double dgeo_fp64(const float *xyz, const float *ls, const float *rot,
 
 // ---------------------------------------------------------------- edge kernel
 __global__ void __launch_bounds__(256)
-    k_edge_cost(const int32_t *__restrict__ elo, const int32_t *__restrict__ ehi, int64_t m,
-                const float *__restrict__ rec, const float *__restrict__ sh, int F,
+    k_edge_cost(const int32_t *__restrict__ slots, const int32_t *__restrict__ nbr,
+                const int32_t *__restrict__ mirror, const int32_t *__restrict__ cid, int kk,
+                int64_t m, const float *__restrict__ rec, const float *__restrict__ sh, int F,
                 const float *__restrict__ zs, const float *__restrict__ us, int S, int mode,
                 float lg, float la, int policy, const float *__restrict__ xyz,
                 const float *__restrict__ ls, const float *__restrict__ rot,
-                const float *__restrict__ logit, float *__restrict__ cost,
-                unsigned long long *fp64_count) {
+                const float *__restrict__ logit, float *__restrict__ cost_slot,
+                float *__restrict__ cost_out, unsigned long long *fp64_count) {
     const float zz0 = zs[0] * zs[0] + zs[1] * zs[1] + zs[2] * zs[2];
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = elo[e], j = ehi[e];
+        const int32_t sl = slots[e];
+        const int32_t va = sl / kk, vb = nbr[sl];
+        const uint32_t ca = cid ? (uint32_t)cid[va] : (uint32_t)va;
+        const uint32_t cb = cid ? (uint32_t)cid[vb] : (uint32_t)vb;
+        // i = lower canonical id: the arithmetic is then independent of row order
+        const int64_t i = ca < cb ? va : vb, j = ca < cb ? vb : va;
         float ri[REC], rj[REC];
         const float4 *pi4 = (const float4 *)(rec + i * REC), *pj4 = (const float4 *)(rec + j * REC);
 #pragma unroll
@@ -330,18 +336,34 @@ __global__ void __launch_bounds__(256)
         }
         unsigned fm = __ballot_sync(__activemask(), flag);
         if (fm && (threadIdx.x & 31) == __ffs(fm) - 1) atomicAdd(fp64_count, (unsigned long long)__popc(fm));
-        cost[e] = lg * dgeo + la * dapp;
+        const float c = lg * dgeo + la * dapp;
+        cost_slot[sl] = c;
+        const int32_t mr = mirror[sl];
+        if (mr >= 0) cost_slot[mr] = c;
+        if (cost_out) cost_out[e] = c;
+    }
+}
+
+__global__ void k_costs_to_slots(const int32_t *__restrict__ lex_slot,
+                                 const int32_t *__restrict__ mirror, int64_t m,
+                                 const float *__restrict__ cost, float *cost_slot) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = lex_slot[e];
+        float c = cost[e];
+        cost_slot[s] = c;
+        if (mirror[s] >= 0) cost_slot[mirror[s]] = c;
     }
 }
 
 }  // namespace
 
-void edge_costs(ngs_ctx *c, const SplatView &s, const GraphDev &g, uint32_t pass, float *cost) {
+void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool lex,
+                float *cost_out) {
     const int64_t m = g.n_edges;
     const int S = c->prm.mc_samples;
     c->h_pin[1] = 0;  // FP64-path edge count of this call (filled below)
     if (m <= 0) return;
-    // common random numbers of this pass
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     std::vector<float> h(4 * (size_t)S);
     host_mc_draws(c->prm.seed, pass, S, h.data(), h.data() + 3 * S);
@@ -354,10 +376,19 @@ void edge_costs(ngs_ctx *c, const SplatView &s, const GraphDev &g, uint32_t pass
     unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c->b_status, 64);
     NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, c->st));
     launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0, k_edge_cost,
-           (const int32_t *)g.elo, (const int32_t *)g.ehi, m, (const float *)rec,
-           (const float *)s.sh, s.F, (const float *)zs, (const float *)(zs + 3 * S), S,
-           c->prm.cost_mode, c->prm.lambda_geo, c->prm.lambda_app, c->prm.fp64_policy,
-           (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
-           (const float *)s.logit, cost, cnt);
+           (const int32_t *)(lex ? g.lex_slot : g.eslot), g.nbr, (const int32_t *)g.mirror, g.cid,
+           g.k_eff, m, (const float *)rec, (const float *)s.sh, s.F, (const float *)zs,
+           (const float *)(zs + 3 * S), S, c->prm.cost_mode, c->prm.lambda_geo,
+           c->prm.lambda_app, c->prm.fp64_policy, (const float *)s.xyz, (const float *)s.ls,
+           (const float *)s.rot, (const float *)s.logit, g.cost_slot, lex ? cost_out : nullptr,
+           cnt);
     NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin + 1, cnt, 8, cudaMemcpyDeviceToHost, c->st));
+}
+
+void costs_to_slots(ngs_ctx *c, GraphDev &g, const float *cost_lex) {
+    const int64_t m = g.n_edges;
+    if (m <= 0) return;
+    launch(c, "costs_to_slots", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0,
+           k_costs_to_slots, (const int32_t *)g.lex_slot, (const int32_t *)g.mirror, m, cost_lex,
+           g.cost_slot);
 }

@@ -163,32 +163,24 @@ __global__ void k_tree_level(float4 *nodes, int64_t first, int64_t count) {
 constexpr int KNN_WARPS = 4;
 constexpr int KNN_STACK = 64;
 
-// Register-resident k-best list kept in DESCENDING order: slot 0 holds the
-// current k-th key, slots [keff, KMAX) hold 0 (below every key) so that every
-// register index is static for any runtime keff.
+// Register-resident k-best list of 64-bit keys (d^2 bits << 32 | canonical
+// id) kept in DESCENDING order: slot 0 holds the current k-th key, slots
+// [keff, KMAX) hold 0 (below every key) so every register index is static.
 template <int KMAX>
 struct TopK {
     uint64_t key[KMAX];
-    int32_t pos[KMAX];
 
     __device__ __forceinline__ void init(int keff) {
 #pragma unroll
-        for (int i = 0; i < KMAX; i++) {
-            key[i] = i < keff ? ~0ull : 0ull;
-            pos[i] = -1;
-        }
+        for (int i = 0; i < KMAX; i++) key[i] = i < keff ? ~0ull : 0ull;
     }
     __device__ __forceinline__ uint64_t kth() const { return key[0]; }
     // insert x < key[0]: drop key[0], keep the list sorted descending
-    __device__ __forceinline__ void insert(uint64_t x, int32_t p) {
+    __device__ __forceinline__ void insert(uint64_t x) {
 #pragma unroll
         for (int i = 0; i < KMAX; i++) {
             uint64_t nxt = i + 1 < KMAX ? key[i + 1] : 0ull;
-            int32_t nxtp = i + 1 < KMAX ? pos[i + 1] : -1;
-            bool take_next = nxt > x;
-            bool take_x = !take_next && x < key[i];
-            key[i] = take_next ? nxt : (take_x ? x : key[i]);
-            pos[i] = take_next ? nxtp : (take_x ? p : pos[i]);
+            key[i] = nxt > x ? nxt : (x < key[i] ? x : key[i]);
         }
     }
     __device__ __forceinline__ float kth_d2() const {
@@ -196,25 +188,37 @@ struct TopK {
     }
 };
 
+// Candidates that pass a lane's threshold are queued per lane in shared
+// memory and inserted in warp-wide rounds afterwards, so the warp pays for
+// max-over-lanes insertions instead of one insertion per candidate any lane
+// accepts.
 template <int KMAX>
 __device__ __forceinline__ void scan_leaf(const float4 *__restrict__ pts, int64_t n, int64_t leaf,
                                           const float4 &q, int64_t qp, bool qvalid, int lane,
-                                          TopK<KMAX> &tk) {
+                                          uint64_t (*queue)[32], TopK<KMAX> &tk) {
     int64_t cp = leaf * NGS_LEAF + lane;
     bool cvalid = cp < n;
     float4 c = cvalid ? pts[cp] : make_float4(0.f, 0.f, 0.f, 0.f);
-    unsigned vmask = __ballot_sync(FULL_MASK, cvalid);
-    int cnt = __popc(vmask);  // valid candidates are a prefix of the leaf
+    int cnt = __popc(__ballot_sync(FULL_MASK, cvalid));  // valid candidates are a prefix
+    const uint64_t thr = tk.kth();
+    int qlen = 0;
     for (int j = 0; j < cnt; j++) {
         float cx = __shfl_sync(FULL_MASK, c.x, j);
         float cy = __shfl_sync(FULL_MASK, c.y, j);
         float cz = __shfl_sync(FULL_MASK, c.z, j);
         uint32_t cw = __float_as_uint(__shfl_sync(FULL_MASK, c.w, j));
-        int64_t cpos = leaf * NGS_LEAF + j;
         float d2 = dist2_rn(__fsub_rn(q.x, cx), __fsub_rn(q.y, cy), __fsub_rn(q.z, cz));
         uint64_t kk = ((uint64_t)__float_as_uint(d2) << 32) | cw;
-        if (qvalid && cpos != qp && kk < tk.kth()) tk.insert(kk, (int32_t)cpos);
+        if (qvalid && leaf * NGS_LEAF + j != qp && kk < thr) queue[qlen++][lane] = kk;
     }
+    int rounds = __reduce_max_sync(FULL_MASK, qlen);
+    for (int r = 0; r < rounds; r++) {
+        if (r < qlen) {
+            uint64_t x = queue[r][lane];
+            if (x < tk.kth()) tk.insert(x);
+        }
+    }
+    __syncwarp();
 }
 
 template <int KMAX>
@@ -222,16 +226,18 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     k_knn(const float4 *__restrict__ pts, int64_t n, int64_t nb, int64_t P,
           const float4 *__restrict__ nodes, int keff, int out_by_cid, int32_t *__restrict__ nbr) {
     __shared__ int stack_all[KNN_WARPS][KNN_STACK];
+    __shared__ uint64_t queue_all[KNN_WARPS][NGS_LEAF][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t b = (int64_t)blockIdx.x * KNN_WARPS + warp;
     if (b >= nb) return;  // uniform per warp
     int *stack = stack_all[warp];
+    uint64_t(*queue)[32] = queue_all[warp];
     const int64_t qp = b * NGS_LEAF + lane;
     const bool qvalid = qp < n;
     const float4 q = qvalid ? pts[qp] : make_float4(0.f, 0.f, 0.f, 0.f);
     TopK<KMAX> tk;
     tk.init(keff);
-    scan_leaf<KMAX>(pts, n, b, q, qp, qvalid, lane, tk);
+    scan_leaf<KMAX>(pts, n, b, q, qp, qvalid, lane, queue, tk);
     const int64_t own = P + b;
     int sp = 0;
     if (lane == 0) stack[0] = 1;
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
         bool need = qvalid && nonempty && md <= tk.kth_d2();
         if (!__any_sync(FULL_MASK, need)) continue;
         if (node >= P) {
-            scan_leaf<KMAX>(pts, n, node - P, q, qp, qvalid, lane, tk);
+            scan_leaf<KMAX>(pts, n, node - P, q, qp, qvalid, lane, queue, tk);
         } else {
             int64_t c0 = 2 * node, c1 = 2 * node + 1;
             float d0 = box_dist2(q, nodes[2 * c0], nodes[2 * c0 + 1]);
@@ -264,15 +270,26 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
         }
     }
     if (qvalid) {
+        // neighbours are written as canonical ids; rows by canonical id
+        // (out_by_cid) or by search position
         int64_t row = out_by_cid ? (int64_t)__float_as_uint(q.w) : qp;
 #pragma unroll
         for (int i = 0; i < KMAX; i++) {  // slot i holds rank keff-1-i
-            if (i < keff) {
-                int32_t v = out_by_cid ? (int32_t)(uint32_t)(tk.key[i] & 0xffffffffu) : tk.pos[i];
-                nbr[row * keff + (keff - 1 - i)] = v;
-            }
+            if (i < keff) nbr[row * keff + (keff - 1 - i)] = (int32_t)(uint32_t)(tk.key[i] & 0xffffffffu);
         }
     }
+}
+
+__global__ void k_cid_to_pos(const int32_t *__restrict__ cid, int64_t n, int32_t *pos_of_cid) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        pos_of_cid[cid[p]] = (int32_t)p;
+}
+
+__global__ void k_map_ids(int32_t *a, int64_t m, const int32_t *__restrict__ pos_of_cid) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = pos_of_cid[a[i]];
 }
 
 }  // namespace
@@ -320,4 +337,12 @@ void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
         launch(c, "knn_k16", grid, block, 0, k_knn<16>, in.pts, n, nb, P, cn, k_eff, by_cid, nbr);
     else
         launch(c, "knn_k32", grid, block, 0, k_knn<32>, in.pts, n, nb, P, cn, k_eff, by_cid, nbr);
+    if (!by_cid) {
+        // search order = rows: translate the canonical ids to rows
+        int32_t *pos_of_cid = ws<int32_t>(c->b_nbr2, n);
+        launch(c, "knn_cid_to_pos", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0,
+               k_cid_to_pos, in.cid, n, pos_of_cid);
+        launch(c, "knn_map_ids", dim3(grid_stride_blocks(c, n * k_eff, 256, 8)), dim3(256), 0,
+               k_map_ids, nbr, n * k_eff, (const int32_t *)pos_of_cid);
+    }
 }

@@ -28,10 +28,28 @@ __global__ void k_match_init(int64_t n, int32_t *mate, int32_t *cand) {
     }
 }
 
-// Re-scan the rows of free vertices whose pointer is unknown or stale.
-__global__ void k_match_scan(int64_t n, const int32_t *__restrict__ rstart,
-                             const int32_t *__restrict__ deg, const int32_t *__restrict__ adj,
-                             const int32_t *__restrict__ adj_eid, const float *__restrict__ cost,
+// Re-scan the incident edges of free vertices whose pointer is unknown or
+// stale: the k slots of the vertex, then its non-mutual in-slots.
+__device__ __forceinline__ void consider(int32_t u, float cst, uint32_t cv,
+                                         const int32_t *__restrict__ cid,
+                                         const int32_t *__restrict__ mate, int32_t &best,
+                                         uint32_t &bk, uint32_t &blo, uint32_t &bhi) {
+    if (mate[u] != -1) return;
+    uint32_t k = cost_order_bits(cst);
+    uint32_t cu = cid_of(cid, u);
+    uint32_t lo = cv < cu ? cv : cu, hi = cv < cu ? cu : cv;
+    bool better = best < 0 || k < bk || (k == bk && (lo < blo || (lo == blo && hi < bhi)));
+    if (better) {
+        best = u;
+        bk = k;
+        blo = lo;
+        bhi = hi;
+    }
+}
+
+__global__ void k_match_scan(int64_t n, int kk, const int32_t *__restrict__ nbr,
+                             const float *__restrict__ cost_slot,
+                             const int32_t *__restrict__ rev_ptr, const int32_t *__restrict__ rev,
                              const int32_t *__restrict__ cid, const int32_t *__restrict__ mate,
                              int32_t *cand, uint32_t *candkey) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -41,23 +59,14 @@ __global__ void k_match_scan(int64_t n, const int32_t *__restrict__ rstart,
         if (c == -1) continue;                  // no free neighbour: stays single
         if (c >= 0 && mate[c] == -1) continue;  // target still free: still the best
         const uint32_t cv = cid_of(cid, (int32_t)v);
-        const int32_t rs = rstart[v];
-        const int d = deg[v];
         int32_t best = -1;
         uint32_t bk = 0xffffffffu, blo = 0xffffffffu, bhi = 0xffffffffu;
-        for (int t = 0; t < d; t++) {
-            int32_t u = adj[rs + t];
-            if (mate[u] != -1) continue;
-            uint32_t k = cost_order_bits(cost[adj_eid[rs + t]]);
-            uint32_t cu = cid_of(cid, u);
-            uint32_t lo = cv < cu ? cv : cu, hi = cv < cu ? cu : cv;
-            bool better = best < 0 || k < bk || (k == bk && (lo < blo || (lo == blo && hi < bhi)));
-            if (better) {
-                best = u;
-                bk = k;
-                blo = lo;
-                bhi = hi;
-            }
+        const int64_t base = v * kk;
+        for (int t = 0; t < kk; t++)
+            consider(nbr[base + t], cost_slot[base + t], cv, cid, mate, best, bk, blo, bhi);
+        for (int32_t r = rev_ptr[v]; r < rev_ptr[v + 1]; r++) {
+            int32_t s = rev[r];
+            consider(s / kk, cost_slot[s], cv, cid, mate, best, bk, blo, bhi);
         }
         cand[v] = best;
         candkey[v] = bk;
@@ -142,8 +151,7 @@ __global__ void k_write_pairs(int64_t n, const int32_t *__restrict__ partner,
 
 }  // namespace
 
-int64_t select_pairs(ngs_ctx *c, const GraphDev &g, const float *cost, int64_t max_pairs,
-                     int32_t *partner) {
+int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *partner) {
     const int64_t n = g.n;
     c->rounds = 0;
     if (n <= 0) return 0;
@@ -165,10 +173,9 @@ int64_t select_pairs(ngs_ctx *c, const GraphDev &g, const float *cost, int64_t m
             if (r + batch > max_rounds)
                 NGS_FAIL(NGS_ERR_TIMEOUT, "matching did not converge in %d rounds", max_rounds);
             for (int b = 0; b < batch; b++, r++) {
-                launch(c, "match_scan", dim3(grid), dim3(256), 0, k_match_scan, n,
-                       (const int32_t *)g.rstart, (const int32_t *)g.deg, (const int32_t *)g.adj,
-                       (const int32_t *)g.adj_eid, cost, g.cid, (const int32_t *)mate, cand,
-                       candkey);
+                launch(c, "match_scan", dim3(grid), dim3(256), 0, k_match_scan, n, g.k_eff,
+                       g.nbr, (const float *)g.cost_slot, (const int32_t *)g.rev_ptr,
+                       (const int32_t *)g.rev, g.cid, (const int32_t *)mate, cand, candkey);
                 launch(c, "match_pair", dim3(grid), dim3(256), 0, k_match_pair, n,
                        (const int32_t *)cand, mate, counts + r);
             }

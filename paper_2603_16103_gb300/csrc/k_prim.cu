@@ -205,6 +205,19 @@ __global__ void k_sel_decide(SelState *s, int32_t *hist, int shift) {
     hist[threadIdx.x] = 0;
 }
 
+__global__ void k_iota(uint32_t *a, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (uint32_t)i;
+}
+
+__global__ void k_gather_u32(const uint32_t *__restrict__ src, const uint32_t *__restrict__ idx,
+                             int64_t n, uint32_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = src[idx[i]];
+}
+
 template <class K>
 __global__ void k_sel_out(const SelState *s, K *out) {
     *out = (K)s->prefix;
@@ -268,4 +281,13 @@ void radix_select_u32(ngs_ctx *c, const uint32_t *keys, int64_t n, int64_t k, ui
 
 void radix_select_u64(ngs_ctx *c, const uint64_t *keys, int64_t n, int64_t k, uint64_t *d_out) {
     radix_select_impl<uint64_t>(c, keys, n, k, d_out, true);
+}
+
+void iota_u32(ngs_ctx *c, uint32_t *a, int64_t n) {
+    launch(c, "iota", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_iota, a, n);
+}
+
+void gather_u32(ngs_ctx *c, const uint32_t *src, const uint32_t *idx, int64_t n, uint32_t *out) {
+    launch(c, "gather_u32", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_gather_u32,
+           src, idx, n, out);
 }

@@ -330,8 +330,9 @@ static void graph_canonical(ngs_ctx *c, const ngs_splats *s) {
         float4 *pts = ws<float4>(c->b_pts, n);
         gather_points(c, s->xyz, nullptr, vals, n, pts);
         int32_t *nbr = ws<int32_t>(c->b_nbr, n * g.k_eff);
-        knn_search(c, KnnInput{pts, n, 1}, g.k_eff, nbr);
+        knn_search(c, KnnInput{pts, n, 1, nullptr}, g.k_eff, nbr);
         build_edges(c, nbr, g);
+        build_lex_view(c, g);
     }
     c->g_valid = true;
     c->g_n = n;
@@ -370,7 +371,7 @@ extern "C" int ngs_edge_costs(ngs_ctx *c, const ngs_splats *s, const ngs_graph *
         NGS_FAIL(NGS_ERR_STATE, "ngs_edge_costs: splats differ from the graph's");
     if (g->n_edges > 0 && !cost) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_edge_costs: cost is NULL");
     c->fp64_edges = 0;
-    edge_costs(c, view_of(s), c->g, pass, cost);
+    edge_costs(c, view_of(s), c->g, pass, true, cost);
     API_END
 }
 
@@ -386,7 +387,8 @@ extern "C" int ngs_select_pairs(ngs_ctx *c, const ngs_graph *g, const float *cos
     const int64_t n = c->g.n;
     if (n <= 1 || g->n_edges == 0 || max_pairs == 0) return NGS_OK;
     int32_t *partner = ws<int32_t>(c->b_partner, n);
-    select_pairs(c, c->g, cost, max_pairs, partner);
+    costs_to_slots(c, c->g, cost);
+    select_pairs(c, c->g, max_pairs, partner);
     *n_pairs = partner_to_pairs(c, partner, nullptr, n, pairs_out);
     API_END
 }
@@ -484,12 +486,11 @@ static void simplify_device(ngs_ctx *c, ngs_splats *s, int64_t target, ngs_stats
         float4 *pts = ws<float4>(c->b_pts, n);
         gather_points(c, A.xyz, cidA, nullptr, n, pts);
         int32_t *nbr = ws<int32_t>(c->b_nbr, n * g.k_eff);
-        knn_search(c, KnnInput{pts, n, 0}, g.k_eff, nbr);
+        knn_search(c, KnnInput{pts, n, 0, cidA}, g.k_eff, nbr);
         build_edges(c, nbr, g);
-        float *cost = ws<float>(c->b_cost, g.n_edges);
-        edge_costs(c, A, g, (uint32_t)pass, cost);
+        edge_costs(c, A, g, (uint32_t)pass, false, nullptr);
         int32_t *partner = ws<int32_t>(c->b_partner, n);
-        int64_t np = select_pairs(c, g, cost, n - target, partner);
+        int64_t np = select_pairs(c, g, n - target, partner);
         fp64_total += (int64_t)c->h_pin[1];  // written by edge_costs, synced since
         if (st && pass < NGS_STATS_MAX_PASSES) {
             st->pass_n[pass] = n;

@@ -69,14 +69,16 @@ struct SplatView {
 struct GraphDev {
     int64_t n;
     int k_eff;
-    const int32_t *cid;   // canonical ids (nullptr = identity)
-    int32_t *rstart;      // n+1 adjacency row starts (capacity layout)
-    int32_t *deg;         // unique neighbours per row
-    int32_t *adj;         // neighbour internal indices, sorted by cid
-    int32_t *adj_eid;     // edge id of each adjacency entry
-    int32_t *eptr;        // n+1 edge offsets per row (upper entries)
-    int32_t *elo, *ehi;   // edges
-    int64_t n_edges;      // host copy
+    const int32_t *cid;     // canonical ids (nullptr = identity)
+    const int32_t *nbr;     // n*k directed neighbours (slot s = v*k + t)
+    int32_t *mirror;        // n*k partner slot of a mutual edge, else -1
+    int32_t *eslot;         // |E| canonical slots, ascending
+    int32_t *rev_ptr;       // n+1 offsets into rev
+    int32_t *rev;           // non-mutual slots pointing at each vertex
+    float *cost_slot;       // n*k cost of the edge of each slot
+    int64_t n_edges;        // |E| (host copy)
+    int32_t *elo, *ehi;     // C-ABI view: lexicographic edges (canonical ids)
+    int32_t *lex_slot;      // canonical slot of lexicographic edge e
 };
 
 struct ngs_ctx {
@@ -164,6 +166,9 @@ void scan_i32(ngs_ctx *c, const int32_t *in, int32_t *out, int64_t n);
 // Result in (keys, vals); tmp buffers of n entries are provided.
 void radix_sort_u32(ngs_ctx *c, uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp,
                     uint32_t *vals_tmp, int64_t n, int bits);
+void iota_u32(ngs_ctx *c, uint32_t *a, int64_t n);
+// out[i] = src[idx[i]]
+void gather_u32(ngs_ctx *c, const uint32_t *src, const uint32_t *idx, int64_t n, uint32_t *out);
 // k-th smallest (0-based) of n 32-bit orderable keys -> *d_out (device).
 void radix_select_u32(ngs_ctx *c, const uint32_t *keys, int64_t n, int64_t k, uint32_t *d_out);
 // k-th smallest (0-based) among the 64-bit keys; entries equal to
@@ -178,6 +183,7 @@ struct KnnInput {
     const float4 *pts;
     int64_t n;
     int out_by_cid;
+    const int32_t *cid;  // canonical id of each search position (out_by_cid = 0)
 };
 // Compute the Morton frame (lo.xyz, 1/side) of n centres into frame[4].
 void morton_frame(ngs_ctx *c, const float *xyz, int64_t n, float *frame);
@@ -190,17 +196,24 @@ void gather_points(ngs_ctx *c, const float *xyz, const int32_t *cid, const uint3
 // Directed kNN: nbr[row*k_eff + t] = internal index of the t-th neighbour.
 void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr);
 
-// Build the symmetric adjacency and the undirected edge list from nbr.
+// Build the slot-form undirected graph from nbr (see k_graph.cu).
 void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g);
+// Lexicographic edge list (elo, ehi, lex_slot) of the graph, for the C ABI.
+void build_lex_view(ngs_ctx *c, GraphDev &g);
 
 // ---------------------------------------------------------------- cost (k_cost.cu)
-void edge_costs(ngs_ctx *c, const SplatView &s, const GraphDev &g, uint32_t pass, float *cost);
+// Cost of every edge into g.cost_slot (both slots of a mutual edge).  With
+// lex = true the edges are visited in lexicographic order and also written
+// to cost_out[e]; otherwise cost_out may be nullptr.
+void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool lex,
+                float *cost_out);
+// cost_slot from caller costs given in lexicographic edge order.
+void costs_to_slots(ngs_ctx *c, GraphDev &g, const float *cost_lex);
 
 // ---------------------------------------------------------------- matching (k_match.cu)
 // Greedy matching under (cost, canonical pair) capped to max_pairs.  Writes
 // partner[v] (selected partner or -1) and returns the pair count (host).
-int64_t select_pairs(ngs_ctx *c, const GraphDev &g, const float *cost, int64_t max_pairs,
-                     int32_t *partner);
+int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *partner);
 // pairs_out (2*count) sorted by lo from partner[]; returns count.
 int64_t partner_to_pairs(ngs_ctx *c, const int32_t *partner, const int32_t *cid, int64_t n,
                          int32_t *pairs_out);
