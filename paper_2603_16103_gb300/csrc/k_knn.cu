@@ -1,14 +1,18 @@
 // k-nearest-neighbour search over splat centres (Sec. 3.1, Algorithm 1 KNN).
 //
-// Points are ordered along a 30-bit Morton curve and cut into leaves of 32
-// (one warp).  An implicit complete binary tree of axis-aligned boxes sits on
-// top of the leaves.  One warp answers the 32 queries of one leaf: it scans
-// its own leaf first, then walks the tree depth first, visiting a node only
-// if some lane's box distance is within that lane's current k-th distance.
-// Each lane keeps a register-resident sorted list of (d^2, canonical id)
-// keys, so the result is exactly the k_eff nearest with ties by canonical id.
-// Box distances and point distances use the same FP32 expression without
-// contraction, so pruning never drops a point the list would accept.
+// Centres are quantised on a 1024^3 grid over the scene's bounding cube and
+// sorted by Morton code, so every cell of every coarser level 2^l (l <= 10)
+// is a contiguous range of the sorted array.  A dense table of range starts
+// at one level l_t (8^l_t ~ 16 n cells, at most 8^9) gives O(1) ranges for l <= l_t and a
+// short binary search inside a table cell for finer levels.
+// Each query (one thread, threads in Morton order) picks the finest level
+// whose 3x3x3 block of cells around it holds at least 64 points, scans its
+// own cell and the 26
+// around it, and then whole shells of cells until its current k-th distance
+// is strictly inside the scanned block (with margins for FP32 rounding of
+// distances and of the quantisation), so the list is exactly the k_eff
+// nearest by (d^2, canonical id).  Distances are (dx^2 + dy^2) + dz^2 in
+// FP32 without contraction.
 #include "ngs_device.cuh"
 #include "ngs_internal.h"
 
@@ -16,13 +20,6 @@ namespace {
 
 __device__ __forceinline__ float dist2_rn(float dx, float dy, float dz) {
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-}
-
-__device__ __forceinline__ float box_dist2(const float4 &q, const float4 &lo, const float4 &hi) {
-    float dx = fmaxf(fmaxf(__fsub_rn(lo.x, q.x), __fsub_rn(q.x, hi.x)), 0.0f);
-    float dy = fmaxf(fmaxf(__fsub_rn(lo.y, q.y), __fsub_rn(q.y, hi.y)), 0.0f);
-    float dz = fmaxf(fmaxf(__fsub_rn(lo.z, q.z), __fsub_rn(q.z, hi.z)), 0.0f);
-    return dist2_rn(dx, dy, dz);
 }
 
 __device__ __forceinline__ uint32_t spread10(uint32_t v) {
@@ -124,44 +121,29 @@ __global__ void k_gather_pts(const float *__restrict__ xyz, const int32_t *__res
     }
 }
 
-// ---------------------------------------------------------------- tree
-__global__ void k_tree_leaves(const float4 *__restrict__ pts, int64_t n, int64_t nb, int64_t P,
-                              float4 *nodes) {
-    int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (b >= P) return;
-    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-    if (b < nb) {
-        int64_t p = b * NGS_LEAF + lane;
-        float x = INFINITY, y = INFINITY, z = INFINITY, X = -INFINITY, Y = -INFINITY, Z = -INFINITY;
-        if (p < n) {
-            float4 v = pts[p];
-            x = X = v.x;
-            y = Y = v.y;
-            z = Z = v.z;
-        }
-        lo = make_float4(warp_min(x), warp_min(y), warp_min(z), 0.f);
-        hi = make_float4(warp_max(X), warp_max(Y), warp_max(Z), 0.f);
+// ---------------------------------------------------------------- cell table
+// Per-cell point counts at the table level; an exclusive scan turns them into
+// T[c] = first sorted position of cell c (T[ncell] = n).
+__global__ void k_cell_count(const uint32_t *__restrict__ scode, int64_t n, int shift,
+                             int32_t *cnt) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c = scode[p] >> shift;
+        // one atomic per run of equal cells inside the warp
+        unsigned peers = __match_any_sync(__activemask(), c);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[c], __popc(peers));
     }
-    if (lane == 0) {
-        nodes[2 * (P + b)] = lo;
-        nodes[2 * (P + b) + 1] = hi;
-    }
-}
-
-__global__ void k_tree_level(float4 *nodes, int64_t first, int64_t count) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    int64_t i = first + t;
-    float4 a0 = nodes[4 * i], a1 = nodes[4 * i + 1], b0 = nodes[4 * i + 2], b1 = nodes[4 * i + 3];
-    nodes[2 * i] = make_float4(fminf(a0.x, b0.x), fminf(a0.y, b0.y), fminf(a0.z, b0.z), 0.f);
-    nodes[2 * i + 1] = make_float4(fmaxf(a1.x, b1.x), fmaxf(a1.y, b1.y), fmaxf(a1.z, b1.z), 0.f);
 }
 
 // ---------------------------------------------------------------- query
-constexpr int KNN_WARPS = 4;
-constexpr int KNN_STACK = 64;
+__device__ __forceinline__ uint32_t compact10(uint32_t v) {
+    v &= 0x09249249u;
+    v = (v ^ (v >> 2)) & 0x030c30c3u;
+    v = (v ^ (v >> 4)) & 0x0300f00fu;
+    v = (v ^ (v >> 8)) & 0x030000ffu;
+    v = (v ^ (v >> 16)) & 0x000003ffu;
+    return v;
+}
 
 // Register-resident k-best list of 64-bit keys (d^2 bits << 32 | canonical
 // id) kept in DESCENDING order: slot 0 holds the current k-th key, slots
@@ -183,100 +165,186 @@ struct TopK {
             key[i] = nxt > x ? nxt : (x < key[i] ? x : key[i]);
         }
     }
-    __device__ __forceinline__ float kth_d2() const {
-        return key[0] == ~0ull ? INFINITY : __uint_as_float((uint32_t)(key[0] >> 32));
-    }
 };
 
-// Candidates that pass a lane's threshold are queued per lane in shared
-// memory and inserted in warp-wide rounds afterwards, so the warp pays for
-// max-over-lanes insertions instead of one insertion per candidate any lane
-// accepts.
-template <int KMAX>
-__device__ __forceinline__ void scan_leaf(const float4 *__restrict__ pts, int64_t n, int64_t leaf,
-                                          const float4 &q, int64_t qp, bool qvalid, int lane,
-                                          uint64_t (*queue)[32], TopK<KMAX> &tk) {
-    int64_t cp = leaf * NGS_LEAF + lane;
-    bool cvalid = cp < n;
-    float4 c = cvalid ? pts[cp] : make_float4(0.f, 0.f, 0.f, 0.f);
-    int cnt = __popc(__ballot_sync(FULL_MASK, cvalid));  // valid candidates are a prefix
-    const uint64_t thr = tk.kth();
-    int qlen = 0;
-    for (int j = 0; j < cnt; j++) {
-        float cx = __shfl_sync(FULL_MASK, c.x, j);
-        float cy = __shfl_sync(FULL_MASK, c.y, j);
-        float cz = __shfl_sync(FULL_MASK, c.z, j);
-        uint32_t cw = __float_as_uint(__shfl_sync(FULL_MASK, c.w, j));
-        float d2 = dist2_rn(__fsub_rn(q.x, cx), __fsub_rn(q.y, cy), __fsub_rn(q.z, cz));
-        uint64_t kk = ((uint64_t)__float_as_uint(d2) << 32) | cw;
-        if (qvalid && leaf * NGS_LEAF + j != qp && kk < thr) queue[qlen++][lane] = kk;
+struct GridCtx {
+    const uint32_t *scode;
+    const int32_t *T;
+    int lt;  // table level
+};
+
+// Sorted-position range of the level-l cell with Morton prefix `pre`.
+__device__ __forceinline__ void cell_range(const GridCtx &g, int l, uint32_t pre, int32_t &a,
+                                           int32_t &b) {
+    if (l <= g.lt) {
+        int sh = 3 * (g.lt - l);
+        a = g.T[(int64_t)pre << sh];
+        b = g.T[((int64_t)pre + 1) << sh];
+    } else {
+        int sh = 3 * (l - g.lt);
+        uint32_t par = pre >> sh;
+        int32_t A = g.T[par], B = g.T[par + 1];
+        const uint32_t lo_code = pre << (3 * (10 - l));
+        const uint32_t hi_code = (pre + 1) << (3 * (10 - l));
+        int32_t x = A, y = B;  // lower_bound(lo_code)
+        while (x < y) {
+            int32_t m = (x + y) >> 1;
+            if (g.scode[m] < lo_code) x = m + 1; else y = m;
+        }
+        a = x;
+        y = B;  // lower_bound(hi_code) in [a, B)
+        while (x < y) {
+            int32_t m = (x + y) >> 1;
+            if (g.scode[m] < hi_code) x = m + 1; else y = m;
+        }
+        b = x;
     }
-    int rounds = __reduce_max_sync(FULL_MASK, qlen);
+}
+
+__device__ __forceinline__ uint32_t interleave(uint32_t x, uint32_t y, uint32_t z) {
+    return spread10(x) | (spread10(y) << 1) | (spread10(z) << 2);
+}
+
+constexpr int KNN_QCAP = 16;   // per-lane candidate queue (shared memory)
+constexpr int KNN_BLOCK_MIN = 64;
+
+// Points in the 3x3x3 block of level-l cells around the level-10 cell (x,y,z).
+__device__ __forceinline__ int block_count(const GridCtx &g, int l, uint32_t x, uint32_t y,
+                                           uint32_t z) {
+    const int sh = 10 - l;
+    const int32_t cx = (int32_t)(x >> sh), cy = (int32_t)(y >> sh), cz = (int32_t)(z >> sh);
+    const int32_t gmax = (1 << l) - 1;
+    int tot = 0;
+    for (int dx = -1; dx <= 1; dx++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dz = -1; dz <= 1; dz++) {
+                const int32_t a = cx + dx, b = cy + dy, c = cz + dz;
+                if (a < 0 || b < 0 || c < 0 || a > gmax || b > gmax || c > gmax) continue;
+                int32_t lo, hi;
+                cell_range(g, l, interleave((uint32_t)a, (uint32_t)b, (uint32_t)c), lo, hi);
+                tot += hi - lo;
+            }
+    return tot;
+}
+constexpr int KNN_BLOCK = 256;
+
+template <int KMAX>
+__device__ __forceinline__ void flush_queue(uint64_t (*queue)[32], int lane, int &qlen,
+                                            TopK<KMAX> &tk) {
+    const int rounds = __reduce_max_sync(FULL_MASK, qlen);
     for (int r = 0; r < rounds; r++) {
         if (r < qlen) {
             uint64_t x = queue[r][lane];
             if (x < tk.kth()) tk.insert(x);
         }
     }
+    qlen = 0;
     __syncwarp();
 }
 
+// One thread per query, threads in Morton order.  Each lane walks its own
+// stream of cells (shell r = 0, 1, 2, ... around its cell) one candidate per
+// step; candidates under the lane's threshold are queued and inserted in
+// warp-wide rounds, so the list updates are not serialised by divergence.
 template <int KMAX>
-__global__ void __launch_bounds__(KNN_WARPS * 32)
-    k_knn(const float4 *__restrict__ pts, int64_t n, int64_t nb, int64_t P,
-          const float4 *__restrict__ nodes, int keff, int out_by_cid, int32_t *__restrict__ nbr) {
-    __shared__ int stack_all[KNN_WARPS][KNN_STACK];
-    __shared__ uint64_t queue_all[KNN_WARPS][NGS_LEAF][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t b = (int64_t)blockIdx.x * KNN_WARPS + warp;
-    if (b >= nb) return;  // uniform per warp
-    int *stack = stack_all[warp];
-    uint64_t(*queue)[32] = queue_all[warp];
-    const int64_t qp = b * NGS_LEAF + lane;
-    const bool qvalid = qp < n;
-    const float4 q = qvalid ? pts[qp] : make_float4(0.f, 0.f, 0.f, 0.f);
-    TopK<KMAX> tk;
-    tk.init(keff);
-    scan_leaf<KMAX>(pts, n, b, q, qp, qvalid, lane, queue, tk);
-    const int64_t own = P + b;
-    int sp = 0;
-    if (lane == 0) stack[0] = 1;
-    sp = 1;
-    __syncwarp();
-    while (sp > 0) {
-        int64_t node = stack[--sp];
-        __syncwarp();
-        if (node == own) continue;
-        float4 lo = nodes[2 * node], hi = nodes[2 * node + 1];
-        bool nonempty = lo.x <= hi.x;
-        float md = box_dist2(q, lo, hi);
-        bool need = qvalid && nonempty && md <= tk.kth_d2();
-        if (!__any_sync(FULL_MASK, need)) continue;
-        if (node >= P) {
-            scan_leaf<KMAX>(pts, n, node - P, q, qp, qvalid, lane, queue, tk);
-        } else {
-            int64_t c0 = 2 * node, c1 = 2 * node + 1;
-            float d0 = box_dist2(q, nodes[2 * c0], nodes[2 * c0 + 1]);
-            float d1 = box_dist2(q, nodes[2 * c1], nodes[2 * c1 + 1]);
-            int v0 = __popc(__ballot_sync(FULL_MASK, qvalid && d0 <= d1));
-            int v1 = __popc(__ballot_sync(FULL_MASK, qvalid && d0 > d1));
-            int64_t first = v0 >= v1 ? c0 : c1, second = v0 >= v1 ? c1 : c0;
-            if (lane == 0) {
-                stack[sp] = (int)second;      // popped last
-                stack[sp + 1] = (int)first;   // popped next
-            }
-            sp += 2;
-            __syncwarp();
+__global__ void __launch_bounds__(KNN_BLOCK, 3)
+    k_knn_grid(const float4 *__restrict__ pts, const uint32_t *__restrict__ scode,
+               const uint32_t *__restrict__ sidx, int64_t n, const int32_t *__restrict__ T, int lt,
+               const float *__restrict__ frame, int keff, int out_by_cid,
+               int32_t *__restrict__ nbr) {
+    __shared__ uint64_t queue_all[KNN_BLOCK / 32][KNN_QCAP][32];
+    const int lane = threadIdx.x & 31;
+    uint64_t(*queue)[32] = queue_all[threadIdx.x >> 5];
+    const GridCtx g{scode, T, lt};
+    const float lx = frame[0], ly = frame[1], lz = frame[2], scale = frame[3];
+    const float inv_scale = 1.0f / scale;
+    const int64_t qp = (int64_t)blockIdx.x * KNN_BLOCK + threadIdx.x;
+    const bool valid = qp < n;
+    const float4 q = valid ? pts[qp] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t code = valid ? scode[qp] : 0u;
+    // level: the finest (up to one below the table level) whose 3x3x3 block
+    // around the query holds at least 64 points, one level finer when that
+    // still holds 64 and the block is crowded
+    const uint32_t qx = compact10(code), qy = compact10(code >> 1), qz = compact10(code >> 2);
+    int l = lt;
+    if (valid) {
+        int bc = block_count(g, l, qx, qy, qz);
+        while (l > 1 && bc < KNN_BLOCK_MIN) {
+            l--;
+            bc = block_count(g, l, qx, qy, qz);
+        }
+        if (bc > 6 * KNN_BLOCK_MIN && l < 10) {
+            int b2 = block_count(g, l + 1, qx, qy, qz);
+            if (b2 >= KNN_BLOCK_MIN) l++;
         }
     }
-    if (qvalid) {
-        // neighbours are written as canonical ids; rows by canonical id
-        // (out_by_cid) or by search position
-        int64_t row = out_by_cid ? (int64_t)__float_as_uint(q.w) : qp;
-#pragma unroll
-        for (int i = 0; i < KMAX; i++) {  // slot i holds rank keff-1-i
-            if (i < keff) nbr[row * keff + (keff - 1 - i)] = (int32_t)(uint32_t)(tk.key[i] & 0xffffffffu);
+    const int sh = 10 - l;
+    const int32_t cx = (int32_t)(qx >> sh), cy = (int32_t)(qy >> sh), cz = (int32_t)(qz >> sh);
+    const int32_t gmax = (1 << l) - 1;
+    const float h = inv_scale * (float)(1 << sh);  // cell side at level l
+    const float margin = 1e-3f * inv_scale;
+    TopK<KMAX> tk;
+    tk.init(keff);
+    int qlen = 0;
+    bool active = valid;
+    for (int r = 0;; r++) {
+        const int side = 2 * r + 1, ncells = side * side * side;
+        int t = 0;
+        int32_t p = 0, b = 0;
+        bool more = active;
+        while (__any_sync(FULL_MASK, more)) {
+            int64_t cand = -1;
+            if (more) {
+                while (p >= b && t < ncells) {
+                    const int dx = t / (side * side) - r, dy = (t / side) % side - r,
+                              dz = t % side - r;
+                    t++;
+                    const int ch = max(max(abs(dx), abs(dy)), abs(dz));
+                    const int32_t x = cx + dx, y = cy + dy, z = cz + dz;
+                    if (ch != r || x < 0 || y < 0 || z < 0 || x > gmax || y > gmax || z > gmax)
+                        continue;
+                    cell_range(g, l, interleave((uint32_t)x, (uint32_t)y, (uint32_t)z), p, b);
+                }
+                if (p < b) cand = p++;
+                else more = false;
+            }
+            if (cand >= 0 && cand != qp) {
+                const float4 c = pts[cand];
+                const float d2 = dist2_rn(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z));
+                const uint64_t kk = ((uint64_t)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
+                if (kk < tk.kth()) queue[qlen++][lane] = kk;
+            }
+            if (__any_sync(FULL_MASK, qlen == KNN_QCAP)) flush_queue<KMAX>(queue, lane, qlen, tk);
         }
+        flush_queue<KMAX>(queue, lane, qlen, tk);
+        if (active) {
+            // distance from q to the outside of the scanned block; a face on
+            // the grid boundary has no point beyond it
+            float G = INFINITY;
+            bool covers_all = true;
+            if (cx - r > 0) { G = fminf(G, q.x - (lx + (float)(cx - r) * h)); covers_all = false; }
+            if (cx + r < gmax) { G = fminf(G, (lx + (float)(cx + r + 1) * h) - q.x); covers_all = false; }
+            if (cy - r > 0) { G = fminf(G, q.y - (ly + (float)(cy - r) * h)); covers_all = false; }
+            if (cy + r < gmax) { G = fminf(G, (ly + (float)(cy + r + 1) * h) - q.y); covers_all = false; }
+            if (cz - r > 0) { G = fminf(G, q.z - (lz + (float)(cz - r) * h)); covers_all = false; }
+            if (cz + r < gmax) { G = fminf(G, (lz + (float)(cz + r + 1) * h) - q.z); covers_all = false; }
+            if (covers_all) {
+                active = false;
+            } else {
+                G -= margin;
+                if (tk.kth() != ~0ull && G > 0.f) {
+                    const float kd = __uint_as_float((uint32_t)(tk.kth() >> 32));
+                    if (kd <= G * G * (1.0f - 4e-6f)) active = false;
+                }
+            }
+        }
+        if (!__any_sync(FULL_MASK, active)) break;
+    }
+    if (valid) {
+        const int64_t row = out_by_cid ? (int64_t)__float_as_uint(q.w) : (int64_t)sidx[qp];
+#pragma unroll
+        for (int i = 0; i < KMAX; i++)  // slot i holds rank keff-1-i
+            if (i < keff) nbr[row * keff + (keff - 1 - i)] = (int32_t)(uint32_t)(tk.key[i] & 0xffffffffu);
     }
 }
 
@@ -315,30 +383,34 @@ void gather_points(ngs_ctx *c, const float *xyz, const int32_t *cid, const uint3
 }
 
 void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
-    int64_t n = in.n;
+    const int64_t n = in.n;
     if (n <= 1 || k_eff <= 0) return;
-    int64_t nb = (n + NGS_LEAF - 1) / NGS_LEAF;
-    int64_t P = 1;
-    while (P < nb) P <<= 1;
-    float4 *nodes = ws<float4>(c->b_nodes, 4 * P);
-    launch(c, "tree_leaves", dim3(blocks_for(P * 32, 256)), dim3(256), 0, k_tree_leaves, in.pts,
-           n, nb, P, nodes);
-    for (int64_t first = P / 2; first >= 1; first /= 2)
-        launch(c, "tree_level", dim3(blocks_for(first, 256)), dim3(256), 0, k_tree_level, nodes,
-               first, first);
-    dim3 grid(blocks_for(nb, KNN_WARPS)), block(KNN_WARPS * 32);
-    int by_cid = in.out_by_cid;
-    const float4 *cn = nodes;
+    // table level: about 4 or more cells per point (at most 8^9 = 134M
+    // cells); finer levels are resolved by a short search inside a cell
+    int lt = 1;
+    while (lt < 9 && ((int64_t)1 << (3 * lt)) < 4 * n) lt++;
+    const int64_t ncell = (int64_t)1 << (3 * lt);
+    int32_t *T = ws<int32_t>(c->b_nodes, ncell + 1);
+    NGS_CHECK_CUDA(cudaMemsetAsync(T, 0, sizeof(int32_t) * ncell, c->st));
+    launch(c, "cell_count", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_cell_count,
+           in.scode, n, 3 * (10 - lt), T);
+    scan_i32(c, T, T, ncell);
+    const unsigned grid = blocks_for(n, KNN_BLOCK);
+    const int32_t *cT = T;
     if (k_eff <= 4)
-        launch(c, "knn_k4", grid, block, 0, k_knn<4>, in.pts, n, nb, P, cn, k_eff, by_cid, nbr);
+        launch(c, "knn_k4", dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<4>, in.pts, in.scode, in.sidx, n,
+               cT, lt, in.frame, k_eff, in.out_by_cid, nbr);
     else if (k_eff <= 8)
-        launch(c, "knn_k8", grid, block, 0, k_knn<8>, in.pts, n, nb, P, cn, k_eff, by_cid, nbr);
+        launch(c, "knn_k8", dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<8>, in.pts, in.scode, in.sidx, n,
+               cT, lt, in.frame, k_eff, in.out_by_cid, nbr);
     else if (k_eff <= 16)
-        launch(c, "knn_k16", grid, block, 0, k_knn<16>, in.pts, n, nb, P, cn, k_eff, by_cid, nbr);
+        launch(c, "knn_k16", dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<16>, in.pts, in.scode, in.sidx, n,
+               cT, lt, in.frame, k_eff, in.out_by_cid, nbr);
     else
-        launch(c, "knn_k32", grid, block, 0, k_knn<32>, in.pts, n, nb, P, cn, k_eff, by_cid, nbr);
-    if (!by_cid) {
-        // search order = rows: translate the canonical ids to rows
+        launch(c, "knn_k32", dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<32>, in.pts, in.scode, in.sidx, n,
+               cT, lt, in.frame, k_eff, in.out_by_cid, nbr);
+    if (!in.out_by_cid) {
+        // rows are internal indices; translate the neighbours' canonical ids
         int32_t *pos_of_cid = ws<int32_t>(c->b_nbr2, n);
         launch(c, "knn_cid_to_pos", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0,
                k_cid_to_pos, in.cid, n, pos_of_cid);

@@ -330,7 +330,7 @@ static void graph_canonical(ngs_ctx *c, const ngs_splats *s) {
         float4 *pts = ws<float4>(c->b_pts, n);
         gather_points(c, s->xyz, nullptr, vals, n, pts);
         int32_t *nbr = ws<int32_t>(c->b_nbr, n * g.k_eff);
-        knn_search(c, KnnInput{pts, n, 1, nullptr}, g.k_eff, nbr);
+        knn_search(c, KnnInput{pts, keys, vals, frame, n, 1, nullptr}, g.k_eff, nbr);
         build_edges(c, nbr, g);
         build_lex_view(c, g);
     }
@@ -483,10 +483,15 @@ static void simplify_device(ngs_ctx *c, ngs_splats *s, int64_t target, ngs_stats
         g.n = n;
         g.k_eff = k_eff_of(n, c->prm.k);
         g.cid = cidA;
+        // exact Morton order of this pass (the working order is close to it)
+        uint32_t *pk = ws<uint32_t>(c->b_codes, n), *pv = ws<uint32_t>(c->b_vals, n);
+        uint32_t *pk2 = ws<uint32_t>(c->b_codes2, n), *pv2 = ws<uint32_t>(c->b_vals2, n);
+        morton_keys(c, A.xyz, n, frame, pk, pv);
+        radix_sort_u32(c, pk, pv, pk2, pv2, n, 30);
         float4 *pts = ws<float4>(c->b_pts, n);
-        gather_points(c, A.xyz, cidA, nullptr, n, pts);
+        gather_points(c, A.xyz, cidA, pv, n, pts);
         int32_t *nbr = ws<int32_t>(c->b_nbr, n * g.k_eff);
-        knn_search(c, KnnInput{pts, n, 0, cidA}, g.k_eff, nbr);
+        knn_search(c, KnnInput{pts, pk, pv, frame, n, 0, cidA}, g.k_eff, nbr);
         build_edges(c, nbr, g);
         edge_costs(c, A, g, (uint32_t)pass, false, nullptr);
         int32_t *partner = ws<int32_t>(c->b_partner, n);

@@ -176,14 +176,20 @@ void radix_select_u32(ngs_ctx *c, const uint32_t *keys, int64_t n, int64_t k, ui
 void radix_select_u64(ngs_ctx *c, const uint64_t *keys, int64_t n, int64_t k, uint64_t *d_out);
 
 // ---------------------------------------------------------------- graph (k_knn.cu, k_graph.cu)
-// Points for the kNN search: float4 (x, y, z, cid bits), in search order.
-// out_by_cid = 1: the search order is a permutation of the rows and cid is
-// the row index (output rows/neighbours by cid); 0: search position = row.
+// Input of the kNN search: points sorted by 30-bit Morton code in `frame`.
+//   pts[p]  = (x, y, z, canonical id bits) at sorted position p
+//   scode[p] = Morton code (ascending), sidx[p] = internal row of position p
+//   out_by_cid = 1: canonical id == internal row; 0: rows are internal
+//   indices and neighbours are translated from canonical ids via cid[]
+//   (cid of each internal row).
 struct KnnInput {
     const float4 *pts;
+    const uint32_t *scode;
+    const uint32_t *sidx;
+    const float *frame;
     int64_t n;
     int out_by_cid;
-    const int32_t *cid;  // canonical id of each search position (out_by_cid = 0)
+    const int32_t *cid;
 };
 // Compute the Morton frame (lo.xyz, 1/side) of n centres into frame[4].
 void morton_frame(ngs_ctx *c, const float *xyz, int64_t n, float *frame);
