@@ -23,7 +23,8 @@
  *       opacity_logit[n]    alpha = 1 / (1 + exp(-logit))
  *       sh[n*sh_dim]        appearance feature f (SH coefficients)
  *     Row i of every array belongs to splat i ("canonical index" i); every
- *     tie-break in the method uses canonical indices.
+ *     tie-break in the method uses canonical indices.  rot (and sh when
+ *     sh_dim is a multiple of 4) must be 16-byte aligned.
  */
 #ifndef NGS_H
 #define NGS_H

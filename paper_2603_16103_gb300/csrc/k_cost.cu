@@ -160,7 +160,7 @@ __device__ double lse2_d(double a, double b) {
     return m + log1p(exp(-fabs(a - b)));
 }
 
-__device__ double dgeo_fp64(const float *xyz, const float *ls, const float *rot,
+__device__ __noinline__ double dgeo_fp64(const float *xyz, const float *ls, const float *rot,
                             const float *logit, int64_t i, int64_t j, int S,
                             const float *__restrict__ zs, const float *__restrict__ us, int mode) {
     G64 gi, gj;
@@ -226,7 +226,24 @@ __device__ double dgeo_fp64(const float *xyz, const float *ls, const float *rot,
 }
 
 // ---------------------------------------------------------------- edge kernel
-__global__ void __launch_bounds__(256)
+// Record layout in float4 groups: G0 = (mu, log w), G1..G3 = R (row-major)
+// then inv_s in G3.yzw, G4/G5 = Sigma (6) + sum log s + min/max scale ratio,
+// G6 = Sigma^{1/2} z_0, G7 = s.  Fields are loaded where they are used to
+// keep the live register set small.
+struct Rec {
+    const float4 *p;
+    __device__ __forceinline__ float4 g(int k) const { return __ldg(p + k); }
+};
+
+__device__ __forceinline__ void load_R(const Rec &r, float *R, float *invs) {
+    const float4 a = r.g(1), b = r.g(2), c = r.g(3);
+    R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w;
+    R[4] = b.x; R[5] = b.y; R[6] = b.z; R[7] = b.w;
+    R[8] = c.x;
+    invs[0] = c.y; invs[1] = c.z; invs[2] = c.w;
+}
+
+__global__ void __launch_bounds__(256, 3)
     k_edge_cost(const int32_t *__restrict__ slots, const int32_t *__restrict__ nbr,
                 const int32_t *__restrict__ mirror, const int32_t *__restrict__ cid, int kk,
                 int64_t m, const float *__restrict__ rec, const float *__restrict__ sh, int F,
@@ -244,18 +261,12 @@ __global__ void __launch_bounds__(256)
         const uint32_t cb = cid ? (uint32_t)cid[vb] : (uint32_t)vb;
         // i = lower canonical id: the arithmetic is then independent of row order
         const int64_t i = ca < cb ? va : vb, j = ca < cb ? vb : va;
-        float ri[REC], rj[REC];
-        const float4 *pi4 = (const float4 *)(rec + i * REC), *pj4 = (const float4 *)(rec + j * REC);
-#pragma unroll
-        for (int k = 0; k < REC / 4; k++) {
-            float4 a = __ldg(pi4 + k), b = __ldg(pj4 + k);
-            ri[4 * k] = a.x; ri[4 * k + 1] = a.y; ri[4 * k + 2] = a.z; ri[4 * k + 3] = a.w;
-            rj[4 * k] = b.x; rj[4 * k + 1] = b.y; rj[4 * k + 2] = b.z; rj[4 * k + 3] = b.w;
-        }
+        const Rec Ri{(const float4 *)(rec + i * REC)}, Rj{(const float4 *)(rec + j * REC)};
         // ---- appearance term
         float dapp = 0.f;
         if ((F & 3) == 0) {
             const float4 *fi = (const float4 *)(sh + i * F), *fj = (const float4 *)(sh + j * F);
+#pragma unroll 4
             for (int t = 0; t < F / 4; t++) {
                 float4 a = __ldg(fi + t), b = __ldg(fj + t);
                 float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
@@ -268,19 +279,23 @@ __global__ void __launch_bounds__(256)
             }
         }
         // ---- MPMM moments (Eqs. vm_weights, vm_cov)
-        const float ld = ri[R_LW] - rj[R_LW];
+        const float4 i0 = Ri.g(0), j0 = Rj.g(0);
+        const float ld = i0.w - j0.w;
         const float lpi = -softplusf(-ld), lpj = -softplusf(ld);
         const float pi = __expf(lpi), pj = __expf(lpj);
-        float d[3] = {ri[R_MU] - rj[R_MU], ri[R_MU + 1] - rj[R_MU + 1], ri[R_MU + 2] - rj[R_MU + 2]};
+        const float d[3] = {i0.x - j0.x, i0.y - j0.y, i0.z - j0.z};
         const float ppd = pi * pj;
         float Sm[6];
         {
+            const float4 i4 = Ri.g(4), i5 = Ri.g(5), j4 = Rj.g(4), j5 = Rj.g(5);
+            const float si[6] = {i4.x, i4.y, i4.z, i4.w, i5.x, i5.y};
+            const float sj[6] = {j4.x, j4.y, j4.z, j4.w, j5.x, j5.y};
             int idx = 0;
 #pragma unroll
             for (int a = 0; a < 3; a++)
 #pragma unroll
                 for (int b = a; b < 3; b++, idx++)
-                    Sm[idx] = pi * ri[R_SIG + idx] + pj * rj[R_SIG + idx] + ppd * d[a] * d[b];
+                    Sm[idx] = pi * si[idx] + pj * sj[idx] + ppd * d[a] * d[b];
         }
         // ---- Cholesky of Sigma_m (00 01 02 11 12 22)
         float L[6], il[3];
@@ -288,45 +303,52 @@ __global__ void __launch_bounds__(256)
         il[0] = 1.0f / L[0];
         L[1] = Sm[1] * il[0];
         L[3] = Sm[2] * il[0];
-        float t11 = Sm[3] - L[1] * L[1];
+        const float t11 = Sm[3] - L[1] * L[1];
         L[2] = sqrtf(fmaxf(t11, 0.f));
         il[1] = 1.0f / L[2];
         L[4] = (Sm[4] - L[3] * L[1]) * il[1];
-        float t22 = Sm[5] - L[3] * L[3] - L[4] * L[4];
+        const float t22 = Sm[5] - L[3] * L[3] - L[4] * L[4];
         L[5] = sqrtf(fmaxf(t22, 0.f));
         il[2] = 1.0f / L[5];
         bool flag = !(Sm[0] > 0.f) || !(t11 > 1e-5f * Sm[3]) || !(t22 > 1e-5f * Sm[5]);
-        if (policy == 1) flag = flag || ri[R_SRATIO] < 1e-3f || rj[R_SRATIO] < 1e-3f;
+        if (policy == 1) flag = flag || Ri.g(5).w < 1e-3f || Rj.g(5).w < 1e-3f;
         float dgeo;
         if (!flag) {
+            float Rm[9], invs_i[3], invs_j[3];
+            load_R(Ri, Rm, invs_i);
+            float Rn[9];
+            load_R(Rj, Rn, invs_j);
             // a_c = log sqrt(det Sm / det Sigma_c) as a product of O(1) ratios
-            const float ai = logf((L[0] * ri[R_INVS]) * (L[2] * ri[R_INVS + 1]) * (L[5] * ri[R_INVS + 2]));
-            const float aj = logf((L[0] * rj[R_INVS]) * (L[2] * rj[R_INVS + 1]) * (L[5] * rj[R_INVS + 2]));
+            const float ai = logf((L[0] * invs_i[0]) * (L[2] * invs_i[1]) * (L[5] * invs_i[2]));
+            const float aj = logf((L[0] * invs_j[0]) * (L[2] * invs_j[1]) * (L[5] * invs_j[2]));
             const float ci = lpi + ai, cj = lpj + aj;
             float acc = 0.f;
             for (int s = 0; s < S; s++) {
                 float yi[3], yj[3], zz;
                 if (s == 0) {
-                    yi[0] = ri[R_Y0]; yi[1] = ri[R_Y0 + 1]; yi[2] = ri[R_Y0 + 2];
-                    yj[0] = rj[R_Y0]; yj[1] = rj[R_Y0 + 1]; yj[2] = rj[R_Y0 + 2];
+                    const float4 a = Ri.g(6), b = Rj.g(6);
+                    yi[0] = a.x; yi[1] = a.y; yi[2] = a.z;
+                    yj[0] = b.x; yj[1] = b.y; yj[2] = b.z;
                     zz = zz0;
                 } else {
                     const float z[3] = {zs[3 * s], zs[3 * s + 1], zs[3 * s + 2]};
-                    sym_sqrt_apply(ri + R_R, ri + R_S, z, yi);
-                    sym_sqrt_apply(rj + R_R, rj + R_S, z, yj);
+                    const float4 a = Ri.g(7), b = Rj.g(7);
+                    const float sa[3] = {a.x, a.y, a.z}, sb[3] = {b.x, b.y, b.z};
+                    sym_sqrt_apply(Rm, sa, z, yi);
+                    sym_sqrt_apply(Rn, sb, z, yj);
                     zz = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
                 }
                 // x = x_i
                 float v1[3] = {d[0] + yi[0], d[1] + yi[1], d[2] + yi[2]};
                 float v2[3] = {pj * d[0] + yi[0], pj * d[1] + yi[1], pj * d[2] + yi[2]};
-                float qj = maha_splat(rj + R_R, rj + R_INVS, v1);
-                float qm = maha_chol(L, il, v2);
+                const float qj = maha_splat(Rn, invs_j, v1);
+                const float qm = maha_chol(L, il, v2);
                 const float gi = lse2(ci - 0.5f * zz, cj - 0.5f * qj) + 0.5f * qm;
                 // x = x_j
                 float w1[3] = {yj[0] - d[0], yj[1] - d[1], yj[2] - d[2]};
                 float w2[3] = {yj[0] - pi * d[0], yj[1] - pi * d[1], yj[2] - pi * d[2]};
-                float qi = maha_splat(ri + R_R, ri + R_INVS, w1);
-                float qm2 = maha_chol(L, il, w2);
+                const float qi = maha_splat(Rm, invs_i, w1);
+                const float qm2 = maha_chol(L, il, w2);
                 const float gj = lse2(ci - 0.5f * qi, cj - 0.5f * zz) + 0.5f * qm2;
                 acc += mode == 0 ? (pi * gi + pj * gj) : (us[s] < pi ? gi : gj);
             }

@@ -207,26 +207,38 @@ __device__ __forceinline__ uint32_t interleave(uint32_t x, uint32_t y, uint32_t 
 
 constexpr int KNN_QCAP = 16;   // per-lane candidate queue (shared memory)
 constexpr int KNN_BLOCK_MIN = 64;
+constexpr int KNN_BLOCK = 256;
 
-// Points in the 3x3x3 block of level-l cells around the level-10 cell (x,y,z).
-__device__ __forceinline__ int block_count(const GridCtx &g, int l, uint32_t x, uint32_t y,
-                                           uint32_t z) {
-    const int sh = 10 - l;
-    const int32_t cx = (int32_t)(x >> sh), cy = (int32_t)(y >> sh), cz = (int32_t)(z >> sh);
+// Points in the 3x3x3 block of level-l cells around cell (cx, cy, cz).
+__device__ __forceinline__ int block_count(const GridCtx &g, int l, int32_t cx, int32_t cy,
+                                           int32_t cz) {
     const int32_t gmax = (1 << l) - 1;
+    uint32_t sx[3], sy[3], sz[3];
+    bool okx[3], oky[3], okz[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int32_t x = cx + d - 1, y = cy + d - 1, z = cz + d - 1;
+        okx[d] = x >= 0 && x <= gmax;
+        oky[d] = y >= 0 && y <= gmax;
+        okz[d] = z >= 0 && z <= gmax;
+        sx[d] = spread10((uint32_t)x);
+        sy[d] = spread10((uint32_t)y) << 1;
+        sz[d] = spread10((uint32_t)z) << 2;
+    }
     int tot = 0;
-    for (int dx = -1; dx <= 1; dx++)
-        for (int dy = -1; dy <= 1; dy++)
-            for (int dz = -1; dz <= 1; dz++) {
-                const int32_t a = cx + dx, b = cy + dy, c = cz + dz;
-                if (a < 0 || b < 0 || c < 0 || a > gmax || b > gmax || c > gmax) continue;
+#pragma unroll
+    for (int dx = 0; dx < 3; dx++)
+#pragma unroll
+        for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+            for (int dz = 0; dz < 3; dz++) {
+                if (!(okx[dx] && oky[dy] && okz[dz])) continue;
                 int32_t lo, hi;
-                cell_range(g, l, interleave((uint32_t)a, (uint32_t)b, (uint32_t)c), lo, hi);
+                cell_range(g, l, sx[dx] | sy[dy] | sz[dz], lo, hi);
                 tot += hi - lo;
             }
     return tot;
 }
-constexpr int KNN_BLOCK = 256;
 
 template <int KMAX>
 __device__ __forceinline__ void flush_queue(uint64_t (*queue)[32], int lane, int &qlen,
@@ -242,10 +254,40 @@ __device__ __forceinline__ void flush_queue(uint64_t (*queue)[32], int lane, int
     __syncwarp();
 }
 
+// The 26 neighbours of a cell ordered by distance class: faces, edges, corners.
+__device__ const char3 kShell1[26] = {
+    {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}, {-1, -1, 0},
+    {-1, 1, 0}, {1, -1, 0}, {1, 1, 0}, {-1, 0, -1}, {-1, 0, 1}, {1, 0, -1}, {1, 0, 1},
+    {0, -1, -1}, {0, -1, 1}, {0, 1, -1}, {0, 1, 1}, {-1, -1, -1}, {-1, -1, 1}, {-1, 1, -1},
+    {-1, 1, 1}, {1, -1, -1}, {1, -1, 1}, {1, 1, -1}, {1, 1, 1}};
+
+// Cells of the shell at Chebyshev distance r around the query cell, in a
+// fixed order (for r = 1: the 6 face neighbours, 12 edge and 8 corner cells).
+__device__ __forceinline__ bool shell_cell(int r, int t, int &dx, int &dy, int &dz) {
+    if (r == 0) {
+        dx = dy = dz = 0;
+        return t == 0;
+    }
+    if (r == 1) {
+        if (t >= 26) return false;
+        const char3 o = kShell1[t];
+        dx = o.x;
+        dy = o.y;
+        dz = o.z;
+        return true;
+    }
+    const int side = 2 * r + 1;
+    if (t >= side * side * side) return false;
+    dx = t / (side * side) - r;
+    dy = (t / side) % side - r;
+    dz = t % side - r;
+    return true;
+}
+
 // One thread per query, threads in Morton order.  Each lane walks its own
-// stream of cells (shell r = 0, 1, 2, ... around its cell) one candidate per
-// step; candidates under the lane's threshold are queued and inserted in
-// warp-wide rounds, so the list updates are not serialised by divergence.
+// stream of cells (shell r = 0, 1, 2, ... around its cell), scanning a cell
+// at a time; candidates under the lane's threshold are queued and inserted
+// in warp-wide rounds, so list updates are not serialised by divergence.
 template <int KMAX>
 __global__ void __launch_bounds__(KNN_BLOCK, 3)
     k_knn_grid(const float4 *__restrict__ pts, const uint32_t *__restrict__ scode,
@@ -262,19 +304,19 @@ __global__ void __launch_bounds__(KNN_BLOCK, 3)
     const bool valid = qp < n;
     const float4 q = valid ? pts[qp] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t code = valid ? scode[qp] : 0u;
-    // level: the finest (up to one below the table level) whose 3x3x3 block
-    // around the query holds at least 64 points, one level finer when that
-    // still holds 64 and the block is crowded
+    // level: the finest (up to the table level) whose 3x3x3 block around the
+    // query holds at least 64 points, one level finer when that still holds
+    // 64 and the block is crowded
     const uint32_t qx = compact10(code), qy = compact10(code >> 1), qz = compact10(code >> 2);
     int l = lt;
     if (valid) {
-        int bc = block_count(g, l, qx, qy, qz);
+        int bc = block_count(g, l, qx >> (10 - l), qy >> (10 - l), qz >> (10 - l));
         while (l > 1 && bc < KNN_BLOCK_MIN) {
             l--;
-            bc = block_count(g, l, qx, qy, qz);
+            bc = block_count(g, l, qx >> (10 - l), qy >> (10 - l), qz >> (10 - l));
         }
         if (bc > 6 * KNN_BLOCK_MIN && l < 10) {
-            int b2 = block_count(g, l + 1, qx, qy, qz);
+            int b2 = block_count(g, l + 1, qx >> (9 - l), qy >> (9 - l), qz >> (9 - l));
             if (b2 >= KNN_BLOCK_MIN) l++;
         }
     }
@@ -288,16 +330,18 @@ __global__ void __launch_bounds__(KNN_BLOCK, 3)
     int qlen = 0;
     bool active = valid;
     for (int r = 0;; r++) {
-        const int side = 2 * r + 1, ncells = side * side * side;
         int t = 0;
         int32_t p = 0, b = 0;
         bool more = active;
         while (__any_sync(FULL_MASK, more)) {
-            int64_t cand = -1;
             if (more) {
-                while (p >= b && t < ncells) {
-                    const int dx = t / (side * side) - r, dy = (t / side) % side - r,
-                              dz = t % side - r;
+                // next non-empty cell of the shell
+                while (p >= b) {
+                    int dx, dy, dz;
+                    if (!shell_cell(r, t, dx, dy, dz)) {
+                        more = false;
+                        break;
+                    }
                     t++;
                     const int ch = max(max(abs(dx), abs(dy)), abs(dz));
                     const int32_t x = cx + dx, y = cy + dy, z = cz + dz;
@@ -305,14 +349,15 @@ __global__ void __launch_bounds__(KNN_BLOCK, 3)
                         continue;
                     cell_range(g, l, interleave((uint32_t)x, (uint32_t)y, (uint32_t)z), p, b);
                 }
-                if (p < b) cand = p++;
-                else more = false;
-            }
-            if (cand >= 0 && cand != qp) {
-                const float4 c = pts[cand];
-                const float d2 = dist2_rn(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z));
-                const uint64_t kk = ((uint64_t)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
-                if (kk < tk.kth()) queue[qlen++][lane] = kk;
+                // scan the cell while the queue has room
+                for (; more && p < b && qlen < KNN_QCAP; p++) {
+                    if (p == qp) continue;
+                    const float4 c = pts[p];
+                    const float d2 =
+                        dist2_rn(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z));
+                    const uint64_t kk = ((uint64_t)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
+                    if (kk < tk.kth()) queue[qlen++][lane] = kk;
+                }
             }
             if (__any_sync(FULL_MASK, qlen == KNN_QCAP)) flush_queue<KMAX>(queue, lane, qlen, tk);
         }

@@ -164,6 +164,26 @@ __device__ __forceinline__ void copy_row(const Rows &in, int64_t a, const WRows 
     }
 }
 
+// Row moves with one thread per 16-byte SH chunk plus one thread for the 11
+// scalar fields, so each row's SH is read and written by consecutive lanes.
+// mode 0: out[pos[v]] = in[v] where keep[v]; 1: out[dst[v]] = in[v];
+// 2: out[v] = in[src[v]].
+__device__ __forceinline__ void move_chunk(const Rows &in, int64_t a, const WRows &out, int64_t b,
+                                           int F, int ch) {
+    const int nch = F >> 2;
+    if (ch < nch) {
+        ((float4 *)(out.sh + b * F))[ch] = __ldg((const float4 *)(in.sh + a * F) + ch);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            out.xyz[3 * b + k] = in.xyz[3 * a + k];
+            out.ls[3 * b + k] = in.ls[3 * a + k];
+        }
+        *(float4 *)(out.rot + 4 * b) = *(const float4 *)(in.rot + 4 * a);
+        out.logit[b] = in.logit[a];
+    }
+}
+
 // merge rows i and j of `in` into row o of `out`; returns 1 if an eigenvalue
 // was raised to the floor
 __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out, int64_t o, int F,
@@ -325,9 +345,19 @@ __global__ void k_keep_flags(int64_t n, const int32_t *__restrict__ role, int32_
 
 __global__ void k_copy_kept(Rows in, WRows out, int64_t n, int F, const int32_t *__restrict__ role,
                             const int32_t *__restrict__ pos) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        if (role[v] == -1) copy_row(in, v, out, pos[v], F);
+    if ((F & 3) == 0) {
+        const int per = (F >> 2) + 1;
+        const int64_t total = n * per;
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t v = t / per;
+            if (role[v] == -1) move_chunk(in, v, out, pos[v], F, (int)(t - v * per));
+        }
+    } else {
+        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+             v += (int64_t)gridDim.x * blockDim.x)
+            if (role[v] == -1) copy_row(in, v, out, pos[v], F);
+    }
 }
 
 __global__ void k_list_merges(int64_t n, const int32_t *__restrict__ mflag,
@@ -409,6 +439,24 @@ __global__ void k_prefilter_flags(const float *__restrict__ logit, int64_t n,
         keep[v] = (double)logit[v] >= thr;
 }
 
+__global__ void k_move_rows(Rows in, WRows out, int64_t n, int F, int mode,
+                            const int32_t *__restrict__ keep, const int32_t *__restrict__ idx) {
+    const int per = (F >> 2) + 1;
+    const int64_t total = n * per;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = t / per;
+        const int ch = (int)(t - v * per);
+        if (mode == 0) {
+            if (keep[v]) move_chunk(in, v, out, idx[v], F, ch);
+        } else if (mode == 1) {
+            move_chunk(in, v, out, idx[v], F, ch);
+        } else {
+            move_chunk(in, idx[v], out, v, F, ch);
+        }
+    }
+}
+
 __global__ void k_compact(Rows in, WRows out, int64_t n, int F, const int32_t *__restrict__ keep,
                           const int32_t *__restrict__ pos) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -459,8 +507,8 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
            (const int32_t *)mpos, list);
     Rows ri = rows_of(in);
     WRows wo = wrows_of(out);
-    launch(c, "copy_kept", dim3(grid), dim3(256), 0, k_copy_kept, ri, wo, n, in.F, role,
-           (const int32_t *)pos);
+    launch(c, "copy_kept", dim3(grid_stride_blocks(c, n * ((in.F >> 2) + 1), 256, 16)), dim3(256),
+           0, k_copy_kept, ri, wo, n, in.F, role, (const int32_t *)pos);
     unsigned long long *hits = (unsigned long long *)ws<uint8_t>(c->b_status, 64) + 1;
     NGS_CHECK_CUDA(cudaMemsetAsync(hits, 0, 8, c->st));
     if (npairs > 0)
@@ -518,21 +566,35 @@ int64_t prefilter_flags(ngs_ctx *c, const float *logit, int64_t n, double tau, i
     return *(int32_t *)c->h_pin;
 }
 
+static void move_rows(ngs_ctx *c, const SplatView &in, SplatView &out, int64_t n, int mode,
+                      const int32_t *keep, const int32_t *idx, const char *name) {
+    if (n <= 0) return;
+    WRows wo = wrows_of(out);
+    if ((in.F & 3) == 0 && in.F <= 64) {
+        const int per = (in.F >> 2) + 1;
+        launch(c, name, dim3(grid_stride_blocks(c, n * per, 256, 16)), dim3(256), 0, k_move_rows,
+               rows_of(in), wo, n, in.F, mode, keep, idx);
+    } else if (mode == 0) {
+        launch(c, name, dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_compact, rows_of(in),
+               wo, n, in.F, keep, idx);
+    } else if (mode == 1) {
+        launch(c, name, dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_scatter, rows_of(in),
+               wo, n, in.F, idx);
+    } else {
+        launch(c, name, dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_gather, rows_of(in),
+               wo, n, in.F, (const uint32_t *)idx);
+    }
+}
+
 void compact_rows(ngs_ctx *c, const SplatView &in, const int32_t *keep, const int32_t *pos,
                   SplatView &out) {
-    WRows wo = wrows_of(out);
-    launch(c, "compact_rows", dim3(grid_stride_blocks(c, in.n, 256, 8)), dim3(256), 0, k_compact,
-           rows_of(in), wo, in.n, in.F, keep, pos);
+    move_rows(c, in, out, in.n, 0, keep, pos, "compact_rows");
 }
 
 void scatter_rows(ngs_ctx *c, const SplatView &in, const int32_t *dst, SplatView &out) {
-    WRows wo = wrows_of(out);
-    launch(c, "scatter_rows", dim3(grid_stride_blocks(c, in.n, 256, 8)), dim3(256), 0, k_scatter,
-           rows_of(in), wo, in.n, in.F, dst);
+    move_rows(c, in, out, in.n, 1, nullptr, dst, "scatter_rows");
 }
 
 void gather_rows(ngs_ctx *c, const SplatView &in, const uint32_t *src, SplatView &out) {
-    WRows wo = wrows_of(out);
-    launch(c, "gather_rows", dim3(grid_stride_blocks(c, out.n, 256, 8)), dim3(256), 0, k_gather,
-           rows_of(in), wo, out.n, in.F, src);
+    move_rows(c, in, out, out.n, 2, nullptr, (const int32_t *)src, "gather_rows");
 }

@@ -246,8 +246,9 @@ static void check_splats(const ngs_splats *s, const char *fn) {
     if (s->sh_dim < 1 || s->sh_dim > 64) NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: sh_dim out of range", fn);
     if (s->n > 0 && (!s->xyz || !s->log_scale || !s->rot || !s->opacity_logit || !s->sh))
         NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: NULL array", fn);
-    if ((s->sh_dim & 3) == 0 && ((uintptr_t)s->sh & 15))
-        NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: sh must be 16-byte aligned", fn);
+    if (((s->sh_dim & 3) == 0 && ((uintptr_t)s->sh & 15)) || ((uintptr_t)s->rot & 15))
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: rot (and sh when sh_dim %% 4 == 0) must be 16-byte aligned",
+                 fn);
 }
 
 static SplatView view_of(const ngs_splats *s) {
