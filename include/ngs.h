@@ -210,6 +210,33 @@ int ngs_simplify(ngs_ctx *ctx, ngs_splats *inout, int64_t target_count, ngs_stat
 int ngs_simplify_host(ngs_ctx *ctx, ngs_splats *host_inout, int64_t target_count,
                       ngs_stats *stats);
 
+/* ---- allocation-free entry point ---- */
+
+/* Largest point count ngs_knn_noalloc accepts. */
+#define NGS_NOALLOC_MAX_N 65536
+
+/* The paper has no counterpart to this call: it exists for callers that
+ * cannot allocate device memory -- hosts that own every device buffer
+ * themselves (an engine or renderer with a fixed memory budget, a plugin
+ * that may only touch the buffers it is handed) or code paths where
+ * cudaMalloc is not acceptable because it can synchronise the device.
+ * It computes exactly the directed neighbour table of ngs_build_graph
+ * (graph->nbr) without a context and without allocating anything:
+ *   xyz    device, n*3 FP32 centres (caller-owned)
+ *   n      0 .. NGS_NOALLOC_MAX_N (larger n returns NGS_ERR_INVALID_ARG)
+ *   k      1 .. NGS_MAX_K; k_eff = min(k, n-1) columns are written
+ *   nbr    device, n*k_eff int32 (caller-owned); row i lists the k_eff
+ *          nearest other centres by (d^2, index)
+ *   stream cudaStream_t as void* (NULL = legacy default stream)
+ * All temporaries live in one fixed device array inside the library (about
+ * 3 MB on every device that loads it, held until the process exits).  That
+ * array is shared by all calls and keeps the last call's contents, so calls
+ * that overlap on the GPU race and must be serialised by the caller.  The
+ * first call on each device looks up the array's device address and should
+ * come before any stream capture.  The call synchronises `stream` once (to
+ * check that every coordinate is finite).  Errors: INVALID_ARG, CUDA. */
+int ngs_knn_noalloc(const float *xyz, int64_t n, int32_t k, int32_t *nbr, void *stream);
+
 /* ---- instrumentation ---- */
 
 /* When enabled, every kernel launch of the ctx is bracketed by CUDA events on

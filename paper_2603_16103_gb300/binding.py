@@ -101,6 +101,7 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_double)]),
     "ngs_profile_reset": (ctypes.c_int, [_P]),
     "ngs_launch_count": (ctypes.c_int64, [_P]),
+    "ngs_knn_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
 }
 
 
@@ -198,6 +199,12 @@ def ngs_simplify_host(ctx: int, s: ngs_splats, target: int) -> dict:
     st = ngs_stats()
     _check(load().ngs_simplify_host(_P(ctx), ctypes.byref(s), target, ctypes.byref(st)))
     return st.as_dict()
+
+
+def ngs_knn_noalloc(xyz_ptr: int, n: int, k: int, nbr_ptr: int, stream=None):
+    """Directed kNN table into caller-owned memory without any allocation."""
+    s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    _check(load().ngs_knn_noalloc(_P(xyz_ptr), n, k, _P(nbr_ptr), _P(s)))
 
 
 def ngs_profile_enable(ctx: int, enable: bool):
