@@ -12,8 +12,8 @@
 //   Sigma_m = V diag(lambda) V^T -> log-scale = log(max(lambda, floor)) / 2,
 //             rotation = V as a unit quaternion.
 // The eigendecomposition starts with an FP32 cyclic Jacobi and is finished
-// in FP64 (Sigma_m assembled in FP64, Jacobi sweeps in FP64 warm-started
-// from the FP32 eigenvectors).  Canonical form: eigenvalues descending,
+// in FP64 (Sigma_m assembled in FP64, one FP64 Jacobi sweep warm-started
+// from the re-orthonormalised FP32 eigenvectors).  Canonical form: eigenvalues descending,
 // each eigenvector's largest-magnitude component positive, det V = +1,
 // quaternion with w >= 0.
 #include "ngs_device.cuh"
@@ -90,6 +90,69 @@ __device__ __forceinline__ T diag2(const T *A) {
     return A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
 }
 
+// FP64 1/sqrt(x) for x of order one or larger than FLT_MIN: an FP32 estimate
+// refined by two Newton steps.
+__device__ __forceinline__ double rsqrt64(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y;
+}
+
+__device__ __forceinline__ void quat_rot64(const float *q, double *R) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double inv = rsqrt64(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// One FP64 Jacobi sweep on a nearly diagonal symmetric B, V <- V J.  When the
+// off-diagonal entry is tiny against the diagonal gap the rotation is the
+// small-angle one, t = b_pq / (b_qq - b_pp) (in FP32: its relative error only
+// scales the residual), c = 1 - t^2/2, s = t c, orthogonal to O(t^4); other
+// rotations use the exact formula in FP64.
+__device__ __forceinline__ void refine_sweep64(double *B, double *V) {
+#pragma unroll
+    for (int pq = 0; pq < 3; pq++) {
+        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+        const double apq = B[3 * p + q];
+        if (apq == 0.0) continue;
+        const double diff = B[3 * q + q] - B[3 * p + p];
+        double c, s;
+        if (fabs(apq) < 1e-4 * fabs(diff)) {
+            const double t = (double)((float)apq / (float)diff);
+            c = 1.0 - 0.5 * t * t;
+            s = t * c;
+        } else {
+            const double tau = diff / (2.0 * apq);
+            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const double bkp = B[3 * k + p], bkq = B[3 * k + q];
+            B[3 * k + p] = c * bkp - s * bkq;
+            B[3 * k + q] = s * bkp + c * bkq;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const double bpk = B[3 * p + k], bqk = B[3 * q + k];
+            B[3 * p + k] = c * bpk - s * bqk;
+            B[3 * q + k] = s * bpk + c * bqk;
+        }
+        B[3 * p + q] = B[3 * q + p] = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const double vkp = V[3 * k + p], vkq = V[3 * k + q];
+            V[3 * k + p] = c * vkp - s * vkq;
+            V[3 * k + q] = s * vkp + c * vkq;
+        }
+    }
+}
+
 // canonical eigen form + quaternion (w >= 0)
 __device__ void canonical_quat(double *lam, double *V, float *q_out) {
     // sort descending (3-element network), permuting columns
@@ -115,27 +178,29 @@ __device__ void canonical_quat(double *lam, double *V, float *q_out) {
                  V[2] * (V[3] * V[7] - V[4] * V[6]);
     if (det < 0)
         for (int r = 0; r < 3; r++) V[3 * r + 2] = -V[3 * r + 2];
-    // rotation matrix -> quaternion, pivot on the largest of trace and diagonal
-    const double *R = V;
-    double tr = R[0] + R[4] + R[8];
-    double w, x, y, z;
+    // rotation matrix -> quaternion (FP32), pivot on the largest of trace and diagonal
+    float R[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) R[k] = (float)V[k];
+    const float tr = R[0] + R[4] + R[8];
+    float w, x, y, z;
     if (tr >= R[0] && tr >= R[4] && tr >= R[8]) {
-        double r = sqrt(1.0 + tr), h = 0.5 / r;
-        w = 0.5 * r; x = (R[7] - R[5]) * h; y = (R[2] - R[6]) * h; z = (R[3] - R[1]) * h;
+        const float r = sqrtf(1.0f + tr), h = 0.5f / r;
+        w = 0.5f * r; x = (R[7] - R[5]) * h; y = (R[2] - R[6]) * h; z = (R[3] - R[1]) * h;
     } else if (R[0] >= R[4] && R[0] >= R[8]) {
-        double r = sqrt(1.0 + R[0] - R[4] - R[8]), h = 0.5 / r;
-        x = 0.5 * r; w = (R[7] - R[5]) * h; y = (R[1] + R[3]) * h; z = (R[2] + R[6]) * h;
+        const float r = sqrtf(1.0f + R[0] - R[4] - R[8]), h = 0.5f / r;
+        x = 0.5f * r; w = (R[7] - R[5]) * h; y = (R[1] + R[3]) * h; z = (R[2] + R[6]) * h;
     } else if (R[4] >= R[8]) {
-        double r = sqrt(1.0 - R[0] + R[4] - R[8]), h = 0.5 / r;
-        y = 0.5 * r; w = (R[2] - R[6]) * h; x = (R[1] + R[3]) * h; z = (R[5] + R[7]) * h;
+        const float r = sqrtf(1.0f - R[0] + R[4] - R[8]), h = 0.5f / r;
+        y = 0.5f * r; w = (R[2] - R[6]) * h; x = (R[1] + R[3]) * h; z = (R[5] + R[7]) * h;
     } else {
-        double r = sqrt(1.0 - R[0] - R[4] + R[8]), h = 0.5 / r;
-        z = 0.5 * r; w = (R[3] - R[1]) * h; x = (R[2] + R[6]) * h; y = (R[5] + R[7]) * h;
+        const float r = sqrtf(1.0f - R[0] - R[4] + R[8]), h = 0.5f / r;
+        z = 0.5f * r; w = (R[3] - R[1]) * h; x = (R[2] + R[6]) * h; y = (R[5] + R[7]) * h;
     }
-    if (w < 0) { w = -w; x = -x; y = -y; z = -z; }
-    double inv = 1.0 / sqrt(w * w + x * x + y * y + z * z);
-    q_out[0] = (float)(w * inv); q_out[1] = (float)(x * inv);
-    q_out[2] = (float)(y * inv); q_out[3] = (float)(z * inv);
+    if (w < 0.f) { w = -w; x = -x; y = -y; z = -z; }
+    const float inv = rsqrtf(w * w + x * x + y * y + z * z);
+    q_out[0] = w * inv; q_out[1] = x * inv;
+    q_out[2] = y * inv; q_out[3] = z * inv;
 }
 
 struct Rows {
@@ -254,20 +319,20 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
     const float lmin = fminf(fminf(A[0], A[4]), A[8]), lmax = fmaxf(fmaxf(A[0], A[4]), A[8]);
     const bool fp64 = policy != 2 || !(lmin > 1e-4f * lmax);
     if (fp64) {
-        // FP64 finish: assemble Sigma_m in FP64, rotate into the FP32 eigenbasis
-        // (re-orthonormalised), and sweep to convergence.
+        // FP64 finish: Sigma_m assembled in FP64 (rotations normalised in FP64,
+        // s^2 and pi taken from their FP32 values), rotated into the
+        // re-orthonormalised FP32 eigenbasis, then one FP64 Jacobi sweep.
         double Ri64[9], Rj64[9], s2i64[3], s2j64[3], Si64[9], Sj64[9], S64[9];
-        quat_to_rot<double>(qi, Ri64);
-        quat_to_rot<double>(qj, Rj64);
+        quat_rot64(qi, Ri64);
+        quat_rot64(qj, Rj64);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            s2i64[a] = exp(2.0 * (double)lsi[a]);
-            s2j64[a] = exp(2.0 * (double)lsj[a]);
+            s2i64[a] = (double)s2i[a];
+            s2j64[a] = (double)s2j[a];
         }
         rot_cov<double>(Ri64, s2i64, Si64);
         rot_cov<double>(Rj64, s2j64, Sj64);
-        const double pid = exp(-softplus_d(-((double)lwi - (double)lwj)));
-        const double pjd = exp(-softplus_d((double)lwi - (double)lwj));
+        const double pid = (double)pi, pjd = (double)pj;
         const double dd[3] = {(double)mi[0] - mj[0], (double)mi[1] - mj[1], (double)mi[2] - mj[2]};
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -279,17 +344,17 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
 #pragma unroll
         for (int k = 0; k < 9; k++) Q[k] = V[k];
         {
-            double n0 = 1.0 / sqrt(Q[0] * Q[0] + Q[3] * Q[3] + Q[6] * Q[6]);
+            const double n0 = rsqrt64(Q[0] * Q[0] + Q[3] * Q[3] + Q[6] * Q[6]);
             Q[0] *= n0; Q[3] *= n0; Q[6] *= n0;
-            double dp = Q[0] * Q[1] + Q[3] * Q[4] + Q[6] * Q[7];
+            const double dp = Q[0] * Q[1] + Q[3] * Q[4] + Q[6] * Q[7];
             Q[1] -= dp * Q[0]; Q[4] -= dp * Q[3]; Q[7] -= dp * Q[6];
-            double n1 = 1.0 / sqrt(Q[1] * Q[1] + Q[4] * Q[4] + Q[7] * Q[7]);
+            const double n1 = rsqrt64(Q[1] * Q[1] + Q[4] * Q[4] + Q[7] * Q[7]);
             Q[1] *= n1; Q[4] *= n1; Q[7] *= n1;
             Q[2] = Q[3] * Q[7] - Q[6] * Q[4];
             Q[5] = Q[6] * Q[1] - Q[0] * Q[7];
             Q[8] = Q[0] * Q[4] - Q[3] * Q[1];
         }
-        // B = Q^T S64 Q
+        // B = Q^T S64 Q (nearly diagonal)
         double T[9], B[9];
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -300,14 +365,11 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int b = a; b < 3; b++) {
-                double v = Q[a] * T[b] + Q[3 + a] * T[3 + b] + Q[6 + a] * T[6 + b];
+                const double v = Q[a] * T[b] + Q[3 + a] * T[3 + b] + Q[6 + a] * T[6 + b];
                 B[3 * a + b] = v;
                 B[3 * b + a] = v;
             }
-        for (int sw = 0; sw < 4; sw++) {
-            if (offdiag2(B) <= 1e-30 * diag2(B)) break;
-            jacobi_sweep<double>(B, Q);
-        }
+        refine_sweep64(B, Q);
         lam[0] = B[0]; lam[1] = B[4]; lam[2] = B[8];
 #pragma unroll
         for (int k = 0; k < 9; k++) V64[k] = Q[k];
@@ -326,7 +388,7 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
             l = eig_floor;
             hits = 1;
         }
-        out.ls[3 * o + a] = (float)(0.5 * log(l));
+        out.ls[3 * o + a] = 0.5f * logf((float)l);
     }
 #pragma unroll
     for (int k = 0; k < 4; k++) out.rot[4 * o + k] = q[k];
