@@ -244,9 +244,8 @@ __device__ __forceinline__ void load_R(const Rec &r, float *R, float *invs) {
 }
 
 __global__ void __launch_bounds__(256, 3)
-    k_edge_cost(const int32_t *__restrict__ slots, const int32_t *__restrict__ nbr,
-                const int32_t *__restrict__ mirror, const int32_t *__restrict__ cid, int kk,
-                int64_t m, const float *__restrict__ rec, const float *__restrict__ sh, int F,
+    k_edge_cost(const int4 *__restrict__ erec, int64_t m, const float *__restrict__ rec,
+                const float *__restrict__ sh, int F,
                 const float *__restrict__ zs, const float *__restrict__ us, int S, int mode,
                 float lg, float la, int policy, const float *__restrict__ xyz,
                 const float *__restrict__ ls, const float *__restrict__ rot,
@@ -255,12 +254,10 @@ __global__ void __launch_bounds__(256, 3)
     const float zz0 = zs[0] * zs[0] + zs[1] * zs[1] + zs[2] * zs[2];
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t sl = slots[e];
-        const int32_t va = sl / kk, vb = nbr[sl];
-        const uint32_t ca = cid ? (uint32_t)cid[va] : (uint32_t)va;
-        const uint32_t cb = cid ? (uint32_t)cid[vb] : (uint32_t)vb;
         // i = lower canonical id: the arithmetic is then independent of row order
-        const int64_t i = ca < cb ? va : vb, j = ca < cb ? vb : va;
+        const int4 er = __ldg(erec + e);
+        const int32_t sl = er.x;
+        const int64_t i = er.y, j = er.z;
         const Rec Ri{(const float4 *)(rec + i * REC)}, Rj{(const float4 *)(rec + j * REC)};
         // ---- appearance term
         float dapp = 0.f;
@@ -360,21 +357,19 @@ __global__ void __launch_bounds__(256, 3)
         if (fm && (threadIdx.x & 31) == __ffs(fm) - 1) atomicAdd(fp64_count, (unsigned long long)__popc(fm));
         const float c = lg * dgeo + la * dapp;
         cost_slot[sl] = c;
-        const int32_t mr = mirror[sl];
-        if (mr >= 0) cost_slot[mr] = c;
+        if (er.w >= 0) cost_slot[er.w] = c;
         if (cost_out) cost_out[e] = c;
     }
 }
 
-__global__ void k_costs_to_slots(const int32_t *__restrict__ lex_slot,
-                                 const int32_t *__restrict__ mirror, int64_t m,
+__global__ void k_costs_to_slots(const int4 *__restrict__ erec_lex, int64_t m,
                                  const float *__restrict__ cost, float *cost_slot) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int32_t s = lex_slot[e];
-        float c = cost[e];
-        cost_slot[s] = c;
-        if (mirror[s] >= 0) cost_slot[mirror[s]] = c;
+        const int4 r = erec_lex[e];
+        const float c = cost[e];
+        cost_slot[r.x] = c;
+        if (r.w >= 0) cost_slot[r.w] = c;
     }
 }
 
@@ -398,8 +393,8 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
     unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c->b_status, 64);
     NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, c->st));
     launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0, k_edge_cost,
-           (const int32_t *)(lex ? g.lex_slot : g.eslot), g.nbr, (const int32_t *)g.mirror, g.cid,
-           g.k_eff, m, (const float *)rec, (const float *)s.sh, s.F, (const float *)zs,
+           (const int4 *)(lex ? g.erec_lex : g.erec), m, (const float *)rec, (const float *)s.sh,
+           s.F, (const float *)zs,
            (const float *)(zs + 3 * S), S, c->prm.cost_mode, c->prm.lambda_geo,
            c->prm.lambda_app, c->prm.fp64_policy, (const float *)s.xyz, (const float *)s.ls,
            (const float *)s.rot, (const float *)s.logit, g.cost_slot, lex ? cost_out : nullptr,
@@ -411,6 +406,5 @@ void costs_to_slots(ngs_ctx *c, GraphDev &g, const float *cost_lex) {
     const int64_t m = g.n_edges;
     if (m <= 0) return;
     launch(c, "costs_to_slots", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0,
-           k_costs_to_slots, (const int32_t *)g.lex_slot, (const int32_t *)g.mirror, m, cost_lex,
-           g.cost_slot);
+           k_costs_to_slots, (const int4 *)g.erec_lex, m, cost_lex, g.cost_slot);
 }

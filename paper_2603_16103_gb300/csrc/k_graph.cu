@@ -5,8 +5,9 @@
 //   * A slot is mutual when v is also in u's list; mirror[s] is then the
 //     partner slot, otherwise -1.
 //   * Each undirected edge has exactly one canonical slot: a non-mutual slot,
-//     or the mutual slot whose row has the lower canonical id.  eslot[]
-//     lists the canonical slots in slot order; |E| = their number.
+//     or the mutual slot whose row has the lower canonical id.  erec[] lists
+//     one record (slot, lo row, hi row, mirror slot) per canonical slot in
+//     slot order; |E| = their number.
 //   * rev[] lists, per vertex u, the non-mutual slots that point at u (its
 //     in-edges not already in its own list).
 // So the incident edges of v are its k slots plus its rev entries, each once,
@@ -32,11 +33,19 @@ __global__ void k_slot_classify(const int32_t *__restrict__ nbr, int64_t n, int 
         const int32_t u = nbr[s];
         const int32_t *row = nbr + (int64_t)u * k;
         int tp = -1;
-        for (int t = 0; t < k; t++)
-            if (row[t] == v) {
-                tp = t;
-                break;
+        if ((k & 3) == 0) {
+            // 16-byte loads of u's row, first match kept
+            for (int t = k - 4; t >= 0; t -= 4) {
+                const int4 r = __ldg((const int4 *)(row + t));
+                if (r.w == v) tp = t + 3;
+                if (r.z == v) tp = t + 2;
+                if (r.y == v) tp = t + 1;
+                if (r.x == v) tp = t;
             }
+        } else {
+            for (int t = k - 1; t >= 0; t--)
+                if (row[t] == v) tp = t;
+        }
         if (tp >= 0) {
             mirror[s] = u * k + tp;
             canon[s] = cid_of(cid, v) < cid_of(cid, u) ? 1 : 0;
@@ -48,18 +57,24 @@ __global__ void k_slot_classify(const int32_t *__restrict__ nbr, int64_t n, int 
     }
 }
 
+// Canonical slots -> edge records (slot, lo row, hi row, mirror slot), where
+// lo is the endpoint with the lower canonical id; reverse index entries.
 __global__ void k_slot_fill(const int32_t *__restrict__ nbr, int64_t n, int k,
-                            const int32_t *__restrict__ mirror, const int32_t *__restrict__ canon,
-                            const int32_t *__restrict__ epos, const int32_t *__restrict__ rev_ptr,
-                            int32_t *revfill, int32_t *eslot, int32_t *rev) {
+                            const int32_t *__restrict__ cid, const int32_t *__restrict__ mirror,
+                            const int32_t *__restrict__ canon, const int32_t *__restrict__ epos,
+                            const int32_t *__restrict__ rev_ptr, int32_t *revfill, int4 *erec,
+                            int32_t *rev) {
     const int64_t m = n * k;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < m;
          s += (int64_t)gridDim.x * blockDim.x) {
-        if (canon[s]) eslot[epos[s]] = (int32_t)s;
-        if (mirror[s] < 0) {
-            int32_t u = nbr[s];
-            rev[rev_ptr[u] + atomicAdd(&revfill[u], 1)] = (int32_t)s;
+        const int32_t u = nbr[s];
+        const int32_t mr = mirror[s];
+        if (canon[s]) {
+            const int32_t v = (int32_t)(s / k);
+            const bool vlo = cid_of(cid, v) < cid_of(cid, u);
+            erec[epos[s]] = make_int4((int32_t)s, vlo ? v : u, vlo ? u : v, mr);
         }
+        if (mr < 0) rev[rev_ptr[u] + atomicAdd(&revfill[u], 1)] = (int32_t)s;
     }
 }
 
@@ -71,29 +86,27 @@ __global__ void k_zero2(int32_t *a, int32_t *b, int64_t n) {
     }
 }
 
-// lexicographic view: keys (lo, hi) of each canonical slot
-__global__ void k_lex_keys(const int32_t *__restrict__ eslot, int64_t ne,
-                           const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ cid,
-                           uint32_t *klo, uint32_t *khi, uint32_t *val) {
+// lexicographic view: keys (lo, hi) of each edge record
+__global__ void k_lex_keys(const int4 *__restrict__ erec, int64_t ne,
+                           const int32_t *__restrict__ cid, uint32_t *klo, uint32_t *khi,
+                           uint32_t *val) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int32_t s = eslot[e];
-        int32_t v = s / k, u = nbr[s];
-        uint32_t cv = cid_of(cid, v), cu = cid_of(cid, u);
-        klo[e] = cv < cu ? cv : cu;
-        khi[e] = cv < cu ? cu : cv;
-        val[e] = (uint32_t)s;
+        const int4 r = erec[e];
+        klo[e] = cid_of(cid, r.y);
+        khi[e] = cid_of(cid, r.z);
+        val[e] = (uint32_t)e;
     }
 }
 
 __global__ void k_lex_view(const uint32_t *__restrict__ klo, const uint32_t *__restrict__ khi,
-                           const uint32_t *__restrict__ val, int64_t ne, int32_t *elo,
-                           int32_t *ehi, int32_t *lex_slot) {
+                           const uint32_t *__restrict__ perm, const int4 *__restrict__ erec,
+                           int64_t ne, int32_t *elo, int32_t *ehi, int4 *erec_lex) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
          e += (int64_t)gridDim.x * blockDim.x) {
         elo[e] = (int32_t)klo[e];
         ehi[e] = (int32_t)khi[e];
-        lex_slot[e] = (int32_t)val[e];
+        erec_lex[e] = erec[perm[e]];
     }
 }
 
@@ -124,11 +137,11 @@ void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
     sync_stream(c);
     g.n_edges = ((int32_t *)c->h_pin)[0];
     const int64_t nrev = ((int32_t *)c->h_pin)[1];
-    g.eslot = ws<int32_t>(c->b_elo, g.n_edges);
+    g.erec = ws<int4>(c->b_elo, g.n_edges);
     g.rev = ws<int32_t>(c->b_upc, nrev);
     launch(c, "slot_fill", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0, k_slot_fill,
-           nbr, n, k, (const int32_t *)g.mirror, (const int32_t *)canon, (const int32_t *)epos,
-           (const int32_t *)g.rev_ptr, revfill, g.eslot, g.rev);
+           nbr, n, k, g.cid, (const int32_t *)g.mirror, (const int32_t *)canon,
+           (const int32_t *)epos, (const int32_t *)g.rev_ptr, revfill, g.erec, g.rev);
     g.cost_slot = ws<float>(c->b_cost, m);
 }
 
@@ -139,8 +152,8 @@ void build_lex_view(ngs_ctx *c, GraphDev &g) {
     uint32_t *val = ws<uint32_t>(c->b_vals, ne);
     uint32_t *t1 = ws<uint32_t>(c->b_vals2, ne);
     launch(c, "lex_keys", dim3(grid_stride_blocks(c, ne, 256, 8)), dim3(256), 0, k_lex_keys,
-           (const int32_t *)g.eslot, ne, (const int32_t *)g.nbr, g.k_eff, g.cid, klo, khi, val);
-    // LSD over (lo, hi): stable sort by hi, then by lo.  Payload = position.
+           (const int4 *)g.erec, ne, g.cid, klo, khi, val);
+    // LSD over (lo, hi): stable sort by hi, then by lo.  Payload = record index.
     uint32_t *idx = ws<uint32_t>(c->b_cid, ne), *idx2 = ws<uint32_t>(c->b_cid2, ne);
     uint32_t *ktmp = ws<uint32_t>(c->b_pos, ne);
     iota_u32(c, idx, ne);
@@ -149,11 +162,10 @@ void build_lex_view(ngs_ctx *c, GraphDev &g) {
     gather_u32(c, klo, idx, ne, t1);          // lo in hi-sorted order
     radix_sort_u32(c, t1, idx, ktmp, idx2, ne, 32);
     g.elo = ws<int32_t>(c->b_ehi, ne);
-    g.ehi = ws<int32_t>(c->b_nbr2, 2 * ne);
-    g.lex_slot = g.ehi + ne;
+    g.ehi = ws<int32_t>(c->b_nbr2, ne);
+    g.erec_lex = ws<int4>(c->b_lexrec, ne);
     gather_u32(c, khi, idx, ne, ktmp);
-    gather_u32(c, val, idx, ne, idx2);
     launch(c, "lex_view", dim3(grid_stride_blocks(c, ne, 256, 8)), dim3(256), 0, k_lex_view,
-           (const uint32_t *)t1, (const uint32_t *)ktmp, (const uint32_t *)idx2, ne, g.elo, g.ehi,
-           g.lex_slot);
+           (const uint32_t *)t1, (const uint32_t *)ktmp, (const uint32_t *)idx,
+           (const int4 *)g.erec, ne, g.elo, g.ehi, g.erec_lex);
 }

@@ -47,13 +47,16 @@ __device__ __forceinline__ void consider(int32_t u, float cst, uint32_t cv,
     }
 }
 
-__global__ void k_match_scan(int64_t n, int kk, const int32_t *__restrict__ nbr,
+__global__ void k_match_scan(const int32_t *__restrict__ wl, const int32_t *__restrict__ wl_count,
+                             int64_t n_all, int kk, const int32_t *__restrict__ nbr,
                              const float *__restrict__ cost_slot,
                              const int32_t *__restrict__ rev_ptr, const int32_t *__restrict__ rev,
                              const int32_t *__restrict__ cid, const int32_t *__restrict__ mate,
                              int32_t *cand, uint32_t *candkey) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cnt = wl ? (int64_t)*wl_count : n_all;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < cnt;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = wl ? (int64_t)wl[idx] : idx;
         if (mate[v] != -1) continue;
         int32_t c = cand[v];
         if (c == -1) continue;                  // no free neighbour: stays single
@@ -73,18 +76,24 @@ __global__ void k_match_scan(int64_t n, int kk, const int32_t *__restrict__ nbr,
     }
 }
 
-// Match mutual pointers; count new pairs of this round.
-__global__ void k_match_pair(int64_t n, const int32_t *__restrict__ cand, int32_t *mate,
-                             int32_t *round_count) {
+// Match mutual pointers; count new pairs of this round; vertices that stay
+// free with a candidate go to the next round's worklist.
+__global__ void k_match_pair(const int32_t *__restrict__ wl, const int32_t *__restrict__ wl_count,
+                             int64_t n_all, const int32_t *__restrict__ cand, int32_t *mate,
+                             int32_t *round_count, int32_t *wl_next, int32_t *wl_next_count) {
+    const int64_t cnt = wl ? (int64_t)*wl_count : n_all;
     int found = 0;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < cnt;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = wl ? (int64_t)wl[idx] : idx;
         if (mate[v] != -1) continue;
-        int32_t u = cand[v];
+        const int32_t u = cand[v];
         if (u < 0) continue;
         if (cand[u] == (int32_t)v) {
             mate[v] = u;
             if (v < u) found++;
+        } else {
+            wl_next[atomicAdd(wl_next_count, 1)] = (int32_t)v;
         }
     }
 #pragma unroll
@@ -159,25 +168,30 @@ int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *
     int32_t *cand = ws<int32_t>(c->b_cand, n);
     uint32_t *candkey = ws<uint32_t>(c->b_candkey, n);
     const int max_rounds = 4096;
-    int32_t *counts = ws<int32_t>(c->b_counts, max_rounds);
-    NGS_CHECK_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * max_rounds, c->st));
+    int32_t *counts = ws<int32_t>(c->b_counts, 2 * max_rounds);
+    int32_t *wl_counts = counts + max_rounds;  // worklist size feeding round r+1
+    NGS_CHECK_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2 * max_rounds, c->st));
+    int32_t *wl[2] = {ws<int32_t>(c->b_sel2, n), ws<int32_t>(c->b_cflag2, n)};
     const unsigned grid = grid_stride_blocks(c, n, 256, 8);
     launch(c, "match_init", dim3(grid), dim3(256), 0, k_match_init, n, mate, cand);
     int64_t matched = 0;
     int r = 0;
     if (g.n_edges > 0 && max_pairs > 0) {
-        // rounds are launched in batches; a batch is checked once on the host
+        // rounds are launched in batches; a batch is checked once on the host.
+        // Round 0 visits every vertex, later rounds only the worklist.
         int batch = 4;
         bool done = false;
         while (!done) {
             if (r + batch > max_rounds)
                 NGS_FAIL(NGS_ERR_TIMEOUT, "matching did not converge in %d rounds", max_rounds);
             for (int b = 0; b < batch; b++, r++) {
-                launch(c, "match_scan", dim3(grid), dim3(256), 0, k_match_scan, n, g.k_eff,
-                       g.nbr, (const float *)g.cost_slot, (const int32_t *)g.rev_ptr,
+                const int32_t *in_wl = r == 0 ? nullptr : wl[(r - 1) & 1];
+                const int32_t *in_cnt = r == 0 ? nullptr : wl_counts + (r - 1);
+                launch(c, "match_scan", dim3(grid), dim3(256), 0, k_match_scan, in_wl, in_cnt, n,
+                       g.k_eff, g.nbr, (const float *)g.cost_slot, (const int32_t *)g.rev_ptr,
                        (const int32_t *)g.rev, g.cid, (const int32_t *)mate, cand, candkey);
-                launch(c, "match_pair", dim3(grid), dim3(256), 0, k_match_pair, n,
-                       (const int32_t *)cand, mate, counts + r);
+                launch(c, "match_pair", dim3(grid), dim3(256), 0, k_match_pair, in_wl, in_cnt, n,
+                       (const int32_t *)cand, mate, counts + r, wl[r & 1], wl_counts + r);
             }
             int32_t *hc = (int32_t *)(c->h_pin + 32);
             NGS_CHECK_CUDA(cudaMemcpyAsync(hc, counts + r - batch, sizeof(int32_t) * batch,

@@ -210,7 +210,8 @@ extern "C" int ngs_destroy(ngs_ctx *c) {
                       &c->b_elo, &c->b_ehi, &c->b_rec, &c->b_cost, &c->b_rng, &c->b_mate,
                       &c->b_cand, &c->b_candkey, &c->b_counts, &c->b_sel, &c->b_role, &c->b_keep,
                       &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
-                      &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2};
+                      &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2,
+                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2};
     for (DevBuf *b : bufs) ws_free(*b);
     for (int k = 0; k < 5; k++) {
         ws_free(c->b_sA[k]);

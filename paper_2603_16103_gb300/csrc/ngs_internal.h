@@ -72,13 +72,13 @@ struct GraphDev {
     const int32_t *cid;     // canonical ids (nullptr = identity)
     const int32_t *nbr;     // n*k directed neighbours (slot s = v*k + t)
     int32_t *mirror;        // n*k partner slot of a mutual edge, else -1
-    int32_t *eslot;         // |E| canonical slots, ascending
+    int4 *erec;             // |E| edge records (slot, lo row, hi row, mirror slot)
     int32_t *rev_ptr;       // n+1 offsets into rev
     int32_t *rev;           // non-mutual slots pointing at each vertex
     float *cost_slot;       // n*k cost of the edge of each slot
     int64_t n_edges;        // |E| (host copy)
     int32_t *elo, *ehi;     // C-ABI view: lexicographic edges (canonical ids)
-    int32_t *lex_slot;      // canonical slot of lexicographic edge e
+    int4 *erec_lex;         // edge records in lexicographic order
 };
 
 struct ngs_ctx {
@@ -102,7 +102,7 @@ struct ngs_ctx {
     DevBuf b_mate, b_cand, b_candkey, b_counts, b_sel, b_role, b_keep, b_pos, b_flag;
     DevBuf b_scan_part, b_status, b_misc, b_cid, b_cid2, b_cflag, b_cscan;
     DevBuf b_sA[5], b_sB[5];     // ping-pong splat arrays
-    DevBuf b_pairs, b_partner, b_nbr2;
+    DevBuf b_pairs, b_partner, b_nbr2, b_lexrec, b_sel2, b_cflag2;
     DevBuf b_host_dev[5];        // device staging for ngs_simplify_host
 
     // pinned host scratch
