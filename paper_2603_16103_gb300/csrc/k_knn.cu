@@ -6,10 +6,11 @@
 // at one level l_t (8^l_t ~ 16 n cells, at most 8^9) gives O(1) ranges for l <= l_t and a
 // short binary search inside a table cell for finer levels.
 // Each query (one thread, threads in Morton order) picks the finest level
-// whose 3x3x3 block of cells around it holds at least 64 points, scans its
-// own cell and the 26
-// around it, and then whole shells of cells until its current k-th distance
-// is strictly inside the scanned block (with margins for FP32 rounding of
+// whose 3x3x3 block of cells around it holds at least 64 points.  It scans
+// its own cell, then the 26 around it (faces, edges, corners; a cell is
+// skipped when its box is already farther than the query's current k-th
+// distance), then whole shells of cells until its k-th distance is strictly
+// inside the scanned block (with margins for FP32 rounding of
 // distances and of the quantisation), so the list is exactly the k_eff
 // nearest by (d^2, canonical id).  Distances are (dx^2 + dy^2) + dz^2 in
 // FP32 without contraction.
@@ -347,6 +348,19 @@ __global__ void __launch_bounds__(KNN_BLOCK, 3)
                     const int32_t x = cx + dx, y = cy + dy, z = cz + dz;
                     if (ch != r || x < 0 || y < 0 || z < 0 || x > gmax || y > gmax || z > gmax)
                         continue;
+                    // skip a cell that no point of it could enter the list from: its
+                    // box (widened by the quantisation margin) is farther than the
+                    // current k-th distance with the FP32 slack of d^2
+                    if (r > 0 && tk.kth() != ~0ull) {
+                        const float ex = fmaxf(fmaxf((lx + (float)x * h - margin) - q.x,
+                                                     q.x - (lx + (float)(x + 1) * h + margin)), 0.f);
+                        const float ey = fmaxf(fmaxf((ly + (float)y * h - margin) - q.y,
+                                                     q.y - (ly + (float)(y + 1) * h + margin)), 0.f);
+                        const float ez = fmaxf(fmaxf((lz + (float)z * h - margin) - q.z,
+                                                     q.z - (lz + (float)(z + 1) * h + margin)), 0.f);
+                        const float kd = __uint_as_float((uint32_t)(tk.kth() >> 32));
+                        if ((ex * ex + ey * ey + ez * ez) * (1.0f - 4e-6f) > kd) continue;
+                    }
                     cell_range(g, l, interleave((uint32_t)x, (uint32_t)y, (uint32_t)z), p, b);
                 }
                 // scan the cell while the queue has room

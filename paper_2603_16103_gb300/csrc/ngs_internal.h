@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ngs.h"
+#include "ngs.h"
 
 #define NGS_MAX_N ((int64_t)1 << 25)  // per-scene splat limit (int32 edge offsets)
 #define NGS_LEAF 32                     // kNN tree leaf = one warp of points
