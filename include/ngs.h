@@ -203,6 +203,25 @@ int ngs_merge_compact(ngs_ctx *ctx, ngs_splats *inout, const int32_t *pairs, int
  * Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
 int ngs_simplify(ngs_ctx *ctx, ngs_splats *inout, int64_t target_count, ngs_stats *stats);
 
+/* Largest scene count of one ngs_batch_simplify call. */
+#define NGS_MAX_SCENES 4096
+
+/* ngs_simplify over nscenes independent scenes in one call (the batched form
+ * of Algorithm 1).  scenes[s] (host array of nscenes descriptors, each
+ * describing device-resident splats as for ngs_simplify; all with the same
+ * sh_dim) is simplified in place towards targets[s] (host, >= 1), and
+ * scenes[s].n receives its final count.  Each scene's result is bit-identical
+ * to ngs_simplify on that scene alone: its pre-filter median, Morton frame,
+ * pair cap n_s - target_s and stop rule are its own, and pass p uses the
+ * random numbers of pass p for every scene.  Scenes with target_s > k run
+ * together (every stage of a pass is one launch over all of them); scenes
+ * with target_s <= k run one after another.  The rows of all scenes together
+ * may not exceed 2^26.  stats (may be NULL) sums the per-pass counts over the
+ * scenes; passes is the largest pass count.
+ * Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
+int ngs_batch_simplify(ngs_ctx *ctx, ngs_splats *scenes, const int64_t *targets,
+                       int32_t nscenes, ngs_stats *stats);
+
 /* ngs_simplify for host-resident splats: copies the n rows of the host
  * arrays (pinned or pageable) to ctx-owned device memory, simplifies, and
  * copies the result rows back into the same host arrays (n updated).

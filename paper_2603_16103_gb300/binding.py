@@ -92,6 +92,9 @@ _SIGS = {
     "ngs_merge_compact": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), _P, ctypes.c_int64]),
     "ngs_simplify": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), ctypes.c_int64,
                                     ctypes.POINTER(ngs_stats)]),
+    "ngs_batch_simplify": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                          ctypes.POINTER(ngs_stats)]),
     "ngs_simplify_host": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), ctypes.c_int64,
                                          ctypes.POINTER(ngs_stats)]),
     "ngs_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -192,6 +195,18 @@ def ngs_merge_compact(ctx: int, s: ngs_splats, pairs_ptr: int, n_pairs: int) -> 
 def ngs_simplify(ctx: int, s: ngs_splats, target: int) -> dict:
     st = ngs_stats()
     _check(load().ngs_simplify(_P(ctx), ctypes.byref(s), target, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def ngs_batch_simplify(ctx: int, scenes, targets) -> dict:
+    """scenes: list of ngs_splats (updated in place), targets: list of ints."""
+    n = len(scenes)
+    arr = (ngs_splats * max(1, n))(*scenes)
+    tg = (ctypes.c_int64 * max(1, n))(*[int(t) for t in targets])
+    st = ngs_stats()
+    _check(load().ngs_batch_simplify(_P(ctx), arr, tg, n, ctypes.byref(st)))
+    for i in range(n):
+        scenes[i].n = arr[i].n
     return st.as_dict()
 
 
@@ -334,6 +349,14 @@ class Context:
         s = ds.struct()
         st = ngs_simplify(self.handle, s, target)
         ds.n = s.n
+        return st
+
+    def batch_simplify(self, scenes, targets) -> dict:
+        """Simplify several DeviceSplats in one call (each in place)."""
+        structs = [ds.struct() for ds in scenes]
+        st = ngs_batch_simplify(self.handle, structs, targets)
+        for ds, s in zip(scenes, structs):
+            ds.n = s.n
         return st
 
     def simplify_host(self, hs: DeviceSplats, target: int) -> dict:

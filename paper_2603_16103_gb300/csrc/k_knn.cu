@@ -3,7 +3,7 @@
 // Centres are quantised on a 1024^3 grid over the scene's bounding cube and
 // sorted by Morton code, so every cell of every coarser level 2^l (l <= 10)
 // is a contiguous range of the sorted array.  A dense table of range starts
-// at one level l_t (8^l_t ~ 16 n cells, at most 8^9) gives O(1) ranges for l <= l_t and a
+// at one level l_t (8^l_t >= 4 n cells, at most 8^9) gives O(1) ranges for l <= l_t and a
 // short binary search inside a table cell for finer levels.
 // Each query (one thread, threads in Morton order) picks the finest level
 // whose 3x3x3 block of cells around it holds at least 64 points.  It scans
@@ -125,13 +125,15 @@ __global__ void k_gather_pts(const float *__restrict__ xyz, const int32_t *__res
 // ---------------------------------------------------------------- cell table
 // Per-cell point counts at the table level; an exclusive scan turns them into
 // T[c] = first sorted position of cell c (T[ncell] = n).
-__global__ void k_cell_count(const uint32_t *__restrict__ scode, int64_t n, int shift,
-                             int32_t *cnt) {
+__global__ void k_cell_count(const uint32_t *__restrict__ scode, const int32_t *__restrict__ ssid,
+                             int64_t n, const int32_t *__restrict__ lts,
+                             const int64_t *__restrict__ toff, int32_t *cnt) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t c = scode[p] >> shift;
+        const int sc = ssid ? ssid[p] : 0;
+        const int64_t c = toff[sc] + (int64_t)(scode[p] >> (3 * (10 - lts[sc])));
         // one atomic per run of equal cells inside the warp
-        unsigned peers = __match_any_sync(__activemask(), c);
+        const unsigned peers = __match_any_sync(__activemask(), (unsigned long long)c);
         if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[c], __popc(peers));
     }
 }
@@ -292,17 +294,22 @@ __device__ __forceinline__ bool shell_cell(int r, int t, int &dx, int &dy, int &
 template <int KMAX>
 __global__ void __launch_bounds__(KNN_BLOCK, 3)
     k_knn_grid(const float4 *__restrict__ pts, const uint32_t *__restrict__ scode,
-               const uint32_t *__restrict__ sidx, int64_t n, const int32_t *__restrict__ T, int lt,
-               const float *__restrict__ frame, int keff, int out_by_cid,
-               int32_t *__restrict__ nbr) {
+               const uint32_t *__restrict__ sidx, const int32_t *__restrict__ ssid, int64_t n,
+               const int32_t *__restrict__ Tall, const int32_t *__restrict__ lts,
+               const int64_t *__restrict__ toff, const float *__restrict__ frames, int keff,
+               int out_by_cid, int32_t *__restrict__ nbr) {
     __shared__ uint64_t queue_all[KNN_BLOCK / 32][KNN_QCAP][32];
     const int lane = threadIdx.x & 31;
     uint64_t(*queue)[32] = queue_all[threadIdx.x >> 5];
-    const GridCtx g{scode, T, lt};
-    const float lx = frame[0], ly = frame[1], lz = frame[2], scale = frame[3];
-    const float inv_scale = 1.0f / scale;
     const int64_t qp = (int64_t)blockIdx.x * KNN_BLOCK + threadIdx.x;
     const bool valid = qp < n;
+    // this query's scene: its Morton frame and its cell table
+    const int sc = (ssid && valid) ? ssid[qp] : 0;
+    const int lt = lts[sc];
+    const GridCtx g{scode, Tall + toff[sc], lt};
+    const float *frame = frames + 8 * sc;
+    const float lx = frame[0], ly = frame[1], lz = frame[2], scale = frame[3];
+    const float inv_scale = 1.0f / scale;
     const float4 q = valid ? pts[qp] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t code = valid ? scode[qp] : 0u;
     // level: the finest (up to the table level) whose 3x3x3 block around the
@@ -441,33 +448,61 @@ void gather_points(ngs_ctx *c, const float *xyz, const int32_t *cid, const uint3
            xyz, cid, order, n, pts);
 }
 
+int knn_table_level(int64_t n) {
+    int lt = 1;
+    while (lt < 9 && ((int64_t)1 << (3 * lt)) < 4 * n) lt++;
+    return lt;
+}
+
 void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
     const int64_t n = in.n;
     if (n <= 1 || k_eff <= 0) return;
-    // table level: about 4 or more cells per point (at most 8^9 = 134M
-    // cells); finer levels are resolved by a short search inside a cell
-    int lt = 1;
-    while (lt < 9 && ((int64_t)1 << (3 * lt)) < 4 * n) lt++;
-    const int64_t ncell = (int64_t)1 << (3 * lt);
-    int32_t *T = ws<int32_t>(c->b_nodes, ncell + 1);
-    NGS_CHECK_CUDA(cudaMemsetAsync(T, 0, sizeof(int32_t) * ncell, c->st));
+    const int S = in.nscenes;
+    // per-scene table levels (about 4 or more cells per point, at most 8^9
+    // cells) and offsets of the concatenated tables; a scene's table ends
+    // with one extra zero count so that the global exclusive scan gives every
+    // cell its sorted start position and the scene its end
+    // (small scene counts stay on the stack: the allocation-free entry point
+    // calls this with one scene)
+    int32_t lt_stack[4];
+    int64_t off_stack[5];
+    std::vector<int32_t> lt_heap;
+    std::vector<int64_t> off_heap;
+    int32_t *hlt = lt_stack;
+    int64_t *hoff = off_stack;
+    if (S > 4) {
+        lt_heap.resize(S);
+        off_heap.resize(S + 1);
+        hlt = lt_heap.data();
+        hoff = off_heap.data();
+    }
+    hoff[0] = 0;
+    for (int s = 0; s < S; s++) {
+        hlt[s] = knn_table_level(in.scene_n[s]);
+        hoff[s + 1] = hoff[s] + ((int64_t)1 << (3 * hlt[s])) + 1;
+    }
+    const int64_t tlen = hoff[S];
+    uint8_t *small = ws<uint8_t>(c->b_knnsc, 16 * (S + 1) + 256);
+    int32_t *dlt = (int32_t *)small;
+    int64_t *doff = (int64_t *)(small + ((4 * (size_t)S + 15) & ~(size_t)15));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dlt, hlt, 4 * S, cudaMemcpyHostToDevice, c->st));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(doff, hoff, 8 * (S + 1), cudaMemcpyHostToDevice, c->st));
+    int32_t *T = ws<int32_t>(c->b_nodes, tlen + 1);
+    NGS_CHECK_CUDA(cudaMemsetAsync(T, 0, sizeof(int32_t) * tlen, c->st));
     launch(c, "cell_count", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_cell_count,
-           in.scode, n, 3 * (10 - lt), T);
-    scan_i32(c, T, T, ncell);
+           in.scode, in.ssid, n, (const int32_t *)dlt, (const int64_t *)doff, T);
+    scan_i32(c, T, T, tlen);
     const unsigned grid = blocks_for(n, KNN_BLOCK);
     const int32_t *cT = T;
-    if (k_eff <= 4)
-        launch(c, "knn_k4", dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<4>, in.pts, in.scode, in.sidx, n,
-               cT, lt, in.frame, k_eff, in.out_by_cid, nbr);
-    else if (k_eff <= 8)
-        launch(c, "knn_k8", dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<8>, in.pts, in.scode, in.sidx, n,
-               cT, lt, in.frame, k_eff, in.out_by_cid, nbr);
-    else if (k_eff <= 16)
-        launch(c, "knn_k16", dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<16>, in.pts, in.scode, in.sidx, n,
-               cT, lt, in.frame, k_eff, in.out_by_cid, nbr);
-    else
-        launch(c, "knn_k32", dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<32>, in.pts, in.scode, in.sidx, n,
-               cT, lt, in.frame, k_eff, in.out_by_cid, nbr);
+#define KNN_LAUNCH(KM, NAME)                                                                   \
+    launch(c, NAME, dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<KM>, in.pts, in.scode, in.sidx,   \
+           in.ssid, n, cT, (const int32_t *)dlt, (const int64_t *)doff, in.frames, k_eff,      \
+           in.out_by_cid, nbr)
+    if (k_eff <= 4) KNN_LAUNCH(4, "knn_k4");
+    else if (k_eff <= 8) KNN_LAUNCH(8, "knn_k8");
+    else if (k_eff <= 16) KNN_LAUNCH(16, "knn_k16");
+    else KNN_LAUNCH(32, "knn_k32");
+#undef KNN_LAUNCH
     if (!in.out_by_cid) {
         // rows are internal indices; translate the neighbours' canonical ids
         int32_t *pos_of_cid = ws<int32_t>(c->b_nbr2, n);

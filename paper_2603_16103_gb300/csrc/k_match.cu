@@ -118,16 +118,18 @@ __global__ void k_pair_keys(int64_t n, const int32_t *__restrict__ mate,
     }
 }
 
-// partner[v] = mate[v] if the pair's key <= threshold (or no cap), else -1.
+// partner[v] = mate[v] if the pair's key <= its scene's threshold (or no
+// cap), else -1.  sid == nullptr: one scene, threshold thr[0].
 __global__ void k_apply_cap(int64_t n, const int32_t *__restrict__ mate,
                             const uint32_t *__restrict__ candkey, const int32_t *__restrict__ cid,
-                            const uint64_t *__restrict__ thr, int capped, int32_t *partner) {
-    const uint64_t T = capped ? *thr : ~0ull;
+                            const int32_t *__restrict__ sid, const uint64_t *__restrict__ thr,
+                            int capped, int32_t *partner) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         int32_t u = mate[v];
         int32_t p = -1;
         if (u >= 0) {
+            const uint64_t T = capped ? thr[sid ? sid[v] : 0] : ~0ull;
             uint32_t cv = cid_of(cid, (int32_t)v), cu = cid_of(cid, u);
             uint64_t k = ((uint64_t)candkey[v] << 32) | (cv < cu ? cv : cu);
             if (k <= T) p = u;
@@ -160,7 +162,7 @@ __global__ void k_write_pairs(int64_t n, const int32_t *__restrict__ partner,
 
 }  // namespace
 
-int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *partner) {
+int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
     const int64_t n = g.n;
     c->rounds = 0;
     if (n <= 0) return 0;
@@ -176,7 +178,7 @@ int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *
     launch(c, "match_init", dim3(grid), dim3(256), 0, k_match_init, n, mate, cand);
     int64_t matched = 0;
     int r = 0;
-    if (g.n_edges > 0 && max_pairs > 0) {
+    if (g.n_edges > 0) {
         // rounds are launched in batches; a batch is checked once on the host.
         // Round 0 visits every vertex, later rounds only the worklist.
         int batch = 4;
@@ -208,16 +210,44 @@ int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *
             batch = batch < 16 ? batch * 2 : 16;
         }
     }
+    return matched;
+}
+
+void pair_keys(ngs_ctx *c, const GraphDev &g, uint64_t *keys) {
+    const int64_t n = g.n;
+    launch(c, "pair_keys", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_pair_keys, n,
+           (const int32_t *)c->b_mate.p, (const uint32_t *)c->b_candkey.p, g.cid, keys);
+}
+
+void apply_cap(ngs_ctx *c, const GraphDev &g, const int32_t *sid, const uint64_t *thr,
+               int capped, int32_t *partner) {
+    const int64_t n = g.n;
+    launch(c, "apply_cap", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_apply_cap, n,
+           (const int32_t *)c->b_mate.p, (const uint32_t *)c->b_candkey.p, g.cid, sid, thr, capped,
+           partner);
+}
+
+int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *partner) {
+    const int64_t n = g.n;
+    if (n <= 0) return 0;
+    int64_t matched = 0;
+    c->rounds = 0;
+    if (max_pairs > 0) {
+        matched = match_rounds(c, g);
+    } else {
+        ws<int32_t>(c->b_mate, n);
+        ws<uint32_t>(c->b_candkey, n);
+        launch(c, "match_init", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_match_init, n,
+               (int32_t *)c->b_mate.p, ws<int32_t>(c->b_cand, n));
+    }
     const bool capped = matched > max_pairs;
     uint64_t *thr = (uint64_t *)ws<uint8_t>(c->b_sel, 64);
     if (capped) {
         uint64_t *keys = (uint64_t *)ws<uint8_t>(c->b_flag, sizeof(uint64_t) * n);
-        launch(c, "pair_keys", dim3(grid), dim3(256), 0, k_pair_keys, n, (const int32_t *)mate,
-               (const uint32_t *)candkey, g.cid, keys);
+        pair_keys(c, g, keys);
         radix_select_u64(c, keys, n, max_pairs - 1, thr);
     }
-    launch(c, "apply_cap", dim3(grid), dim3(256), 0, k_apply_cap, n, (const int32_t *)mate,
-           (const uint32_t *)candkey, g.cid, (const uint64_t *)thr, capped ? 1 : 0, partner);
+    apply_cap(c, g, nullptr, thr, capped ? 1 : 0, partner);
     return capped ? max_pairs : matched;
 }
 

@@ -211,13 +211,15 @@ extern "C" int ngs_destroy(ngs_ctx *c) {
                       &c->b_cand, &c->b_candkey, &c->b_counts, &c->b_sel, &c->b_role, &c->b_keep,
                       &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
                       &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2,
-                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2};
+                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc};
     for (DevBuf *b : bufs) ws_free(*b);
     for (int k = 0; k < 5; k++) {
         ws_free(c->b_sA[k]);
         ws_free(c->b_sB[k]);
         ws_free(c->b_host_dev[k]);
+        ws_free(c->b_sC[k]);
     }
+    for (DevBuf &b : c->b_eng) ws_free(b);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -279,11 +281,6 @@ static void copy_rows_d2d(ngs_ctx *c, const SplatView &src, SplatView &dst, int6
     NGS_CHECK_CUDA(cudaMemcpyAsync(dst.sh, src.sh, 4 * (size_t)F * n, cudaMemcpyDeviceToDevice, c->st));
 }
 
-static int k_eff_of(int64_t n, int k) {
-    int ke = k < 1 ? 1 : k;
-    if ((int64_t)ke > n - 1) ke = (int)(n - 1);
-    return ke;
-}
 
 static void check_finite_frame(ngs_ctx *c, const float *frame) {
     NGS_CHECK_CUDA(cudaMemcpyAsync((float *)(c->h_pin + 4), frame + 4, 4, cudaMemcpyDeviceToHost, c->st));
@@ -318,6 +315,7 @@ static void graph_canonical(ngs_ctx *c, const ngs_splats *s) {
     const int64_t n = s->n;
     GraphDev &g = c->g;
     g = GraphDev{};
+    check_slots(n, c->prm.k, "ngs_build_graph");
     g.n = n;
     g.k_eff = n >= 2 ? k_eff_of(n, c->prm.k) : 0;
     g.cid = nullptr;
@@ -332,7 +330,8 @@ static void graph_canonical(ngs_ctx *c, const ngs_splats *s) {
         float4 *pts = ws<float4>(c->b_pts, n);
         gather_points(c, s->xyz, nullptr, vals, n, pts);
         int32_t *nbr = ws<int32_t>(c->b_nbr, n * g.k_eff);
-        knn_search(c, KnnInput{pts, keys, vals, frame, n, 1, nullptr}, g.k_eff, nbr);
+        const int64_t sn = n;
+        knn_search(c, KnnInput{pts, keys, vals, nullptr, frame, &sn, 1, n, 1, nullptr}, g.k_eff, nbr);
         build_edges(c, nbr, g);
         build_lex_view(c, g);
     }
@@ -417,130 +416,77 @@ extern "C" int ngs_merge_compact(ngs_ctx *c, ngs_splats *s, const int32_t *pairs
 }
 
 // ---------------------------------------------------------------- end to end
-namespace {
-__global__ void k_mark_dropped(uint32_t *keys, const int32_t *__restrict__ keep, int64_t n) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        if (!keep[v]) keys[v] |= 1u << 30;
-}
-__global__ void k_fill_ones(int32_t *a, int64_t n) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        a[v] = 1;
-}
-__global__ void k_gather_cid(const uint32_t *__restrict__ order, const int32_t *__restrict__ pos,
-                             int64_t n, int32_t *cid) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x)
-        cid[p] = pos[order[p]];
-}
-}  // namespace
-
-static void simplify_device(ngs_ctx *c, ngs_splats *s, int64_t target, ngs_stats *st) {
-    const int64_t n0 = s->n;
-    const int F = s->sh_dim;
-    if (st) {
-        memset(st, 0, sizeof(*st));
-        st->n_input = n0;
-    }
-    const int64_t launches0 = c->launches;
-    c->fp64_edges = 0;
-    c->floor_hits = 0;
-    if (n0 <= 0) return;
-    // pre-filter flags (Algorithm 1) and canonical ids of the survivors
-    int32_t *keep = ws<int32_t>(c->b_role, n0 + 1);
-    int64_t nf;
-    const unsigned g0 = grid_stride_blocks(c, n0, 256, 8);
-    if (c->prm.prefilter) {
-        nf = prefilter_flags(c, s->opacity_logit, n0, c->prm.tau, keep);
-    } else {
-        launch(c, "fill_ones", dim3(g0), dim3(256), 0, k_fill_ones, keep, n0);
-        scan_i32(c, keep, ws<int32_t>(c->b_pos, n0 + 1), n0);
-        nf = n0;
-    }
-    int32_t *pos = (int32_t *)c->b_pos.p;
-    if (st) st->n_filtered = nf;
-    // Morton order of the survivors: the working arrays stay in this order;
-    // canonical ids ride along for every tie-break
-    float *frame = ws<float>(c->b_frame, 8);
-    morton_frame(c, s->xyz, n0, frame);
-    check_finite_frame(c, frame);
-    uint32_t *keys = ws<uint32_t>(c->b_codes, n0), *order = ws<uint32_t>(c->b_vals, n0);
-    uint32_t *k2 = ws<uint32_t>(c->b_codes2, n0), *v2 = ws<uint32_t>(c->b_vals2, n0);
-    morton_keys(c, s->xyz, n0, frame, keys, order);
-    launch(c, "mark_dropped", dim3(g0), dim3(256), 0, k_mark_dropped, keys, (const int32_t *)keep, n0);
-    radix_sort_u32(c, keys, order, k2, v2, n0, 31);
-    SplatView A = scratch_view(c, c->b_sA, nf, F), B = scratch_view(c, c->b_sB, nf, F);
-    int32_t *cidA = ws<int32_t>(c->b_cid, nf + 1), *cidB = ws<int32_t>(c->b_cid2, nf + 1);
-    A.n = nf;
-    gather_rows(c, view_of(s), order, A);
-    launch(c, "gather_cid", dim3(grid_stride_blocks(c, nf, 256, 8)), dim3(256), 0, k_gather_cid,
-           (const uint32_t *)order, (const int32_t *)pos, nf, cidA);
-    int64_t n = nf;
-    int pass = 0;
-    int64_t fp64_total = 0;
-    while (n > target && n > 1 && pass < c->prm.max_passes) {
-        GraphDev &g = c->g;
-        g = GraphDev{};
-        g.n = n;
-        g.k_eff = k_eff_of(n, c->prm.k);
-        g.cid = cidA;
-        // exact Morton order of this pass (the working order is close to it)
-        uint32_t *pk = ws<uint32_t>(c->b_codes, n), *pv = ws<uint32_t>(c->b_vals, n);
-        uint32_t *pk2 = ws<uint32_t>(c->b_codes2, n), *pv2 = ws<uint32_t>(c->b_vals2, n);
-        morton_keys(c, A.xyz, n, frame, pk, pv);
-        radix_sort_u32(c, pk, pv, pk2, pv2, n, 30);
-        float4 *pts = ws<float4>(c->b_pts, n);
-        gather_points(c, A.xyz, cidA, pv, n, pts);
-        int32_t *nbr = ws<int32_t>(c->b_nbr, n * g.k_eff);
-        knn_search(c, KnnInput{pts, pk, pv, frame, n, 0, cidA}, g.k_eff, nbr);
-        build_edges(c, nbr, g);
-        edge_costs(c, A, g, (uint32_t)pass, false, nullptr);
-        int32_t *partner = ws<int32_t>(c->b_partner, n);
-        int64_t np = select_pairs(c, g, n - target, partner);
-        fp64_total += (int64_t)c->h_pin[1];  // written by edge_costs, synced since
-        if (st && pass < NGS_STATS_MAX_PASSES) {
-            st->pass_n[pass] = n;
-            st->pass_edges[pass] = g.n_edges;
-            st->pass_pairs[pass] = np;
-            st->matching_rounds += c->rounds;
-        }
-        pass++;
-        if (np == 0) break;
-        int32_t *role = ws<int32_t>(c->b_role, n);
-        partner_to_role(c, partner, cidA, n, role);
-        int64_t nn = merge_compact(c, A, role, B, cidA, cidB);
-        std::swap(A, B);
-        std::swap(cidA, cidB);
-        n = nn;
-        A.n = n;
-    }
-    // back to canonical order, in the caller's arrays
-    SplatView dst = view_of(s);
-    scatter_rows(c, A, cidA, dst);
-    sync_stream(c);
-    s->n = n;
-    c->g_valid = false;
-    // keep buffer identities consistent for the next call (A/B may have swapped)
-    if (A.xyz != (float *)c->b_sA[0].p) {
-        std::swap(c->b_sA, c->b_sB);
-    }
-    if (cidA != (int32_t *)c->b_cid.p) std::swap(c->b_cid, c->b_cid2);
-    if (st) {
-        st->n_output = n;
-        st->passes = pass;
-        st->fp64_cost_edges = fp64_total;
-        st->eig_floor_hits = c->floor_hits;
-        st->gpu_launches = c->launches - launches0;
-    }
-}
-
 extern "C" int ngs_simplify(ngs_ctx *c, ngs_splats *s, int64_t target, ngs_stats *st) {
     if (!c) return NGS_ERR_INVALID_ARG;
     API_BEGIN
     check_splats(s, "ngs_simplify");
     if (target < 1) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_simplify: target_count < 1");
-    simplify_device(c, s, target, st);
+    engine_simplify(c, s, &target, 1, st);
+    API_END
+}
+
+extern "C" int ngs_batch_simplify(ngs_ctx *c, ngs_splats *scenes, const int64_t *targets,
+                                  int32_t nscenes, ngs_stats *st) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    if (nscenes < 0 || nscenes > NGS_MAX_SCENES)
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_batch_simplify: nscenes=%d outside [0, %d]",
+                 (int)nscenes, NGS_MAX_SCENES);
+    if (nscenes > 0 && (!scenes || !targets))
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_batch_simplify: NULL scenes or targets");
+    int64_t total = 0;
+    for (int s = 0; s < nscenes; s++) {
+        check_splats(&scenes[s], "ngs_batch_simplify");
+        if (scenes[s].sh_dim != scenes[0].sh_dim)
+            NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_batch_simplify: scene %d sh_dim %d != %d", s,
+                     scenes[s].sh_dim, scenes[0].sh_dim);
+        if (targets[s] < 1)
+            NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_batch_simplify: scene %d target_count < 1", s);
+        total += scenes[s].n;
+    }
+    if (total > NGS_MAX_N)
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_batch_simplify: %lld splats in total, above %lld",
+                 (long long)total, (long long)NGS_MAX_N);
+    // scenes whose target leaves room for a full neighbour list share one
+    // engine run; the others (target <= k) run alone, one after another
+    std::vector<ngs_splats> big;
+    std::vector<int64_t> big_t;
+    std::vector<int> big_idx;
+    ngs_stats acc, one;
+    memset(&acc, 0, sizeof(acc));
+    const int ke = k_eff_of(INT64_MAX, c->prm.k);
+    const int64_t l0 = c->launches;
+    auto add = [&](const ngs_stats &x) {
+        acc.n_input += x.n_input;
+        acc.n_filtered += x.n_filtered;
+        acc.n_output += x.n_output;
+        for (int p = 0; p < NGS_STATS_MAX_PASSES; p++) {
+            acc.pass_n[p] += x.pass_n[p];
+            acc.pass_edges[p] += x.pass_edges[p];
+            acc.pass_pairs[p] += x.pass_pairs[p];
+        }
+        acc.passes = acc.passes > x.passes ? acc.passes : x.passes;
+        acc.matching_rounds += x.matching_rounds;
+        acc.fp64_cost_edges += x.fp64_cost_edges;
+        acc.eig_floor_hits += x.eig_floor_hits;
+    };
+    for (int s = 0; s < nscenes; s++) {
+        if (targets[s] > ke) {
+            big.push_back(scenes[s]);
+            big_t.push_back(targets[s]);
+            big_idx.push_back(s);
+        } else {
+            engine_simplify(c, &scenes[s], &targets[s], 1, &one);
+            add(one);
+        }
+    }
+    if (!big.empty()) {
+        engine_simplify(c, big.data(), big_t.data(), (int)big.size(), &one);
+        add(one);
+        for (size_t i = 0; i < big.size(); i++) scenes[big_idx[i]].n = big[i].n;
+    }
+    acc.gpu_launches = c->launches - l0;
+    if (st) *st = acc;
     API_END
 }
 
@@ -563,7 +509,7 @@ extern "C" int ngs_simplify_host(ngs_ctx *c, ngs_splats *h, int64_t target, ngs_
     float *dp[5] = {d.xyz, d.log_scale, d.rot, d.opacity_logit, d.sh};
     for (int k = 0; k < 5; k++)
         NGS_CHECK_CUDA(cudaMemcpyAsync(dp[k], hp[k], sz[k] * n, cudaMemcpyHostToDevice, c->st));
-    simplify_device(c, &d, target, st);
+    engine_simplify(c, &d, &target, 1, st);
     for (int k = 0; k < 5; k++)
         NGS_CHECK_CUDA(cudaMemcpyAsync(hp[k], dp[k], sz[k] * d.n, cudaMemcpyDeviceToHost, c->st));
     sync_stream(c);

@@ -9,7 +9,10 @@
 
 #include "ngs.h"
 
-#define NGS_MAX_N ((int64_t)1 << 25)  // per-scene splat limit (int32 edge offsets)
+// rows of one call (all scenes of a batch together); n * k_eff must also stay
+// at or below NGS_MAX_SLOTS, so that slot indices v * k_eff + j fit int32
+#define NGS_MAX_N ((int64_t)1 << 26)
+#define NGS_MAX_SLOTS ((int64_t)1 << 30)
 #define NGS_LEAF 32                     // kNN tree leaf = one warp of points
 
 // ---------------------------------------------------------------- errors
@@ -102,8 +105,10 @@ struct ngs_ctx {
     DevBuf b_mate, b_cand, b_candkey, b_counts, b_sel, b_role, b_keep, b_pos, b_flag;
     DevBuf b_scan_part, b_status, b_misc, b_cid, b_cid2, b_cflag, b_cscan;
     DevBuf b_sA[5], b_sB[5];     // ping-pong splat arrays
-    DevBuf b_pairs, b_partner, b_nbr2, b_lexrec, b_sel2, b_cflag2;
+    DevBuf b_pairs, b_partner, b_nbr2, b_lexrec, b_sel2, b_cflag2, b_knnsc;
     DevBuf b_host_dev[5];        // device staging for ngs_simplify_host
+    DevBuf b_sC[5];              // third splat array set (several scenes at once)
+    DevBuf b_eng[32];            // per-scene tables and scratch of the multi-scene engine
 
     // pinned host scratch
     int64_t *h_pin = nullptr;
@@ -176,9 +181,13 @@ void radix_select_u32(ngs_ctx *c, const uint32_t *keys, int64_t n, int64_t k, ui
 void radix_select_u64(ngs_ctx *c, const uint64_t *keys, int64_t n, int64_t k, uint64_t *d_out);
 
 // ---------------------------------------------------------------- graph (k_knn.cu, k_graph.cu)
-// Input of the kNN search: points sorted by 30-bit Morton code in `frame`.
+// Input of the kNN search: points grouped by scene and sorted by 30-bit
+// Morton code in their scene's frame.
 //   pts[p]  = (x, y, z, canonical id bits) at sorted position p
-//   scode[p] = Morton code (ascending), sidx[p] = internal row of position p
+//   scode[p] = Morton code (ascending within a scene), sidx[p] = internal row
+//   ssid[p] = scene of position p (nullptr: one scene)
+//   frames  = nscenes x 8 floats (lo.xyz, cells per unit, ...), device
+//   scene_n = points per scene (host, nscenes entries)
 //   out_by_cid = 1: canonical id == internal row; 0: rows are internal
 //   indices and neighbours are translated from canonical ids via cid[]
 //   (cid of each internal row).
@@ -186,11 +195,30 @@ struct KnnInput {
     const float4 *pts;
     const uint32_t *scode;
     const uint32_t *sidx;
-    const float *frame;
+    const int32_t *ssid;
+    const float *frames;
+    const int64_t *scene_n;
+    int nscenes;
     int64_t n;
     int out_by_cid;
     const int32_t *cid;
 };
+int knn_table_level(int64_t n);
+// neighbours per splat in a pass over n splats: min(max(1, k), n - 1)
+inline int k_eff_of(int64_t n, int k) {
+    int ke = k < 1 ? 1 : k;
+    if ((int64_t)ke > n - 1) ke = (int)(n - 1);
+    return ke;
+}
+inline void check_slots(int64_t n, int k, const char *fn) {
+    if (n >= 2 && n * (int64_t)k_eff_of(n, k) > NGS_MAX_SLOTS)
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "%s: n=%lld times k_eff=%d is above %lld", fn, (long long)n,
+                 k_eff_of(n, k), (long long)NGS_MAX_SLOTS);
+}
+// Algorithm 1 over S scenes at once (scenes[s] in place, targets[s] >= 1);
+// S == 1 is ngs_simplify.  For S > 1 every target must exceed
+// min(max(1, k), NGS_MAX_K) so that all scenes share one k_eff.
+void engine_simplify(ngs_ctx *c, ngs_splats *scenes, const int64_t *targets, int S, ngs_stats *st);
 // Compute the Morton frame (lo.xyz, 1/side) of n centres into frame[4].
 void morton_frame(ngs_ctx *c, const float *xyz, int64_t n, float *frame);
 // Morton keys of n centres in `frame`, with vals = 0..n-1 (or given).
@@ -220,6 +248,15 @@ void costs_to_slots(ngs_ctx *c, GraphDev &g, const float *cost_lex);
 // Greedy matching under (cost, canonical pair) capped to max_pairs.  Writes
 // partner[v] (selected partner or -1) and returns the pair count (host).
 int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *partner);
+// Locally-dominant rounds only: mate[] in c->b_mate, edge cost keys in
+// c->b_candkey; returns the number of matched pairs.
+int64_t match_rounds(ngs_ctx *c, const GraphDev &g);
+// keys[v] = (cost bits << 32 | lo cid) at the lower-cid endpoint of each
+// matched pair, UINT64_MAX elsewhere.
+void pair_keys(ngs_ctx *c, const GraphDev &g, uint64_t *keys);
+// partner[v] from mate[] with per-scene thresholds thr[sid[v]] (capped = 0: none).
+void apply_cap(ngs_ctx *c, const GraphDev &g, const int32_t *sid, const uint64_t *thr,
+               int capped, int32_t *partner);
 // pairs_out (2*count) sorted by lo from partner[]; returns count.
 int64_t partner_to_pairs(ngs_ctx *c, const int32_t *partner, const int32_t *cid, int64_t n,
                          int32_t *pairs_out);

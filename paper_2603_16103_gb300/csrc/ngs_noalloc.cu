@@ -37,8 +37,9 @@ constexpr size_t kKeys = align256(4 * kMaxN);
 constexpr size_t kHist = align256(4 * (256 * kTiles + 1));
 constexpr size_t kPart = align256(4 * (kCells / 2048 + 2));
 constexpr size_t kPts = align256(16 * kMaxN);
-constexpr size_t kTable = align256(4 * (kCells + 1));
-constexpr size_t kScratchBytes = kAcc + kFrame + 4 * kKeys + kHist + kPart + kPts + kTable;
+constexpr size_t kTable = align256(4 * (kCells + 2));
+constexpr size_t kKnnSc = align256(16 * 2 + 256);
+constexpr size_t kScratchBytes = kAcc + kFrame + 4 * kKeys + kHist + kPart + kPts + kTable + kKnnSc;
 
 __device__ __align__(256) unsigned char g_knn_scratch[kScratchBytes];
 
@@ -112,6 +113,7 @@ extern "C" int ngs_knn_noalloc(const float *xyz, int64_t n, int32_t k, int32_t *
     bind(c.b_scan_part, cur, kPart);
     bind(c.b_pts, cur, kPts);
     bind(c.b_nodes, cur, kTable);
+    bind(c.b_knnsc, cur, kKnnSc);
     int rc = NGS_OK;
     try {
         const int ke = (int)(k < n - 1 ? k : n - 1);
@@ -126,7 +128,8 @@ extern "C" int ngs_knn_noalloc(const float *xyz, int64_t n, int32_t k, int32_t *
         radix_sort_u32(&c, keys, vals, (uint32_t *)c.b_codes2.p, (uint32_t *)c.b_vals2.p, n, 30);
         float4 *pts = (float4 *)c.b_pts.p;
         gather_points(&c, xyz, nullptr, vals, n, pts);
-        knn_search(&c, KnnInput{pts, keys, vals, frame, n, 1, nullptr}, ke, nbr);
+        const int64_t sn = n;
+        knn_search(&c, KnnInput{pts, keys, vals, nullptr, frame, &sn, 1, n, 1, nullptr}, ke, nbr);
     } catch (const NgsError &err) {
         rc = err.code;
     } catch (...) {
@@ -135,7 +138,7 @@ extern "C" int ngs_knn_noalloc(const float *xyz, int64_t n, int32_t k, int32_t *
     }
     // the slices belong to the static array: detach them before the stack ctx goes away
     DevBuf *bound[] = {&c.b_bbox, &c.b_frame, &c.b_codes, &c.b_vals, &c.b_codes2,
-                       &c.b_vals2, &c.b_hist, &c.b_scan_part, &c.b_pts, &c.b_nodes};
+                       &c.b_vals2, &c.b_hist, &c.b_scan_part, &c.b_pts, &c.b_nodes, &c.b_knnsc};
     for (DevBuf *b : bound) *b = DevBuf{};
     return rc;
 }
