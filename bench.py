@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and serving measurements")
+    ap.add_argument("--form-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -178,6 +181,66 @@ def cpu_baseline(args):
     return {"value": sample.n / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
             "sample": f"one oracle simplify of a {sample.n}-splat scene of the same recipe "
                       f"-> {args.ratio:g} ({dt:.1f} s)"}
+
+
+def _timed(torch, stream, fn):
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    out = fn()
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1), out
+
+
+def batched_form(B, torch, synth, args):
+    """64 scenes (sizes log-uniform on [50k, 2M], ratios from {0.5, 0.25, 0.1}):
+    one ngs_batch_simplify call vs ngs_simplify per scene back to back."""
+    specs = synth.batch_specs()
+    pristine = [B.DeviceSplats(*synth.patches_cube_device(n, seed)) for n, r, seed in specs]
+    targets = [max(int(math.ceil(r * n)), 1) for n, r, seed in specs]
+    work = [p.clone() for p in pristine]
+    total = sum(p.n for p in pristine)
+
+    def restore():
+        for w, p in zip(work, pristine):
+            for a, b in zip(w.tensors(), p.tensors()):
+                a.copy_(b)
+            w.n = p.n
+
+    ctx = B.Context()
+    stream = torch.cuda.current_stream()
+    res = {}
+    outs = {}
+    for mode in ("batched", "sequential"):
+        if mode == "batched":
+            run = lambda: ctx.batch_simplify(work, targets)["gpu_launches"]
+        else:
+            run = lambda: sum(ctx.simplify(w, t)["gpu_launches"] for w, t in zip(work, targets))
+        times, launches = [], 0
+        for it in range(1 + args.form_steps):
+            restore()
+            torch.cuda.synchronize()
+            ms, nl = _timed(torch, stream, run)
+            if it >= 1:
+                times.append(ms)
+                launches += nl
+        outs[mode] = [tuple(a[:w.n].clone() for a in w.tensors()) for w in work]
+        ms = statistics.median(times)
+        res[mode] = {"value": total / (ms / 1e3), "unit": UNIT, "ms": ms,
+                     "gpu_launches": launches / args.form_steps}
+    identical = all(all(torch.equal(a, b) for a, b in zip(x, y))
+                    for x, y in zip(outs["batched"], outs["sequential"]))
+    ctx.close()
+    del work, pristine, outs
+    torch.cuda.empty_cache()
+    return {"workload": f"{len(specs)} patch scenes, {total} splats in total, sizes "
+                        "log-uniform on [50k, 2M], ratios from {0.5, 0.25, 0.1}, "
+                        "device-generated (batch_specs)",
+            "scenes": len(specs), "splats": total, "batched": res["batched"],
+            "sequential": res["sequential"],
+            "speedup": res["sequential"]["ms"] / res["batched"]["ms"],
+            "identical_outputs": identical, "steps": args.form_steps}
 
 
 def main():
@@ -304,6 +367,10 @@ def main():
         e2e = {"value": ws * n0 * reps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    forms = {}
+    if not args.no_forms:
+        forms["batched"] = batched_form(B, torch, synth, args)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(args)
@@ -324,6 +391,7 @@ def main():
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
+        out.update(forms)
         print(json.dumps(out), flush=True)
     ctx.close()
     if ws > 1:

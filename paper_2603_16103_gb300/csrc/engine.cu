@@ -292,10 +292,11 @@ __device__ __forceinline__ uint32_t spread10e(uint32_t v) {
 }
 
 // 30-bit Morton code of each row in its scene's frame (same quantisation as
-// the single-frame kernel)
+// the single-frame kernel); with `keep`, dropped rows get bit 30 so that
+// they sort after every kept row
 __global__ void k_morton_rows(const float *__restrict__ xyz, const int32_t *__restrict__ sid,
-                              int64_t n, const float *__restrict__ frames, uint32_t *keys,
-                              uint32_t *vals) {
+                              int64_t n, const float *__restrict__ frames,
+                              const int32_t *__restrict__ keep, uint32_t *keys, uint32_t *vals) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float *f = frames + 8 * (sid ? sid[i] : 0);
@@ -307,7 +308,8 @@ __global__ void k_morton_rows(const float *__restrict__ xyz, const int32_t *__re
             const float v = q[a];
             cc[a] = (v >= 1023.0f) ? 1023u : (v > 0.0f ? (uint32_t)v : 0u);
         }
-        keys[i] = spread10e(cc[0]) | (spread10e(cc[1]) << 1) | (spread10e(cc[2]) << 2);
+        keys[i] = spread10e(cc[0]) | (spread10e(cc[1]) << 1) | (spread10e(cc[2]) << 2) |
+                  (keep && !keep[i] ? 1u << 30 : 0u);
         vals[i] = (uint32_t)i;
     }
 }
@@ -523,13 +525,22 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     {
         uint32_t *keys = ws<uint32_t>(c->b_codes, N0), *order = ws<uint32_t>(c->b_vals, N0);
         uint32_t *k2 = ws<uint32_t>(c->b_codes2, N0), *v2 = ws<uint32_t>(c->b_vals2, N0);
-        launch(c, "morton", dim3(g0), dim3(256), 0, k_morton_rows, IN.xyz,
-               (const int32_t *)sid_in, N0, (const float *)frames, keys, order);
-        radix_sort_u32(c, keys, order, k2, v2, N0, 30);
-        // stable by scene; pre-filtered rows (scene S) last
-        launch(c, "gather_sid", dim3(g0), dim3(256), 0, k_gather_sid, (const int32_t *)sid_in,
-               (const uint32_t *)order, N0, S, (const int32_t *)keep, keys);
-        radix_sort_u32(c, keys, order, k2, v2, N0, bits_for(S));
+        if (!multi) {  // (dropped, code) in one 31-bit sort
+            launch(c, "morton", dim3(g0), dim3(256), 0, k_morton_rows, IN.xyz,
+                   (const int32_t *)nullptr, N0, (const float *)frames, (const int32_t *)keep,
+                   keys, order);
+            radix_sort_u32(c, keys, order, k2, v2, N0, 31);
+        } else {
+            launch(c, "morton", dim3(g0), dim3(256), 0, k_morton_rows, IN.xyz,
+                   (const int32_t *)sid_in, N0, (const float *)frames, (const int32_t *)nullptr,
+                   keys, order);
+            radix_sort_u32(c, keys, order, k2, v2, N0, 30);
+            // stable by scene; pre-filtered rows (scene S) last
+            launch(c, "gather_sid", dim3(g0), dim3(256), 0, k_gather_sid,
+                   (const int32_t *)sid_in, (const uint32_t *)order, N0, S,
+                   (const int32_t *)keep, keys);
+            radix_sort_u32(c, keys, order, k2, v2, N0, bits_for(S));
+        }
         A = scratch(c, c->b_sA, nf, F);
         B = multi ? scratch(c, c->b_sC, nf, F) : scratch(c, c->b_sB, nf, F);
         gather_rows(c, IN, order, A);
@@ -630,7 +641,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         int32_t *ssid = nullptr;
         launch(c, "morton", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0, k_morton_rows,
                (const float *)A.xyz, multi ? (const int32_t *)sidA : (const int32_t *)nullptr, nA,
-               (const float *)frames, pk, pv);
+               (const float *)frames, (const int32_t *)nullptr, pk, pv);
         if (multi) {
             NGS_CHECK_CUDA(cudaMemcpyAsync(code_row, pk, 4 * nA, cudaMemcpyDeviceToDevice, c->st));
             radix_sort_u32(c, pk, pv, pk2, pv2, nA, 30);

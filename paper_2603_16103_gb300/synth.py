@@ -184,3 +184,95 @@ def workload(name: str) -> Scene:
         return patches_cube(200_000, seed=3, frac_degenerate=0.05, frac_duplicate=0.01)
     raise KeyError(name)
 
+
+
+# Device-side generation ------------------------------------------------------
+#
+# The batched and serving workloads hold tens of millions of splats; drawing
+# them with numpy takes about 1.7 s per million on one core.  These functions
+# follow the patches_cube recipe above exactly (same distributions, same
+# per-patch parameters, which are drawn on the host from default_rng(seed))
+# but draw the per-splat values on the GPU with a torch generator seeded from
+# the same seed, so the values differ from patches_cube(n, seed) while the
+# distribution is the same.
+
+def patches_cube_device(n: int, seed: int, device="cuda", n_patches: int = 64,
+                        cube: float = 20.0, frac_degenerate: float = 0.0,
+                        frac_duplicate: float = 0.0, sh_dim: int = SH_DIM):
+    """patches_cube drawn on `device`; returns a tuple of 5 contiguous float32
+    tensors (xyz, log_scale, rot, logit, sh)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    kinds = np.arange(n_patches) % 2
+    radius = rng.uniform(0.5, 2.5, size=n_patches)
+    side = rng.uniform(1.0, 5.0, size=n_patches)
+    centres = rng.uniform(0.1 * cube, 0.9 * cube, size=(n_patches, 3))
+    mult = np.exp(rng.uniform(0.0, math.log(10.0), size=n_patches))
+    area = np.where(kinds == 0, 4.0 * math.pi * radius ** 2, side ** 2)
+    counts = _split_counts(area * mult, n)
+    frames = [_orthonormal_frame(rng) for _ in range(n_patches)]
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 7919 + 17)
+    f32 = dict(dtype=torch.float32, device=device)
+    pid = torch.repeat_interleave(torch.arange(n_patches, device=device),
+                                  torch.as_tensor(counts, device=device))
+    c = torch.as_tensor(centres, **f32)[pid]
+    sph = torch.as_tensor(kinds == 0, device=device)[pid].unsqueeze(1)
+    # spheres: direction on S^2 times radius + jitter
+    d = torch.randn((n, 3), generator=g, **f32)
+    d = d / d.norm(dim=1, keepdim=True)
+    r = torch.as_tensor(radius, **f32)[pid].unsqueeze(1) + 0.01 * torch.randn((n, 1), generator=g, **f32)
+    p_s = c + d * r
+    # planes: uniform square in the patch frame + normal jitter
+    nrm = torch.as_tensor(np.stack([f[0] for f in frames]), **f32)[pid]
+    e1 = torch.as_tensor(np.stack([f[1] for f in frames]), **f32)[pid]
+    e2 = torch.as_tensor(np.stack([f[2] for f in frames]), **f32)[pid]
+    half = 0.5 * torch.as_tensor(side, **f32)[pid].unsqueeze(1)
+    a = (torch.rand((n, 1), generator=g, **f32) * 2 - 1) * half
+    b = (torch.rand((n, 1), generator=g, **f32) * 2 - 1) * half
+    h = 0.01 * torch.randn((n, 1), generator=g, **f32)
+    p_p = c + a * e1 + b * e2 + h * nrm
+    xyz = torch.where(sph, p_s, p_p)
+    del p_s, p_p, d, nrm, e1, e2
+    log_scale = -4.5 + 0.5 * torch.randn((n, 3), generator=g, **f32)
+    q = torch.randn((n, 4), generator=g, **f32)
+    rot = q / q.norm(dim=1, keepdim=True)
+    logit = 1.5 * torch.randn((n,), generator=g, **f32)
+    sh = 0.05 * torch.randn((n, sh_dim), generator=g, **f32)
+    ndc = min(3, sh_dim)
+    sh[:, :ndc] *= 10.0  # DC: N(0, 0.5)
+    if frac_degenerate > 0:
+        m = int(round(frac_degenerate * n))
+        idx = torch.randperm(n, generator=g, device=device)[:m]
+        ax = torch.randint(0, 3, (m,), generator=g, device=device)
+        log_scale[idx, ax] = -12.0 + 3.0 * torch.rand((m,), generator=g, **f32)
+    if frac_duplicate > 0:
+        m = int(round(frac_duplicate * n))
+        dst = torch.randperm(n, generator=g, device=device)[:m]
+        src = torch.randint(0, n, (m,), generator=g, device=device)
+        xyz[dst] = xyz[src]
+    perm = torch.randperm(n, generator=g, device=device)
+    return tuple(t[perm].contiguous() for t in (xyz, log_scale, rot, logit, sh))
+
+
+def batch_specs(n_scenes: int = 64, lo: int = 50_000, hi: int = 2_000_000,
+                ratios=(0.5, 0.25, 0.1), seed: int = 1000):
+    """Scene sizes (log-uniform on [lo, hi]), target ratios (uniform over
+    `ratios`) and seeds (seed, seed+1, ...) of the batched workload."""
+    rng = np.random.default_rng(seed - 1)
+    sizes = np.exp(rng.uniform(math.log(lo), math.log(hi), n_scenes)).astype(np.int64)
+    rs = np.asarray(ratios)[rng.integers(0, len(ratios), n_scenes)]
+    return [(int(n), float(r), seed + i) for i, (n, r) in enumerate(zip(sizes, rs))]
+
+
+def serve_specs(n_jobs: int = 200, rate: float = 20.0, lo: int = 20_000, hi: int = 6_000_000,
+                ratios=(0.5, 0.1, 0.01), seed: int = 2000):
+    """Poisson request stream: (arrival time s, size, ratio, scene seed) per
+    job; sizes log-uniform on [lo, hi], ratios uniform over `ratios`."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
+    t -= t[0]
+    sizes = np.exp(rng.uniform(math.log(lo), math.log(hi), n_jobs)).astype(np.int64)
+    rs = np.asarray(ratios)[rng.integers(0, len(ratios), n_jobs)]
+    return [(float(a), int(n), float(r), seed + 1 + i)
+            for i, (a, n, r) in enumerate(zip(t, sizes, rs))]
