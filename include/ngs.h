@@ -269,6 +269,104 @@ int ngs_profile_get(ngs_ctx *ctx, int i, const char **name, int64_t *launches, d
 int ngs_profile_reset(ngs_ctx *ctx);
 /* Total kernels launched by the ctx since creation (all calls). */
 int64_t ngs_launch_count(ngs_ctx *ctx);
+/* Device workspace the ctx currently holds, in bytes (grows with the largest
+ * input seen; released by ngs_destroy). */
+int64_t ngs_workspace_bytes(ngs_ctx *ctx);
+/* Give the ctx's device workspace back to the library's memory pool (the
+ * next call grows it again).  Invalidates the graph of ngs_build_graph.
+ * Synchronises the ctx stream.  Errors: CUDA. */
+int ngs_release_workspace(ngs_ctx *ctx);
+/* Move the ctx to another CUDA stream (NULL = legacy default stream) after
+ * the work queued on its current stream has finished.  Errors: CUDA. */
+int ngs_set_stream(ngs_ctx *ctx, void *stream);
+
+/* ---- serving form ----
+ *
+ * A request loop for simplification jobs of different sizes and targets.
+ * The server owns `slots` workers; each has its own ctx, CUDA stream and
+ * host thread, so the passes of jobs on different slots overlap on the GPU.
+ * A free worker takes the oldest queued job once its admission estimate
+ * (bytes_per_splat * n) fits the HBM budget next to what the other workers
+ * hold; with group_small, it also takes later queued jobs of at most
+ * small_rows splats (up to group_rows in total) and runs them together as
+ * one ngs_batch_simplify, so jobs that arrive while others are on the GPU
+ * join the next free slot's batch.  Every job's result is bit-identical to
+ * ngs_simplify on it alone (the batched engine guarantees this per scene).
+ * Large runs (priority_rows) take a high-priority stream so that the jobs
+ * that set the latency tail are not slowed by small concurrent ones, which
+ * fill the SMs the large run leaves idle.
+ * slots = 1 without grouping is plain one-at-a-time processing.
+ * Job splats are device arrays owned by the caller, simplified in place; they
+ * must stay valid and untouched until the job has finished.
+ * dry_run_ns_per_splat > 0 replaces the GPU work by a host sleep of that many
+ * nanoseconds per splat (no CUDA call at all): the scheduler alone, for
+ * tests without a GPU. */
+typedef struct ngs_server ngs_server;
+
+typedef struct {
+    int32_t slots;                /* concurrent workers (1..64), default 4      */
+    int32_t group_small;          /* batch small queued jobs together (0/1), 1  */
+    int64_t hbm_budget_bytes;     /* admission budget, default 150e9            */
+    int64_t bytes_per_splat;      /* admission estimate per input splat, 1536   */
+    int64_t small_rows;           /* jobs up to this size may be grouped, 1e6  */
+    int64_t group_rows;           /* rows of one group at most, 4e6             */
+    double dry_run_ns_per_splat;  /* > 0: host-only scheduler run, default 0   */
+    int64_t priority_rows;        /* runs of at least this many rows go on a
+                                     high-priority stream, smaller ones on a
+                                     low-priority one (0: one priority), 1e6  */
+} ngs_server_config;
+
+/* Status of a job (ngs_job_info.status). */
+#define NGS_JOB_QUEUED  1
+#define NGS_JOB_RUNNING 2
+#define NGS_JOB_DONE    0
+/* negative: the job failed with that NGS_ERR_* code */
+
+typedef struct {
+    int32_t status;
+    int32_t slot;          /* worker that ran it (-1 while queued)              */
+    int64_t group;         /* id of the run it was part of (jobs of one batch share it) */
+    int32_t group_size;    /* jobs in that run                                  */
+    int64_t n_in, target, n_out;
+    double submit_s, start_s, finish_s;  /* seconds on the server's clock       */
+} ngs_job_info;
+
+typedef struct {
+    int64_t submitted, finished, failed, queued, running, groups;
+    int64_t reserved_bytes;       /* admission estimates of the running jobs    */
+    int64_t peak_reserved_bytes;
+    int64_t workspace_bytes;      /* device workspace the workers hold now      */
+    int64_t peak_workspace_bytes;
+    int64_t gpu_launches;         /* kernels launched by all workers            */
+} ngs_server_stats;
+
+void ngs_server_default_config(ngs_server_config *cfg);
+/* params: as for ngs_create (NULL = defaults); cfg NULL = defaults.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int ngs_server_create(ngs_server **srv, const ngs_params *params, const ngs_server_config *cfg);
+/* Stops accepting jobs, lets queued and running jobs finish, joins the
+ * workers and frees everything. */
+int ngs_server_destroy(ngs_server *srv);
+/* Queue a job (host descriptor of device splats, copied; target >= 1).
+ * A job whose estimate exceeds the whole budget fails at once with BUDGET.
+ * Errors: INVALID_ARG, BUDGET, STATE (server stopping). */
+int ngs_serve_submit(ngs_server *srv, const ngs_splats *job, int64_t target, uint64_t *job_id);
+/* Non-blocking: *done = 1 when the job has finished (or failed), else 0;
+ * *n_out (may be NULL) = final count.  Returns the job's error code if it
+ * failed.  Errors: INVALID_ARG (unknown id). */
+int ngs_serve_poll(ngs_server *srv, uint64_t job_id, int *done, int64_t *n_out);
+/* Block until the job finishes or timeout_s passes (TIMEOUT). */
+int ngs_serve_wait(ngs_server *srv, uint64_t job_id, double timeout_s, int64_t *n_out);
+int ngs_serve_info(ngs_server *srv, uint64_t job_id, ngs_job_info *info);
+int ngs_server_get_stats(ngs_server *srv, ngs_server_stats *stats);
+/* Seconds on the server's clock (steady, 0 at creation). */
+double ngs_server_clock(ngs_server *srv);
+/* Replay a request stream: job i is submitted at arrival_s[i] seconds after
+ * the call starts (by a host thread that sleeps until then), then the call
+ * waits for all of them.  job_ids (may be NULL) receives the ids.  Returns
+ * the first submit error, or OK.  Latency of job i = finish_s - submit_s. */
+int ngs_serve_replay(ngs_server *srv, const ngs_splats *jobs, const int64_t *targets,
+                     const double *arrival_s, int32_t n_jobs, uint64_t *job_ids);
 
 #ifdef __cplusplus
 }

@@ -76,6 +76,37 @@ class ngs_stats(ctypes.Structure):
                 "eig_floor_hits": self.eig_floor_hits, "gpu_launches": self.gpu_launches}
 
 
+class ngs_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("group_small", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("bytes_per_splat", ctypes.c_int64),
+                ("small_rows", ctypes.c_int64), ("group_rows", ctypes.c_int64),
+                ("dry_run_ns_per_splat", ctypes.c_double), ("priority_rows", ctypes.c_int64)]
+
+
+class ngs_job_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("group", ctypes.c_int64),
+                ("group_size", ctypes.c_int32), ("n_in", ctypes.c_int64),
+                ("target", ctypes.c_int64), ("n_out", ctypes.c_int64),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("finish_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ngs_server_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "submitted", "finished", "failed", "queued", "running", "groups", "reserved_bytes",
+        "peak_reserved_bytes", "workspace_bytes", "peak_workspace_bytes", "gpu_launches")]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+NGS_JOB_QUEUED = 1
+NGS_JOB_RUNNING = 2
+NGS_JOB_DONE = 0
+
 _P = ctypes.c_void_p
 _SIGS = {
     "ngs_default_params": (None, [ctypes.POINTER(ngs_params)]),
@@ -105,6 +136,26 @@ _SIGS = {
     "ngs_profile_reset": (ctypes.c_int, [_P]),
     "ngs_launch_count": (ctypes.c_int64, [_P]),
     "ngs_knn_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
+    "ngs_workspace_bytes": (ctypes.c_int64, [_P]),
+    "ngs_release_workspace": (ctypes.c_int, [_P]),
+    "ngs_set_stream": (ctypes.c_int, [_P, _P]),
+    "ngs_server_default_config": (None, [ctypes.POINTER(ngs_server_config)]),
+    "ngs_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ngs_params),
+                                         ctypes.POINTER(ngs_server_config)]),
+    "ngs_server_destroy": (ctypes.c_int, [_P]),
+    "ngs_serve_submit": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "ngs_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "ngs_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "ngs_serve_info": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ngs_job_info)]),
+    "ngs_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ngs_server_stats)]),
+    "ngs_server_clock": (ctypes.c_double, [_P]),
+    "ngs_serve_replay": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats),
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 
@@ -379,3 +430,80 @@ def _wrap_i32(ptr, count, device):
     if count <= 0 or not ptr:
         return torch.zeros(0, dtype=torch.int32, device=device)
     return torch.as_tensor(_DevArray(ptr, count), device=device).clone()
+
+
+# ---------------------------------------------------------------- serving form
+def ngs_server_default_config() -> ngs_server_config:
+    c = ngs_server_config()
+    load().ngs_server_default_config(ctypes.byref(c))
+    return c
+
+
+class Server:
+    """Request loop of the serving form (see ngs_server_create)."""
+
+    def __init__(self, params: ngs_params | None = None, **cfg):
+        c = ngs_server_default_config()
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        self.config = c
+        p = params or ngs_default_params()
+        h = _P()
+        _check(load().ngs_server_create(ctypes.byref(h), ctypes.byref(p), ctypes.byref(c)))
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            load().ngs_server_destroy(_P(self.handle))
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, s: ngs_splats, target: int) -> int:
+        jid = ctypes.c_uint64()
+        _check(load().ngs_serve_submit(_P(self.handle), ctypes.byref(s), target,
+                                       ctypes.byref(jid)))
+        return jid.value
+
+    def poll(self, jid: int):
+        done, n = ctypes.c_int(), ctypes.c_int64()
+        _check(load().ngs_serve_poll(_P(self.handle), jid, ctypes.byref(done), ctypes.byref(n)))
+        return bool(done.value), n.value
+
+    def wait(self, jid: int, timeout_s: float = 600.0) -> int:
+        n = ctypes.c_int64()
+        _check(load().ngs_serve_wait(_P(self.handle), jid, timeout_s, ctypes.byref(n)))
+        return n.value
+
+    def info(self, jid: int) -> dict:
+        i = ngs_job_info()
+        _check(load().ngs_serve_info(_P(self.handle), jid, ctypes.byref(i)))
+        return i.as_dict()
+
+    def stats(self) -> dict:
+        st = ngs_server_stats()
+        _check(load().ngs_server_get_stats(_P(self.handle), ctypes.byref(st)))
+        return st.as_dict()
+
+    def clock(self) -> float:
+        return load().ngs_server_clock(_P(self.handle))
+
+    def replay(self, jobs, targets, arrivals):
+        """jobs: list of ngs_splats; returns the job ids (raises on a submit error)."""
+        n = len(jobs)
+        arr = (ngs_splats * max(1, n))(*jobs)
+        tg = (ctypes.c_int64 * max(1, n))(*[int(t) for t in targets])
+        at = (ctypes.c_double * max(1, n))(*[float(a) for a in arrivals])
+        ids = (ctypes.c_uint64 * max(1, n))()
+        _check(load().ngs_serve_replay(_P(self.handle), arr, tg, at, n, ids))
+        return list(ids[:n])

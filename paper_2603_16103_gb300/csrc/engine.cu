@@ -388,11 +388,11 @@ int bits_for(int S) {
 
 SplatView scratch(ngs_ctx *c, DevBuf *b, int64_t n, int F) {
     SplatView v;
-    v.xyz = ws<float>(b[0], 3 * n);
-    v.ls = ws<float>(b[1], 3 * n);
-    v.rot = ws<float>(b[2], 4 * n);
-    v.logit = ws<float>(b[3], n);
-    v.sh = ws<float>(b[4], (int64_t)F * n);
+    v.xyz = ws<float>(c, b[0], 3 * n);
+    v.ls = ws<float>(c, b[1], 3 * n);
+    v.rot = ws<float>(c, b[2], 4 * n);
+    v.logit = ws<float>(c, b[3], n);
+    v.sh = ws<float>(c, b[4], (int64_t)F * n);
     v.n = n;
     v.F = F;
     return v;
@@ -402,7 +402,7 @@ SrcRows rows(const SplatView &v) { return SrcRows{v.xyz, v.ls, v.rot, v.logit, v
 
 template <class T>
 T *upload(ngs_ctx *c, DevBuf &b, const T *h, size_t count) {
-    T *d = (T *)ws_get(b, sizeof(T) * (count ? count : 1));
+    T *d = (T *)ws_get(c, b, sizeof(T) * (count ? count : 1));
     if (count)
         NGS_CHECK_CUDA(cudaMemcpyAsync(d, h, sizeof(T) * count, cudaMemcpyHostToDevice, c->st));
     return d;
@@ -454,29 +454,29 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
                dim3(256), 0, k_gather_scenes, dsrc, din0, S, N0, F, rows(IN));
     }
     const unsigned g0 = grid_stride_blocks(c, N0, 256, 8);
-    int32_t *sid_in = ws<int32_t>(c->b_eng[E_SID], N0);
+    int32_t *sid_in = ws<int32_t>(c, c->b_eng[E_SID], N0);
     if (multi) launch(c, "fill_sid", dim3(g0), dim3(256), 0, k_fill_sid, din0, S, N0, sid_in);
     else NGS_CHECK_CUDA(cudaMemsetAsync(sid_in, 0, 4 * N0, c->st));
 
     // ---- pre-filter (Algorithm 1), one median per scene
-    int32_t *keep = ws<int32_t>(c->b_role, N0 + 1);
-    int32_t *pos = ws<int32_t>(c->b_pos, N0 + 1);
+    int32_t *keep = ws<int32_t>(c, c->b_role, N0 + 1);
+    int32_t *pos = ws<int32_t>(c, c->b_pos, N0 + 1);
     if (!c->prm.prefilter) {
         launch(c, "fill_ones", dim3(g0), dim3(256), 0, k_fill_ones, keep, N0);
         scan_i32(c, keep, pos, N0);
     } else if (!multi) {
         prefilter_flags(c, IN.logit, N0, c->prm.tau, keep);  // leaves its scan in b_pos
     } else {
-        uint32_t *k0 = ws<uint32_t>(c->b_codes, N0), *kc = ws<uint32_t>(c->b_codes2, N0);
-        uint32_t *vals = ws<uint32_t>(c->b_vals, N0), *v2 = ws<uint32_t>(c->b_vals2, N0);
-        uint32_t *kt = ws<uint32_t>(c->b_eng[E_TMP], N0);
+        uint32_t *k0 = ws<uint32_t>(c, c->b_codes, N0), *kc = ws<uint32_t>(c, c->b_codes2, N0);
+        uint32_t *vals = ws<uint32_t>(c, c->b_vals, N0), *v2 = ws<uint32_t>(c, c->b_vals2, N0);
+        uint32_t *kt = ws<uint32_t>(c, c->b_eng[E_TMP], N0);
         launch(c, "logit_keys", dim3(g0), dim3(256), 0, k_logit_keys_rows, IN.logit, N0, k0, kc,
                vals);
         radix_sort_u32(c, kc, vals, kt, v2, N0, 32);
         launch(c, "gather_sid", dim3(g0), dim3(256), 0, k_gather_sid, (const int32_t *)sid_in,
                (const uint32_t *)vals, N0, S, (const int32_t *)nullptr, kc);
         radix_sort_u32(c, kc, vals, kt, v2, N0, bits_for(S));
-        double *thr = (double *)ws<uint8_t>(c->b_eng[E_THR], 8 * (S + 1));
+        double *thr = (double *)ws<uint8_t>(c, c->b_eng[E_THR], 8 * (S + 1));
         launch(c, "scene_thr", dim3(blocks_for(S, 128)), dim3(128), 0, k_scene_thr,
                (const uint32_t *)k0, (const uint32_t *)vals, din0, S,
                log(c->prm.tau / (1.0 - c->prm.tau)), thr);
@@ -497,9 +497,9 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     if (st) st->n_filtered = nf;
 
     // ---- Morton frames per scene (over all input rows)
-    float *frames = ws<float>(c->b_frame, 8 * S);
+    float *frames = ws<float>(c, c->b_frame, 8 * S);
     {
-        uint32_t *acc = ws<uint32_t>(c->b_bbox, 8 * S + 8);
+        uint32_t *acc = ws<uint32_t>(c, c->b_bbox, 8 * S + 8);
         uint32_t *bad = acc + 8 * S;
         NGS_CHECK_CUDA(cudaMemsetAsync(bad, 0, 4, c->st));
         if (!multi) {
@@ -523,8 +523,8 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     SplatView A, B;
     int32_t *cidA = nullptr, *cidB = nullptr;
     {
-        uint32_t *keys = ws<uint32_t>(c->b_codes, N0), *order = ws<uint32_t>(c->b_vals, N0);
-        uint32_t *k2 = ws<uint32_t>(c->b_codes2, N0), *v2 = ws<uint32_t>(c->b_vals2, N0);
+        uint32_t *keys = ws<uint32_t>(c, c->b_codes, N0), *order = ws<uint32_t>(c, c->b_vals, N0);
+        uint32_t *k2 = ws<uint32_t>(c, c->b_codes2, N0), *v2 = ws<uint32_t>(c, c->b_vals2, N0);
         if (!multi) {  // (dropped, code) in one 31-bit sort
             launch(c, "morton", dim3(g0), dim3(256), 0, k_morton_rows, IN.xyz,
                    (const int32_t *)nullptr, N0, (const float *)frames, (const int32_t *)keep,
@@ -544,8 +544,8 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         A = scratch(c, c->b_sA, nf, F);
         B = multi ? scratch(c, c->b_sC, nf, F) : scratch(c, c->b_sB, nf, F);
         gather_rows(c, IN, order, A);
-        cidA = ws<int32_t>(c->b_cid, nf + 1);
-        cidB = ws<int32_t>(c->b_cid2, nf + 1);
+        cidA = ws<int32_t>(c, c->b_cid, nf + 1);
+        cidB = ws<int32_t>(c, c->b_cid2, nf + 1);
         launch(c, "gather_cid", dim3(grid_stride_blocks(c, nf, 256, 8)), dim3(256), 0,
                k_gather_cid, (const uint32_t *)order, (const int32_t *)pos, nf, cidA);
     }
@@ -559,7 +559,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         running[s] = n[s] > tgt[s] && n[s] > 1;
     }
     for (int s = 0; s <= S; s++) wstart[s] = kin[s];
-    int32_t *sidA = ws<int32_t>(c->b_eng[E_SIDW], nf + 1);
+    int32_t *sidA = ws<int32_t>(c, c->b_eng[E_SIDW], nf + 1);
 
     // write stopped scenes back (canonical order) and drop them from A
     auto extract = [&](bool all) {
@@ -588,8 +588,8 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
                     if (stop[s]) removed += n[s];
                 }
                 const int64_t *dshift = upload(c, c->b_eng[E_SHIFT], shift.data(), S);
-                int32_t *kp = ws<int32_t>(c->b_keep, nA + 1);
-                int32_t *pp = ws<int32_t>(c->b_eng[E_POS2], nA + 1);
+                int32_t *kp = ws<int32_t>(c, c->b_keep, nA + 1);
+                int32_t *pp = ws<int32_t>(c, c->b_eng[E_POS2], nA + 1);
                 launch(c, "running_flags", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0,
                        k_running_flags, nA, (const int32_t *)sidA, dstop, kp);
                 scan_i32(c, kp, pp, nA);
@@ -635,9 +635,9 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
                 NGS_FAIL(NGS_ERR_STATE, "scene %d: k_eff differs within a batch", s);
         g.cid = cidA;
         // exact Morton order of this pass, grouped by scene
-        uint32_t *pk = ws<uint32_t>(c->b_codes, nA), *pv = ws<uint32_t>(c->b_vals, nA);
-        uint32_t *pk2 = ws<uint32_t>(c->b_codes2, nA), *pv2 = ws<uint32_t>(c->b_vals2, nA);
-        uint32_t *code_row = ws<uint32_t>(c->b_eng[E_TMP], nA);
+        uint32_t *pk = ws<uint32_t>(c, c->b_codes, nA), *pv = ws<uint32_t>(c, c->b_vals, nA);
+        uint32_t *pk2 = ws<uint32_t>(c, c->b_codes2, nA), *pv2 = ws<uint32_t>(c, c->b_vals2, nA);
+        uint32_t *code_row = ws<uint32_t>(c, c->b_eng[E_TMP], nA);
         int32_t *ssid = nullptr;
         launch(c, "morton", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0, k_morton_rows,
                (const float *)A.xyz, multi ? (const int32_t *)sidA : (const int32_t *)nullptr, nA,
@@ -645,7 +645,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         if (multi) {
             NGS_CHECK_CUDA(cudaMemcpyAsync(code_row, pk, 4 * nA, cudaMemcpyDeviceToDevice, c->st));
             radix_sort_u32(c, pk, pv, pk2, pv2, nA, 30);
-            uint32_t *sk = ws<uint32_t>(c->b_eng[E_SSID], nA);
+            uint32_t *sk = ws<uint32_t>(c, c->b_eng[E_SSID], nA);
             launch(c, "gather_sid", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0,
                    k_gather_sid, (const int32_t *)sidA, (const uint32_t *)pv, nA, S,
                    (const int32_t *)nullptr, sk);
@@ -655,16 +655,16 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         } else {
             radix_sort_u32(c, pk, pv, pk2, pv2, nA, 30);
         }
-        float4 *pts = ws<float4>(c->b_pts, nA);
+        float4 *pts = ws<float4>(c, c->b_pts, nA);
         gather_points(c, A.xyz, cidA, pv, nA, pts);
-        int32_t *nbr = ws<int32_t>(c->b_nbr, nA * g.k_eff);
+        int32_t *nbr = ws<int32_t>(c, c->b_nbr, nA * g.k_eff);
         std::vector<int64_t> scene_n(S);
         for (int s = 0; s < S; s++) scene_n[s] = out_done[s] ? 0 : n[s];
         knn_search(c, KnnInput{pts, pk, pv, ssid, frames, scene_n.data(), S, nA, 0, cidA},
                    g.k_eff, nbr);
         build_edges(c, nbr, g);
         edge_costs(c, A, g, (uint32_t)pass, false, nullptr);
-        int32_t *partner = ws<int32_t>(c->b_partner, nA);
+        int32_t *partner = ws<int32_t>(c, c->b_partner, nA);
         int64_t np = 0;
         if (!multi) {
             P[0] = n[0] - tgt[0];
@@ -673,7 +673,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         } else {
             const int64_t matched = match_rounds(c, g);
             std::vector<int32_t> cnt(S, 0);
-            int32_t *dcnt = ws<int32_t>(c->b_eng[E_CNT], S + 1);
+            int32_t *dcnt = ws<int32_t>(c, c->b_eng[E_CNT], S + 1);
             NGS_CHECK_CUDA(cudaMemsetAsync(dcnt, 0, 4 * S, c->st));
             if (matched > 0)
                 launch(c, "scene_pairs", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0,
@@ -690,19 +690,19 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
                 capped = capped || cnt[s] > P[s];
                 seg[s + 1] = seg[s] + cnt[s];
             }
-            uint64_t *thr = (uint64_t *)ws<uint8_t>(c->b_eng[E_THR], 8 * (S + 1));
+            uint64_t *thr = (uint64_t *)ws<uint8_t>(c, c->b_eng[E_THR], 8 * (S + 1));
             if (capped) {
                 // per-scene thresholds: pair keys sorted by (scene, cost, lo id)
-                uint64_t *keys = (uint64_t *)ws<uint8_t>(c->b_flag, 8 * nA);
+                uint64_t *keys = (uint64_t *)ws<uint8_t>(c, c->b_flag, 8 * nA);
                 pair_keys(c, g, keys);
-                int32_t *fl = ws<int32_t>(c->b_keep, nA + 1), *fp = ws<int32_t>(c->b_eng[E_POS2], nA + 1);
+                int32_t *fl = ws<int32_t>(c, c->b_keep, nA + 1), *fp = ws<int32_t>(c, c->b_eng[E_POS2], nA + 1);
                 launch(c, "key_flags", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0,
                        k_key_flags, nA, (const uint64_t *)keys, fl);
                 scan_i32(c, fl, fp, nA);
                 const int64_t m = seg[S];
-                uint32_t *klo = ws<uint32_t>(c->b_eng[E_KLO], m), *khi = ws<uint32_t>(c->b_eng[E_KHI], m);
-                uint32_t *ks = ws<uint32_t>(c->b_eng[E_KS], m), *ord = ws<uint32_t>(c->b_eng[E_ORD], m);
-                uint32_t *t1 = ws<uint32_t>(c->b_eng[E_T1], m), *t2 = ws<uint32_t>(c->b_eng[E_T2], m);
+                uint32_t *klo = ws<uint32_t>(c, c->b_eng[E_KLO], m), *khi = ws<uint32_t>(c, c->b_eng[E_KHI], m);
+                uint32_t *ks = ws<uint32_t>(c, c->b_eng[E_KS], m), *ord = ws<uint32_t>(c, c->b_eng[E_ORD], m);
+                uint32_t *t1 = ws<uint32_t>(c, c->b_eng[E_T1], m), *t2 = ws<uint32_t>(c, c->b_eng[E_T2], m);
                 launch(c, "pair_list", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0,
                        k_pair_list, nA, (const uint64_t *)keys, (const int32_t *)fp,
                        (const int32_t *)sidA, klo, khi, ks);
@@ -712,10 +712,10 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
                 gather_u32(c, khi, ord, m, t1);
                 radix_sort_u32(c, t1, ord, t2, pk2, m, 32);  // then by cost bits
                 gather_u32(c, ks, ord, m, t2);
-                uint32_t *t3 = ws<uint32_t>(c->b_eng[E_T3], m);
+                uint32_t *t3 = ws<uint32_t>(c, c->b_eng[E_T3], m);
                 gather_u32(c, khi, ord, m, t3);             // cost bits in (cost, lo) order
                 // stable by scene, carrying the cost bits alongside through a second payload pass
-                uint32_t *ord2 = ws<uint32_t>(c->b_eng[E_ORD2], m);
+                uint32_t *ord2 = ws<uint32_t>(c, c->b_eng[E_ORD2], m);
                 iota_u32(c, ord2, m);
                 radix_sort_u32(c, t2, ord2, t1, pk2, m, bits_for(S));
                 gather_u32(c, t3, ord2, m, t1);             // cost bits in (scene, cost, lo) order
@@ -740,7 +740,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         for (int s = 0; s < S; s++)
             if (!out_done[s] && pairs_s[s] == 0) running[s] = 0;  // no pair: this scene stops
         if (np > 0) {
-            int32_t *role = ws<int32_t>(c->b_role, nA);
+            int32_t *role = ws<int32_t>(c, c->b_role, nA);
             partner_to_role(c, partner, cidA, nA, role);
             B.n = nA;
             const int64_t nn = merge_compact(c, A, role, B, cidA, cidB);

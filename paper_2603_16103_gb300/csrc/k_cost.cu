@@ -384,13 +384,13 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     std::vector<float> h(4 * (size_t)S);
     host_mc_draws(c->prm.seed, pass, S, h.data(), h.data() + 3 * S);
-    float *zs = ws<float>(c->b_rng, 4 * S);
+    float *zs = ws<float>(c, c->b_rng, 4 * S);
     NGS_CHECK_CUDA(cudaMemcpyAsync(zs, h.data(), sizeof(float) * 4 * S, cudaMemcpyHostToDevice,
                                    c->st));
-    float *rec = ws<float>(c->b_rec, s.n * REC);
+    float *rec = ws<float>(c, c->b_rec, s.n * REC);
     launch(c, "cost_prep", dim3(grid_stride_blocks(c, s.n, 256, 8)), dim3(256), 0, k_prep, s.xyz,
            s.ls, s.rot, s.logit, s.n, (const float *)zs, rec);
-    unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c->b_status, 64);
+    unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c, c->b_status, 64);
     NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, c->st));
     launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0, k_edge_cost,
            (const int4 *)(lex ? g.erec_lex : g.erec), m, (const float *)rec, (const float *)s.sh,

@@ -119,12 +119,12 @@ void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
     g.nbr = nbr;
     if (n <= 1 || k <= 0) return;
     const int64_t m = n * k;
-    g.mirror = ws<int32_t>(c->b_adj, m);
-    int32_t *canon = ws<int32_t>(c->b_flag, m + 1);
-    int32_t *epos = ws<int32_t>(c->b_adjeid, m + 1);
-    int32_t *revcnt = ws<int32_t>(c->b_deg, n + 1);
-    int32_t *revfill = ws<int32_t>(c->b_fill, n + 1);
-    g.rev_ptr = ws<int32_t>(c->b_rstart, n + 1);
+    g.mirror = ws<int32_t>(c, c->b_adj, m);
+    int32_t *canon = ws<int32_t>(c, c->b_flag, m + 1);
+    int32_t *epos = ws<int32_t>(c, c->b_adjeid, m + 1);
+    int32_t *revcnt = ws<int32_t>(c, c->b_deg, n + 1);
+    int32_t *revfill = ws<int32_t>(c, c->b_fill, n + 1);
+    g.rev_ptr = ws<int32_t>(c, c->b_rstart, n + 1);
     launch(c, "zero2", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_zero2, revcnt,
            revfill, n);
     launch(c, "slot_classify", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0,
@@ -137,33 +137,33 @@ void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
     sync_stream(c);
     g.n_edges = ((int32_t *)c->h_pin)[0];
     const int64_t nrev = ((int32_t *)c->h_pin)[1];
-    g.erec = ws<int4>(c->b_elo, g.n_edges);
-    g.rev = ws<int32_t>(c->b_upc, nrev);
+    g.erec = ws<int4>(c, c->b_elo, g.n_edges);
+    g.rev = ws<int32_t>(c, c->b_upc, nrev);
     launch(c, "slot_fill", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0, k_slot_fill,
            nbr, n, k, g.cid, (const int32_t *)g.mirror, (const int32_t *)canon,
            (const int32_t *)epos, (const int32_t *)g.rev_ptr, revfill, g.erec, g.rev);
-    g.cost_slot = ws<float>(c->b_cost, m);
+    g.cost_slot = ws<float>(c, c->b_cost, m);
 }
 
 void build_lex_view(ngs_ctx *c, GraphDev &g) {
     const int64_t ne = g.n_edges;
     if (ne <= 0) return;
-    uint32_t *klo = ws<uint32_t>(c->b_codes, ne), *khi = ws<uint32_t>(c->b_codes2, ne);
-    uint32_t *val = ws<uint32_t>(c->b_vals, ne);
-    uint32_t *t1 = ws<uint32_t>(c->b_vals2, ne);
+    uint32_t *klo = ws<uint32_t>(c, c->b_codes, ne), *khi = ws<uint32_t>(c, c->b_codes2, ne);
+    uint32_t *val = ws<uint32_t>(c, c->b_vals, ne);
+    uint32_t *t1 = ws<uint32_t>(c, c->b_vals2, ne);
     launch(c, "lex_keys", dim3(grid_stride_blocks(c, ne, 256, 8)), dim3(256), 0, k_lex_keys,
            (const int4 *)g.erec, ne, g.cid, klo, khi, val);
     // LSD over (lo, hi): stable sort by hi, then by lo.  Payload = record index.
-    uint32_t *idx = ws<uint32_t>(c->b_cid, ne), *idx2 = ws<uint32_t>(c->b_cid2, ne);
-    uint32_t *ktmp = ws<uint32_t>(c->b_pos, ne);
+    uint32_t *idx = ws<uint32_t>(c, c->b_cid, ne), *idx2 = ws<uint32_t>(c, c->b_cid2, ne);
+    uint32_t *ktmp = ws<uint32_t>(c, c->b_pos, ne);
     iota_u32(c, idx, ne);
     NGS_CHECK_CUDA(cudaMemcpyAsync(t1, khi, 4 * ne, cudaMemcpyDeviceToDevice, c->st));
     radix_sort_u32(c, t1, idx, ktmp, idx2, ne, 32);
     gather_u32(c, klo, idx, ne, t1);          // lo in hi-sorted order
     radix_sort_u32(c, t1, idx, ktmp, idx2, ne, 32);
-    g.elo = ws<int32_t>(c->b_ehi, ne);
-    g.ehi = ws<int32_t>(c->b_nbr2, ne);
-    g.erec_lex = ws<int4>(c->b_lexrec, ne);
+    g.elo = ws<int32_t>(c, c->b_ehi, ne);
+    g.ehi = ws<int32_t>(c, c->b_nbr2, ne);
+    g.erec_lex = ws<int4>(c, c->b_lexrec, ne);
     gather_u32(c, khi, idx, ne, ktmp);
     launch(c, "lex_view", dim3(grid_stride_blocks(c, ne, 256, 8)), dim3(256), 0, k_lex_view,
            (const uint32_t *)t1, (const uint32_t *)ktmp, (const uint32_t *)idx,

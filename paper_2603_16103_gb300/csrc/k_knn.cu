@@ -429,7 +429,7 @@ __global__ void k_map_ids(int32_t *a, int64_t m, const int32_t *__restrict__ pos
 }  // namespace
 
 void morton_frame(ngs_ctx *c, const float *xyz, int64_t n, float *frame) {
-    uint32_t *acc = ws<uint32_t>(c->b_bbox, 8);
+    uint32_t *acc = ws<uint32_t>(c, c->b_bbox, 8);
     launch(c, "frame_init", dim3(1), dim3(32), 0, k_frame_init, acc);
     launch(c, "frame_reduce", dim3(grid_stride_blocks(c, n, 256, 4)), dim3(256), 0,
            k_frame_reduce, xyz, n, acc);
@@ -482,12 +482,12 @@ void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
         hoff[s + 1] = hoff[s] + ((int64_t)1 << (3 * hlt[s])) + 1;
     }
     const int64_t tlen = hoff[S];
-    uint8_t *small = ws<uint8_t>(c->b_knnsc, 16 * (S + 1) + 256);
+    uint8_t *small = ws<uint8_t>(c, c->b_knnsc, 16 * (S + 1) + 256);
     int32_t *dlt = (int32_t *)small;
     int64_t *doff = (int64_t *)(small + ((4 * (size_t)S + 15) & ~(size_t)15));
     NGS_CHECK_CUDA(cudaMemcpyAsync(dlt, hlt, 4 * S, cudaMemcpyHostToDevice, c->st));
     NGS_CHECK_CUDA(cudaMemcpyAsync(doff, hoff, 8 * (S + 1), cudaMemcpyHostToDevice, c->st));
-    int32_t *T = ws<int32_t>(c->b_nodes, tlen + 1);
+    int32_t *T = ws<int32_t>(c, c->b_nodes, tlen + 1);
     NGS_CHECK_CUDA(cudaMemsetAsync(T, 0, sizeof(int32_t) * tlen, c->st));
     launch(c, "cell_count", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_cell_count,
            in.scode, in.ssid, n, (const int32_t *)dlt, (const int64_t *)doff, T);
@@ -505,7 +505,7 @@ void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
 #undef KNN_LAUNCH
     if (!in.out_by_cid) {
         // rows are internal indices; translate the neighbours' canonical ids
-        int32_t *pos_of_cid = ws<int32_t>(c->b_nbr2, n);
+        int32_t *pos_of_cid = ws<int32_t>(c, c->b_nbr2, n);
         launch(c, "knn_cid_to_pos", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0,
                k_cid_to_pos, in.cid, n, pos_of_cid);
         launch(c, "knn_map_ids", dim3(grid_stride_blocks(c, n * k_eff, 256, 8)), dim3(256), 0,

@@ -166,14 +166,14 @@ int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
     const int64_t n = g.n;
     c->rounds = 0;
     if (n <= 0) return 0;
-    int32_t *mate = ws<int32_t>(c->b_mate, n);
-    int32_t *cand = ws<int32_t>(c->b_cand, n);
-    uint32_t *candkey = ws<uint32_t>(c->b_candkey, n);
+    int32_t *mate = ws<int32_t>(c, c->b_mate, n);
+    int32_t *cand = ws<int32_t>(c, c->b_cand, n);
+    uint32_t *candkey = ws<uint32_t>(c, c->b_candkey, n);
     const int max_rounds = 4096;
-    int32_t *counts = ws<int32_t>(c->b_counts, 2 * max_rounds);
+    int32_t *counts = ws<int32_t>(c, c->b_counts, 2 * max_rounds);
     int32_t *wl_counts = counts + max_rounds;  // worklist size feeding round r+1
     NGS_CHECK_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2 * max_rounds, c->st));
-    int32_t *wl[2] = {ws<int32_t>(c->b_sel2, n), ws<int32_t>(c->b_cflag2, n)};
+    int32_t *wl[2] = {ws<int32_t>(c, c->b_sel2, n), ws<int32_t>(c, c->b_cflag2, n)};
     const unsigned grid = grid_stride_blocks(c, n, 256, 8);
     launch(c, "match_init", dim3(grid), dim3(256), 0, k_match_init, n, mate, cand);
     int64_t matched = 0;
@@ -235,15 +235,15 @@ int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *
     if (max_pairs > 0) {
         matched = match_rounds(c, g);
     } else {
-        ws<int32_t>(c->b_mate, n);
-        ws<uint32_t>(c->b_candkey, n);
+        ws<int32_t>(c, c->b_mate, n);
+        ws<uint32_t>(c, c->b_candkey, n);
         launch(c, "match_init", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_match_init, n,
-               (int32_t *)c->b_mate.p, ws<int32_t>(c->b_cand, n));
+               (int32_t *)c->b_mate.p, ws<int32_t>(c, c->b_cand, n));
     }
     const bool capped = matched > max_pairs;
-    uint64_t *thr = (uint64_t *)ws<uint8_t>(c->b_sel, 64);
+    uint64_t *thr = (uint64_t *)ws<uint8_t>(c, c->b_sel, 64);
     if (capped) {
-        uint64_t *keys = (uint64_t *)ws<uint8_t>(c->b_flag, sizeof(uint64_t) * n);
+        uint64_t *keys = (uint64_t *)ws<uint8_t>(c, c->b_flag, sizeof(uint64_t) * n);
         pair_keys(c, g, keys);
         radix_select_u64(c, keys, n, max_pairs - 1, thr);
     }
@@ -254,8 +254,8 @@ int64_t select_pairs(ngs_ctx *c, const GraphDev &g, int64_t max_pairs, int32_t *
 int64_t partner_to_pairs(ngs_ctx *c, const int32_t *partner, const int32_t *cid, int64_t n,
                          int32_t *pairs_out) {
     if (n <= 0) return 0;
-    int32_t *flag = ws<int32_t>(c->b_keep, n + 1);
-    int32_t *pos = ws<int32_t>(c->b_pos, n + 1);
+    int32_t *flag = ws<int32_t>(c, c->b_keep, n + 1);
+    int32_t *pos = ws<int32_t>(c, c->b_pos, n + 1);
     const unsigned grid = grid_stride_blocks(c, n, 256, 8);
     launch(c, "lo_flags", dim3(grid), dim3(256), 0, k_lo_flags, n, partner, cid, flag);
     scan_i32(c, flag, pos, n);

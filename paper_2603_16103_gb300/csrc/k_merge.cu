@@ -551,9 +551,9 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
         out.n = 0;
         return 0;
     }
-    int32_t *keep = ws<int32_t>(c->b_keep, n + 1);
-    int32_t *pos = ws<int32_t>(c->b_pos, n + 1);
-    int32_t *mflag = ws<int32_t>(c->b_flag, 2 * (n + 1));
+    int32_t *keep = ws<int32_t>(c, c->b_keep, n + 1);
+    int32_t *pos = ws<int32_t>(c, c->b_pos, n + 1);
+    int32_t *mflag = ws<int32_t>(c, c->b_flag, 2 * (n + 1));
     int32_t *mpos = mflag + (n + 1);
     const unsigned grid = grid_stride_blocks(c, n, 256, 8);
     launch(c, "keep_flags", dim3(grid), dim3(256), 0, k_keep_flags, n, role, keep, mflag);
@@ -564,14 +564,14 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
     sync_stream(c);
     const int64_t nout = ((int32_t *)c->h_pin)[0];
     const int64_t npairs = ((int32_t *)c->h_pin)[1];
-    int32_t *list = ws<int32_t>(c->b_pairs, npairs);
+    int32_t *list = ws<int32_t>(c, c->b_pairs, npairs);
     launch(c, "list_merges", dim3(grid), dim3(256), 0, k_list_merges, n, (const int32_t *)mflag,
            (const int32_t *)mpos, list);
     Rows ri = rows_of(in);
     WRows wo = wrows_of(out);
     launch(c, "copy_kept", dim3(grid_stride_blocks(c, n * ((in.F >> 2) + 1), 256, 16)), dim3(256),
            0, k_copy_kept, ri, wo, n, in.F, role, (const int32_t *)pos);
-    unsigned long long *hits = (unsigned long long *)ws<uint8_t>(c->b_status, 64) + 1;
+    unsigned long long *hits = (unsigned long long *)ws<uint8_t>(c, c->b_status, 64) + 1;
     NGS_CHECK_CUDA(cudaMemsetAsync(hits, 0, 8, c->st));
     if (npairs > 0)
         launch(c, "merge", dim3(grid_stride_blocks(c, npairs, 128, 16)), dim3(128), 0, k_merge, ri,
@@ -579,8 +579,8 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
                c->prm.eig_floor, c->prm.fp64_policy, hits);
     NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin + 2, hits, 8, cudaMemcpyDeviceToHost, c->st));
     if (cid) {
-        int32_t *cflag = ws<int32_t>(c->b_cflag, n + 1);
-        int32_t *cscan = ws<int32_t>(c->b_cscan, n + 1);
+        int32_t *cflag = ws<int32_t>(c, c->b_cflag, n + 1);
+        int32_t *cscan = ws<int32_t>(c, c->b_cscan, n + 1);
         launch(c, "cid_flags", dim3(grid), dim3(256), 0, k_cid_flags, n, cid, (const int32_t *)keep,
                cflag);
         scan_i32(c, cflag, cscan, n);
@@ -595,7 +595,7 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
 
 bool pairs_to_role(ngs_ctx *c, const int32_t *pairs, int64_t npairs, int64_t n, int32_t *role) {
     NGS_CHECK_CUDA(cudaMemsetAsync(role, 0xff, sizeof(int32_t) * n, c->st));  // -1
-    int32_t *err = (int32_t *)ws<uint8_t>(c->b_status, 64) + 8;
+    int32_t *err = (int32_t *)ws<uint8_t>(c, c->b_status, 64) + 8;
     NGS_CHECK_CUDA(cudaMemsetAsync(err, 0, 4, c->st));
     if (npairs > 0)
         launch(c, "pairs_role", dim3(grid_stride_blocks(c, npairs, 256, 8)), dim3(256), 0,
@@ -613,15 +613,15 @@ void partner_to_role(ngs_ctx *c, const int32_t *partner, const int32_t *cid, int
 
 int64_t prefilter_flags(ngs_ctx *c, const float *logit, int64_t n, double tau, int32_t *keep) {
     if (n <= 0) return 0;
-    uint32_t *keys = ws<uint32_t>(c->b_codes, n);
-    uint32_t *med = (uint32_t *)ws<uint8_t>(c->b_sel, 64);
+    uint32_t *keys = ws<uint32_t>(c, c->b_codes, n);
+    uint32_t *med = (uint32_t *)ws<uint8_t>(c, c->b_sel, 64);
     const unsigned grid = grid_stride_blocks(c, n, 256, 8);
     launch(c, "logit_keys", dim3(grid), dim3(256), 0, k_logit_keys, logit, n, keys);
     radix_select_u32(c, keys, n, (n - 1) / 2, med);
     const double l_tau = log(tau / (1.0 - tau));
     launch(c, "prefilter_flags", dim3(grid), dim3(256), 0, k_prefilter_flags, logit, n,
            (const uint32_t *)med, l_tau, keep);
-    int32_t *pos = ws<int32_t>(c->b_pos, n + 1);
+    int32_t *pos = ws<int32_t>(c, c->b_pos, n + 1);
     scan_i32(c, keep, pos, n);
     NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin, pos + n, 4, cudaMemcpyDeviceToHost, c->st));
     sync_stream(c);

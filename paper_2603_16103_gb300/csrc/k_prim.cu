@@ -228,7 +228,7 @@ __global__ void k_sel_out(const SelState *s, K *out) {
 void scan_i32(ngs_ctx *c, const int32_t *in, int32_t *out, int64_t n) {
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb < 1) nb = 1;
-    int32_t *part = ws<int32_t>(c->b_scan_part, nb + 1);
+    int32_t *part = ws<int32_t>(c, c->b_scan_part, nb + 1);
     launch(c, "scan_reduce", dim3((unsigned)nb), dim3(SCAN_THREADS), 0, k_scan_reduce, in, n, part);
     launch(c, "scan_partials", dim3(1), dim3(1024), 0, k_scan_partials, part, nb);
     launch(c, "scan_apply", dim3((unsigned)nb), dim3(SCAN_THREADS), 0, k_scan_apply, in, out, n,
@@ -239,7 +239,7 @@ void radix_sort_u32(ngs_ctx *c, uint32_t *keys, uint32_t *vals, uint32_t *keys_t
                     uint32_t *vals_tmp, int64_t n, int bits) {
     if (n <= 1) return;
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-    int32_t *hist = ws<int32_t>(c->b_hist, 256 * ntiles + 1);
+    int32_t *hist = ws<int32_t>(c, c->b_hist, 256 * ntiles + 1);
     uint32_t *ka = keys, *va = vals, *kb = keys_tmp, *vb = vals_tmp;
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; p++) {
@@ -262,7 +262,7 @@ void radix_sort_u32(ngs_ctx *c, uint32_t *keys, uint32_t *vals, uint32_t *keys_t
 template <class K>
 static void radix_select_impl(ngs_ctx *c, const K *keys, int64_t n, int64_t k, K *d_out,
                               bool skip_max) {
-    uint8_t *misc = ws<uint8_t>(c->b_misc, 4096);
+    uint8_t *misc = ws<uint8_t>(c, c->b_misc, 4096);
     SelState *st = (SelState *)misc;
     int32_t *hist = (int32_t *)(misc + 256);
     launch(c, "sel_init", dim3(1), dim3(256), 0, k_sel_init, st, k, hist);

@@ -5,6 +5,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include <algorithm>
 #include <utility>
 
@@ -35,27 +37,55 @@ extern "C" const char *ngs_last_error(void) { return g_err; }
     return NGS_OK;
 
 // ---------------------------------------------------------------- workspace
-void *ws_get(DevBuf &b, size_t bytes) {
+// One memory pool per device, private to the library.  Its release threshold
+// is unlimited, so blocks freed when a buffer grows stay cached for the next
+// request instead of going back to the driver at every synchronisation.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static cudaMemPool_t pool_of(int dev) {
+    if (dev < 0 || dev >= 64) NGS_FAIL(NGS_ERR_CUDA, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        NGS_CHECK_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t thr = UINT64_MAX;
+        NGS_CHECK_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pool[dev] = p;
+    }
+    return g_pool[dev];
+}
+
+void *ws_get(ngs_ctx *c, DevBuf &b, size_t bytes) {
     if (bytes <= b.bytes) return b.p;
     if (b.p) {
-        NGS_CHECK_CUDA(cudaFree(b.p));  // implicit device sync: safe for in-flight work
+        NGS_CHECK_CUDA(cudaFreeAsync(b.p, c->st));  // after the queued work that used it
+        c->ws_bytes -= (int64_t)b.bytes;
         b.p = nullptr;
         b.bytes = 0;
     }
     size_t want = bytes + bytes / 8 + 256;
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, want);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, want, pool_of(c->device), c->st);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        NGS_FAIL(NGS_ERR_OOM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+        NGS_FAIL(NGS_ERR_OOM, "device allocation of %zu bytes failed: %s", want,
+                 cudaGetErrorString(e));
     }
     b.p = p;
     b.bytes = want;
+    c->ws_bytes += (int64_t)want;
     return p;
 }
 
-static void ws_free(DevBuf &b) {
-    if (b.p) cudaFree(b.p);
+static void ws_free(ngs_ctx *c, DevBuf &b) {
+    if (b.p) cudaFreeAsync(b.p, c->st);
+    c->ws_bytes -= (int64_t)b.bytes;
     b.p = nullptr;
     b.bytes = 0;
 }
@@ -201,9 +231,7 @@ extern "C" int ngs_create(ngs_ctx **out, const ngs_params *p, void *stream) {
     return NGS_OK;
 }
 
-extern "C" int ngs_destroy(ngs_ctx *c) {
-    if (!c) return NGS_OK;
-    cudaStreamSynchronize(c->st);
+static void release_all(ngs_ctx *c) {
     DevBuf *bufs[] = {&c->b_pts, &c->b_codes, &c->b_codes2, &c->b_vals, &c->b_vals2, &c->b_hist,
                       &c->b_bbox, &c->b_frame, &c->b_nodes, &c->b_nbr, &c->b_deg, &c->b_cap,
                       &c->b_rstart, &c->b_adj, &c->b_adjeid, &c->b_fill, &c->b_upc, &c->b_eptr,
@@ -212,14 +240,38 @@ extern "C" int ngs_destroy(ngs_ctx *c) {
                       &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
                       &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2,
                       &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc};
-    for (DevBuf *b : bufs) ws_free(*b);
+    for (DevBuf *b : bufs) ws_free(c, *b);
     for (int k = 0; k < 5; k++) {
-        ws_free(c->b_sA[k]);
-        ws_free(c->b_sB[k]);
-        ws_free(c->b_host_dev[k]);
-        ws_free(c->b_sC[k]);
+        ws_free(c, c->b_sA[k]);
+        ws_free(c, c->b_sB[k]);
+        ws_free(c, c->b_host_dev[k]);
+        ws_free(c, c->b_sC[k]);
     }
-    for (DevBuf &b : c->b_eng) ws_free(b);
+    for (DevBuf &b : c->b_eng) ws_free(c, b);
+    c->g_valid = false;
+    cudaStreamSynchronize(c->st);
+    // hand the now unused blocks back to the driver (blocks other contexts
+    // still hold stay in the pool)
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (c->device >= 0 && c->device < 64) pool = g_pool[c->device];
+    }
+    if (pool) cudaMemPoolTrimTo(pool, 0);
+}
+
+extern "C" int ngs_release_workspace(ngs_ctx *c) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    NGS_CHECK_CUDA(cudaStreamSynchronize(c->st));
+    release_all(c);
+    API_END
+}
+
+extern "C" int ngs_destroy(ngs_ctx *c) {
+    if (!c) return NGS_OK;
+    cudaStreamSynchronize(c->st);
+    release_all(c);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -260,11 +312,11 @@ static SplatView view_of(const ngs_splats *s) {
 
 static SplatView scratch_view(ngs_ctx *c, DevBuf *b, int64_t n, int F) {
     SplatView v;
-    v.xyz = ws<float>(b[0], 3 * n);
-    v.ls = ws<float>(b[1], 3 * n);
-    v.rot = ws<float>(b[2], 4 * n);
-    v.logit = ws<float>(b[3], n);
-    v.sh = ws<float>(b[4], (int64_t)F * n);
+    v.xyz = ws<float>(c, b[0], 3 * n);
+    v.ls = ws<float>(c, b[1], 3 * n);
+    v.rot = ws<float>(c, b[2], 4 * n);
+    v.logit = ws<float>(c, b[3], n);
+    v.sh = ws<float>(c, b[4], (int64_t)F * n);
     v.n = n;
     v.F = F;
     (void)c;
@@ -296,7 +348,7 @@ extern "C" int ngs_prefilter(ngs_ctx *c, ngs_splats *s) {
     check_splats(s, "ngs_prefilter");
     const int64_t n = s->n;
     if (n <= 0) return NGS_OK;
-    int32_t *keep = ws<int32_t>(c->b_role, n + 1);
+    int32_t *keep = ws<int32_t>(c, c->b_role, n + 1);
     int64_t kept = prefilter_flags(c, s->opacity_logit, n, c->prm.tau, keep);
     if (kept < n) {
         SplatView in = view_of(s);
@@ -320,16 +372,16 @@ static void graph_canonical(ngs_ctx *c, const ngs_splats *s) {
     g.k_eff = n >= 2 ? k_eff_of(n, c->prm.k) : 0;
     g.cid = nullptr;
     if (n >= 2) {
-        float *frame = ws<float>(c->b_frame, 8);
+        float *frame = ws<float>(c, c->b_frame, 8);
         morton_frame(c, s->xyz, n, frame);
         check_finite_frame(c, frame);
-        uint32_t *keys = ws<uint32_t>(c->b_codes, n), *vals = ws<uint32_t>(c->b_vals, n);
-        uint32_t *k2 = ws<uint32_t>(c->b_codes2, n), *v2 = ws<uint32_t>(c->b_vals2, n);
+        uint32_t *keys = ws<uint32_t>(c, c->b_codes, n), *vals = ws<uint32_t>(c, c->b_vals, n);
+        uint32_t *k2 = ws<uint32_t>(c, c->b_codes2, n), *v2 = ws<uint32_t>(c, c->b_vals2, n);
         morton_keys(c, s->xyz, n, frame, keys, vals);
         radix_sort_u32(c, keys, vals, k2, v2, n, 30);
-        float4 *pts = ws<float4>(c->b_pts, n);
+        float4 *pts = ws<float4>(c, c->b_pts, n);
         gather_points(c, s->xyz, nullptr, vals, n, pts);
-        int32_t *nbr = ws<int32_t>(c->b_nbr, n * g.k_eff);
+        int32_t *nbr = ws<int32_t>(c, c->b_nbr, n * g.k_eff);
         const int64_t sn = n;
         knn_search(c, KnnInput{pts, keys, vals, nullptr, frame, &sn, 1, n, 1, nullptr}, g.k_eff, nbr);
         build_edges(c, nbr, g);
@@ -387,7 +439,7 @@ extern "C" int ngs_select_pairs(ngs_ctx *c, const ngs_graph *g, const float *cos
         NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_select_pairs: NULL array");
     const int64_t n = c->g.n;
     if (n <= 1 || g->n_edges == 0 || max_pairs == 0) return NGS_OK;
-    int32_t *partner = ws<int32_t>(c->b_partner, n);
+    int32_t *partner = ws<int32_t>(c, c->b_partner, n);
     costs_to_slots(c, c->g, cost);
     select_pairs(c, c->g, max_pairs, partner);
     *n_pairs = partner_to_pairs(c, partner, nullptr, n, pairs_out);
@@ -402,7 +454,7 @@ extern "C" int ngs_merge_compact(ngs_ctx *c, ngs_splats *s, const int32_t *pairs
     if (n_pairs < 0 || n_pairs > n / 2 || (n_pairs > 0 && !pairs))
         NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_merge_compact: bad pair list");
     if (n_pairs == 0) return NGS_OK;
-    int32_t *role = ws<int32_t>(c->b_role, n);
+    int32_t *role = ws<int32_t>(c, c->b_role, n);
     if (!pairs_to_role(c, pairs, n_pairs, n, role))
         NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_merge_compact: pairs out of range, unordered or not disjoint");
     SplatView in = view_of(s);
@@ -498,11 +550,11 @@ extern "C" int ngs_simplify_host(ngs_ctx *c, ngs_splats *h, int64_t target, ngs_
     const int64_t n = h->n;
     const int F = h->sh_dim;
     ngs_splats d = *h;
-    d.xyz = ws<float>(c->b_host_dev[0], 3 * n);
-    d.log_scale = ws<float>(c->b_host_dev[1], 3 * n);
-    d.rot = ws<float>(c->b_host_dev[2], 4 * n);
-    d.opacity_logit = ws<float>(c->b_host_dev[3], n);
-    d.sh = ws<float>(c->b_host_dev[4], (int64_t)F * n);
+    d.xyz = ws<float>(c, c->b_host_dev[0], 3 * n);
+    d.log_scale = ws<float>(c, c->b_host_dev[1], 3 * n);
+    d.rot = ws<float>(c, c->b_host_dev[2], 4 * n);
+    d.opacity_logit = ws<float>(c, c->b_host_dev[3], n);
+    d.sh = ws<float>(c, c->b_host_dev[4], (int64_t)F * n);
     d.cap = n;
     const size_t sz[5] = {12, 12, 16, 4, 4 * (size_t)F};
     float *hp[5] = {h->xyz, h->log_scale, h->rot, h->opacity_logit, h->sh};
@@ -555,3 +607,15 @@ extern "C" int ngs_profile_reset(ngs_ctx *c) {
 }
 
 extern "C" int64_t ngs_launch_count(ngs_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" int64_t ngs_workspace_bytes(ngs_ctx *c) { return c ? c->ws_bytes : 0; }
+
+extern "C" int ngs_set_stream(ngs_ctx *c, void *stream) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    if ((cudaStream_t)stream != c->st) {
+        NGS_CHECK_CUDA(cudaStreamSynchronize(c->st));
+        c->st = (cudaStream_t)stream;
+    }
+    API_END
+}

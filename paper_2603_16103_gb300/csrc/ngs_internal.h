@@ -43,11 +43,16 @@ struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
 };
-// Grow-only device buffer (contents are not preserved on growth).
-void *ws_get(DevBuf &b, size_t bytes);
+// Grow-only device buffer (contents are not preserved on growth).  Memory
+// comes from the library's stream-ordered pool on the ctx's stream: growing
+// a buffer frees the old block after the work already queued on that stream
+// and never synchronises the device, so contexts on other streams keep
+// running.
+struct ngs_ctx;
+void *ws_get(ngs_ctx *c, DevBuf &b, size_t bytes);
 template <class T>
-T *ws(DevBuf &b, int64_t count) {
-    return (T *)ws_get(b, (size_t)(count > 0 ? count : 1) * sizeof(T));
+T *ws(ngs_ctx *c, DevBuf &b, int64_t count) {
+    return (T *)ws_get(c, b, (size_t)(count > 0 ? count : 1) * sizeof(T));
 }
 
 // ---------------------------------------------------------------- ctx
@@ -119,6 +124,7 @@ struct ngs_ctx {
     std::vector<PendingEv> pending;
     std::vector<cudaEvent_t> ev_free;
     int64_t launches = 0;
+    int64_t ws_bytes = 0;         // device workspace currently held
 
     // per-call counters
     int64_t fp64_edges = 0;

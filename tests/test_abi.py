@@ -57,8 +57,10 @@ def test_struct_layouts_match_header():
     import subprocess
     import tempfile
     from paper_2603_16103_gb300 import binding
-    src = ('#include <stdio.h>\n#include "ngs.h"\nint main(){printf("%zu %zu %zu %zu\\n",'
-           'sizeof(ngs_splats),sizeof(ngs_params),sizeof(ngs_graph),sizeof(ngs_stats));}\n')
+    names = ["ngs_splats", "ngs_params", "ngs_graph", "ngs_stats", "ngs_server_config",
+             "ngs_job_info", "ngs_server_stats"]
+    src = ('#include <stdio.h>\n#include "ngs.h"\nint main(){'
+           + "".join(f'printf("%zu\\n", sizeof({n}));' for n in names) + "}\n")
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "s.c")
         open(c, "w").write(src)
@@ -66,8 +68,7 @@ def test_struct_layouts_match_header():
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True,
                                                 check=True).stdout.split()]
-    assert sizes == [ctypes.sizeof(binding.ngs_splats), ctypes.sizeof(binding.ngs_params),
-                     ctypes.sizeof(binding.ngs_graph), ctypes.sizeof(binding.ngs_stats)]
+    assert sizes == [ctypes.sizeof(getattr(binding, n)) for n in names]
 
 
 def test_product_path_does_not_import_the_oracle():
