@@ -36,20 +36,31 @@ METRIC = "Gaussians simplified/s (6M->10%)"
 UNIT = "Gaussians/s"
 SPLAT_BYTES = 4 * (3 + 3 + 4 + 1 + 48)   # 236 B per splat, SH degree 3
 
-# Algorithmic bytes of each kernel per launch (one touch of what the method
-# must read and write): n = splats of the pass, e = undirected edges, p = pairs.
-ALGO_BYTES = {
-    "knn_k16": lambda n, e, p: n * (12 + 64),                  # read mu, write 16 ids
-    "edge_cost": lambda n, e, p: n * SPLAT_BYTES + e * 12,     # attributes once, (lo,hi) + cost per edge
-    "merge": lambda n, e, p: p * 3 * SPLAT_BYTES,              # read two rows, write one
-    "copy_kept": lambda n, e, p: (n - 2 * p) * 2 * SPLAT_BYTES,
-    "match_scan": lambda n, e, p: 2 * e * 8 + n * 8,           # adjacency + costs, mate/cand
-    "graph_row_sort": lambda n, e, p: 2 * e * 4 * 2 + n * 8,
+# Algorithmic work of each kernel, summed over the passes of one step, from
+# the per-pass splat count n, undirected edge count e and pair count p:
+# (bound, work, unit).  HBM-bound kernels count the bytes the method must
+# move (one touch of what it reads and writes); the kNN search is bound by
+# instruction issue, and its work is the FP32 distance arithmetic of the
+# smallest block it scans: 64 candidates per query x 9 ops (3 sub, 3 mul,
+# 2 add, 1 compare).
+KNN_OPS_PER_QUERY = 64 * 9
+ALGO = {
+    "knn_k16": ("alu", lambda n, e, p: n * KNN_OPS_PER_QUERY, "Gop/s"),
+    "edge_cost": ("hbm", lambda n, e, p: n * SPLAT_BYTES + e * 12, "GB/s"),
+    "cost_prep": ("hbm", lambda n, e, p: n * (SPLAT_BYTES + 128), "GB/s"),
+    "merge": ("hbm", lambda n, e, p: p * 3 * SPLAT_BYTES, "GB/s"),
+    "copy_kept": ("hbm", lambda n, e, p: (n - 2 * p) * 2 * SPLAT_BYTES, "GB/s"),
+    "slot_classify": ("hbm", lambda n, e, p: n * 16 * 4 * 2, "GB/s"),
+    "slot_fill": ("hbm", lambda n, e, p: n * 16 * 4 + e * 16, "GB/s"),
 }
 
-# DRAM traffic per launch from ncu captures (bytes per splat of the pass);
-# see profiles/ for the captures.  None until a capture of the current kernel exists.
-NCU_TRAFFIC_PER_SPLAT = {}
+# DRAM traffic per launch from ncu captures, in bytes per splat of the pass
+# (the profiles/ summaries give the commands and the raw counters).
+NCU_TRAFFIC_PER_SPLAT = {
+    "knn_k16": 42.51,      # 42.50 MB over 999,792 queries (knn_grid_patches1m.md)
+    "edge_cost": 563.55,   # 563.43 MB over 999,792 splats (edge_cost_patches1m.md)
+    "merge": 342.97,       # 342.90 MB, pass of 999,792 splats (merge_patches1m.md)
+}
 
 
 def parse():
@@ -396,24 +407,34 @@ def main():
 
     # ---- roofline of the dominant kernel (event-timed live above)
     pk, src = peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * 128 * pk.get("sm_max_mhz", 2070.0) / 1e3   # FP32 lane ops, Gop/s
     kern_total = sum(p[2] for p in prof) or 1.0
-    dom = max(prof, key=lambda p: p[2])
-    name, nl, ms = dom
     per_step = [(stats["pass_n"][i], stats["pass_edges"][i], stats["pass_pairs"][i])
-                 for i in range(stats["passes"])]
-    roof = None
-    if name in ALGO_BYTES and per_step:
-        byts = sum(ALGO_BYTES[name](*x) for x in per_step)          # per step
+                for i in range(stats["passes"])]
+
+    def roofline(entry):
+        name, nl, ms = entry
+        if name not in ALGO or not per_step or nl == 0:
+            return None
+        bound, fn, unit = ALGO[name]
+        work = sum(fn(*x) for x in per_step)                          # per step
         launches_per_step = nl / args.steps
-        avg_launch_ms = ms / nl
-        per_launch = byts / launches_per_step
-        achieved = per_launch / (avg_launch_ms / 1e3) / 1e9
+        avg_launch_s = ms / nl / 1e3
+        achieved = work / launches_per_step / avg_launch_s / 1e9
+        peak = pk["hbm_gbs"] if bound == "hbm" else alu_peak
         traffic = None
         if name in NCU_TRAFFIC_PER_SPLAT:
             traffic = NCU_TRAFFIC_PER_SPLAT[name] * sum(x[0] for x in per_step) / launches_per_step
-        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                "peak_source": src, "share": ms / kern_total}
+        return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": (f"{src} hbm_gbs" if bound == "hbm" else
+                                f"{sms} SMs x 128 FP32 lanes x {src} sm_max_mhz"),
+                "share": ms / kern_total, "ms_per_launch": avg_launch_s * 1e3}
+
+    dom = max(prof, key=lambda p: p[2])
+    roof = roofline(dom)
+    roofs = [r for r in (roofline(p) for p in sorted(prof, key=lambda p: -p[2])) if r]
     kernels = [{"name": p[0], "launches_per_step": p[1] / args.steps,
                 "ms_per_step": p[2] / args.steps, "share": p[2] / kern_total}
                for p in sorted(prof, key=lambda p: -p[2])[:12]]
@@ -462,7 +483,7 @@ def main():
                        "l2": "inputs (1.42 GB) larger than L2, restored from a pristine "
                              "device copy before every step",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "roofline_by_kernel": roofs, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
         out.update(forms)

@@ -321,13 +321,6 @@ __global__ void k_gather_cid(const uint32_t *__restrict__ order, const int32_t *
         cid[p] = pos[order[p]];
 }
 
-__global__ void k_gather_i32(const int32_t *__restrict__ src, const uint32_t *__restrict__ idx,
-                             int64_t n, int32_t *out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = src[idx[i]];
-}
-
 // ---- per-scene pair counts and caps
 __global__ void k_scene_pairs(int64_t n, const int32_t *__restrict__ mate,
                               const int32_t *__restrict__ cid, const int32_t *__restrict__ sid,
