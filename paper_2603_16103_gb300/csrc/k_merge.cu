@@ -90,13 +90,12 @@ __device__ __forceinline__ T diag2(const T *A) {
     return A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
 }
 
-// FP64 1/sqrt(x) for x of order one or larger than FLT_MIN: an FP32 estimate
-// refined by two Newton steps.
+// 1/sqrt(x) for x of order one (a squared norm of a nearly unit vector): an
+// FP32 estimate (relative error below 2^-22) refined by one FP64 Newton step,
+// which leaves a relative error below 1e-13.
 __device__ __forceinline__ double rsqrt64(double x) {
-    double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    y = y * (1.5 - 0.5 * x * y * y);
-    return y;
+    const double y = (double)rsqrtf((float)x);
+    return y * (1.5 - 0.5 * x * y * y);
 }
 
 __device__ __forceinline__ void quat_rot64(const float *q, double *R) {
@@ -108,18 +107,26 @@ __device__ __forceinline__ void quat_rot64(const float *q, double *R) {
     R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
 }
 
-// One FP64 Jacobi sweep on a nearly diagonal symmetric B, V <- V J.  When the
+// One FP64 Jacobi sweep on a nearly diagonal symmetric B (upper triangle
+// b[0..5] = 00 01 02 11 12 22), V <- V J, B <- J^T B J.  When the
 // off-diagonal entry is tiny against the diagonal gap the rotation is the
 // small-angle one, t = b_pq / (b_qq - b_pp) (in FP32: its relative error only
 // scales the residual), c = 1 - t^2/2, s = t c, orthogonal to O(t^4); other
-// rotations use the exact formula in FP64.
-__device__ __forceinline__ void refine_sweep64(double *B, double *V) {
+// rotations use the exact formula in FP64.  Only the entries the rotation
+// changes are updated: b_pp, b_qq, b_rp, b_rq (r the third index).
+__device__ __forceinline__ void refine_sweep64(double *b, double *V) {
 #pragma unroll
     for (int pq = 0; pq < 3; pq++) {
-        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
-        const double apq = B[3 * p + q];
+        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2, r = 3 - p - q;
+        // upper-triangle slots of (p,p), (q,q), (p,q), (r,p), (r,q)
+        const int ipp = p == 0 ? 0 : 3, iqq = q == 1 ? 3 : 5;
+        const int ipq = pq == 0 ? 1 : (pq == 1 ? 2 : 4);
+        const int irp = pq == 0 ? 2 : 1;  // (2,0) / (1,0) / (0,1)
+        const int irq = pq == 2 ? 2 : 4;  // (2,1) / (1,2) / (0,2)
+        const double apq = b[ipq];
         if (apq == 0.0) continue;
-        const double diff = B[3 * q + q] - B[3 * p + p];
+        const double app = b[ipp], aqq = b[iqq];
+        const double diff = aqq - app;
         double c, s;
         if (fabs(apq) < 1e-4 * fabs(diff)) {
             const double t = (double)((float)apq / (float)diff);
@@ -131,19 +138,13 @@ __device__ __forceinline__ void refine_sweep64(double *B, double *V) {
             c = 1.0 / sqrt(1.0 + t * t);
             s = t * c;
         }
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const double bkp = B[3 * k + p], bkq = B[3 * k + q];
-            B[3 * k + p] = c * bkp - s * bkq;
-            B[3 * k + q] = s * bkp + c * bkq;
-        }
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const double bpk = B[3 * p + k], bqk = B[3 * q + k];
-            B[3 * p + k] = c * bpk - s * bqk;
-            B[3 * q + k] = s * bpk + c * bqk;
-        }
-        B[3 * p + q] = B[3 * q + p] = 0.0;
+        const double cc = c * c, ss = s * s, cs2 = 2.0 * c * s;
+        const double arp = b[irp], arq = b[irq];
+        b[ipp] = cc * app - cs2 * apq + ss * aqq;
+        b[iqq] = ss * app + cs2 * apq + cc * aqq;
+        b[ipq] = 0.0;
+        b[irp] = c * arp - s * arq;
+        b[irq] = s * arp + c * arq;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const double vkp = V[3 * k + p], vkq = V[3 * k + q];
@@ -151,6 +152,22 @@ __device__ __forceinline__ void refine_sweep64(double *B, double *V) {
             V[3 * k + q] = s * vkp + c * vkq;
         }
     }
+}
+
+// Sigma = R diag(s2) R^T in FP64 from an FP64 rotation and FP32 squared
+// scales, upper triangle (00 01 02 11 12 22)
+__device__ __forceinline__ void rot_cov6_64(const double *R, const float *s2, double *S6) {
+    double Rs[9];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) Rs[3 * a + k] = R[3 * a + k] * (double)s2[k];
+    int idx = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = a; b < 3; b++, idx++)
+            S6[idx] = Rs[3 * a] * R[3 * b] + Rs[3 * a + 1] * R[3 * b + 1] + Rs[3 * a + 2] * R[3 * b + 2];
 }
 
 // canonical eigen form + quaternion (w >= 0)
@@ -174,9 +191,13 @@ __device__ void canonical_quat(double *lam, double *V, float *q_out) {
         if (V[3 * best + cidx] < 0)
             for (int r = 0; r < 3; r++) V[3 * r + cidx] = -V[3 * r + cidx];
     }
-    double det = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
-                 V[2] * (V[3] * V[7] - V[4] * V[6]);
-    if (det < 0)
+    // det V = +-1: its sign in FP32
+    float Vf[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) Vf[k] = (float)V[k];
+    const float det = Vf[0] * (Vf[4] * Vf[8] - Vf[5] * Vf[7]) - Vf[1] * (Vf[3] * Vf[8] - Vf[5] * Vf[6]) +
+                      Vf[2] * (Vf[3] * Vf[7] - Vf[4] * Vf[6]);
+    if (det < 0.f)
         for (int r = 0; r < 3; r++) V[3 * r + 2] = -V[3 * r + 2];
     // rotation matrix -> quaternion (FP32), pivot on the largest of trace and diagonal
     float R[9];
@@ -322,23 +343,24 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
         // FP64 finish: Sigma_m assembled in FP64 (rotations normalised in FP64,
         // s^2 and pi taken from their FP32 values), rotated into the
         // re-orthonormalised FP32 eigenbasis, then one FP64 Jacobi sweep.
-        double Ri64[9], Rj64[9], s2i64[3], s2j64[3], Si64[9], Sj64[9], S64[9];
+        double Ri64[9], Rj64[9], Si6[6], Sj6[6], S64[9];
         quat_rot64(qi, Ri64);
         quat_rot64(qj, Rj64);
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            s2i64[a] = (double)s2i[a];
-            s2j64[a] = (double)s2j[a];
-        }
-        rot_cov<double>(Ri64, s2i64, Si64);
-        rot_cov<double>(Rj64, s2j64, Sj64);
-        const double pid = (double)pi, pjd = (double)pj;
+        rot_cov6_64(Ri64, s2i, Si6);
+        rot_cov6_64(Rj64, s2j, Sj6);
+        const double pid = (double)pi, pjd = (double)pj, ppd64 = pid * pjd;
         const double dd[3] = {(double)mi[0] - mj[0], (double)mi[1] - mj[1], (double)mi[2] - mj[2]};
+        {
+            int idx = 0;
 #pragma unroll
-        for (int a = 0; a < 3; a++)
+            for (int a = 0; a < 3; a++)
 #pragma unroll
-            for (int b = 0; b < 3; b++)
-                S64[3 * a + b] = pid * Si64[3 * a + b] + pjd * Sj64[3 * a + b] + pid * pjd * dd[a] * dd[b];
+                for (int b = a; b < 3; b++, idx++) {
+                    const double v = pid * Si6[idx] + pjd * Sj6[idx] + ppd64 * dd[a] * dd[b];
+                    S64[3 * a + b] = v;
+                    S64[3 * b + a] = v;
+                }
+        }
         // Gram-Schmidt of the FP32 eigenvectors (columns of V)
         double Q[9];
 #pragma unroll
@@ -354,23 +376,23 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
             Q[5] = Q[6] * Q[1] - Q[0] * Q[7];
             Q[8] = Q[0] * Q[4] - Q[3] * Q[1];
         }
-        // B = Q^T S64 Q (nearly diagonal)
-        double T[9], B[9];
+        // B = Q^T S64 Q (nearly diagonal), upper triangle
+        double T[9], B[6];
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int b = 0; b < 3; b++)
                 T[3 * a + b] = S64[3 * a] * Q[b] + S64[3 * a + 1] * Q[3 + b] + S64[3 * a + 2] * Q[6 + b];
+        {
+            int idx = 0;
 #pragma unroll
-        for (int a = 0; a < 3; a++)
+            for (int a = 0; a < 3; a++)
 #pragma unroll
-            for (int b = a; b < 3; b++) {
-                const double v = Q[a] * T[b] + Q[3 + a] * T[3 + b] + Q[6 + a] * T[6 + b];
-                B[3 * a + b] = v;
-                B[3 * b + a] = v;
-            }
+                for (int b = a; b < 3; b++, idx++)
+                    B[idx] = Q[a] * T[b] + Q[3 + a] * T[3 + b] + Q[6 + a] * T[6 + b];
+        }
         refine_sweep64(B, Q);
-        lam[0] = B[0]; lam[1] = B[4]; lam[2] = B[8];
+        lam[0] = B[0]; lam[1] = B[3]; lam[2] = B[5];
 #pragma unroll
         for (int k = 0; k < 9; k++) V64[k] = Q[k];
     } else {
