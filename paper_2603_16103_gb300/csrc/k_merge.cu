@@ -117,8 +117,8 @@ __device__ __forceinline__ void quat_rot64(const float *q, double *R) {
 __device__ __forceinline__ void refine_sweep64(double *b, double *V) {
 #pragma unroll
     for (int pq = 0; pq < 3; pq++) {
-        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2, r = 3 - p - q;
-        // upper-triangle slots of (p,p), (q,q), (p,q), (r,p), (r,q)
+        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+        // upper-triangle slots of (p,p), (q,q), (p,q), (r,p), (r,q), r = 3 - p - q
         const int ipp = p == 0 ? 0 : 3, iqq = q == 1 ? 3 : 5;
         const int ipq = pq == 0 ? 1 : (pq == 1 ? 2 : 4);
         const int irp = pq == 0 ? 2 : 1;  // (2,0) / (1,0) / (0,1)
