@@ -29,21 +29,21 @@ __global__ void k_match_init(int64_t n, int32_t *mate, int32_t *cand) {
 }
 
 // Re-scan the incident edges of free vertices whose pointer is unknown or
-// stale: the k slots of the vertex, then its non-mutual in-slots.
-__device__ __forceinline__ void consider(int32_t u, float cst, uint32_t cv,
-                                         const int32_t *__restrict__ cid,
-                                         const int32_t *__restrict__ mate, int32_t &best,
-                                         uint32_t &bk, uint32_t &blo, uint32_t &bhi) {
-    if (mate[u] != -1) return;
-    uint32_t k = cost_order_bits(cst);
-    uint32_t cu = cid_of(cid, u);
-    uint32_t lo = cv < cu ? cv : cu, hi = cv < cu ? cu : cv;
-    bool better = best < 0 || k < bk || (k == bk && (lo < blo || (lo == blo && hi < bhi)));
-    if (better) {
+// stale: the k slots of the vertex, then its non-mutual in-slots.  All edges
+// considered here contain v, and for a fixed v the order of (lo, hi) is the
+// order of the other endpoint's canonical id (a lower neighbour gives a
+// lower lo; two higher neighbours share lo = v).  Ties on cost are therefore
+// broken by that id alone, loaded only when a tie occurs.
+__device__ __forceinline__ void consider(int32_t u, float cst, const int32_t *__restrict__ cid,
+                                         const int32_t *__restrict__ mate, bool all_free,
+                                         int32_t &best, uint32_t &bk) {
+    if (!all_free && mate[u] != -1) return;
+    const uint32_t k = cost_order_bits(cst);
+    if (best < 0 || k < bk) {
         best = u;
         bk = k;
-        blo = lo;
-        bhi = hi;
+    } else if (k == bk && cid_of(cid, u) < cid_of(cid, best)) {
+        best = u;
     }
 }
 
@@ -61,15 +61,15 @@ __global__ void k_match_scan(const int32_t *__restrict__ wl, const int32_t *__re
         int32_t c = cand[v];
         if (c == -1) continue;                  // no free neighbour: stays single
         if (c >= 0 && mate[c] == -1) continue;  // target still free: still the best
-        const uint32_t cv = cid_of(cid, (int32_t)v);
+        const bool all_free = wl == nullptr;  // round 0: no vertex is matched yet
         int32_t best = -1;
-        uint32_t bk = 0xffffffffu, blo = 0xffffffffu, bhi = 0xffffffffu;
+        uint32_t bk = 0xffffffffu;
         const int64_t base = v * kk;
         for (int t = 0; t < kk; t++)
-            consider(nbr[base + t], cost_slot[base + t], cv, cid, mate, best, bk, blo, bhi);
+            consider(nbr[base + t], cost_slot[base + t], cid, mate, all_free, best, bk);
         for (int32_t r = rev_ptr[v]; r < rev_ptr[v + 1]; r++) {
             int32_t s = rev[r];
-            consider(s / kk, cost_slot[s], cv, cid, mate, best, bk, blo, bhi);
+            consider(s / kk, cost_slot[s], cid, mate, all_free, best, bk);
         }
         cand[v] = best;
         candkey[v] = bk;
@@ -82,18 +82,32 @@ __global__ void k_match_pair(const int32_t *__restrict__ wl, const int32_t *__re
                              int64_t n_all, const int32_t *__restrict__ cand, int32_t *mate,
                              int32_t *round_count, int32_t *wl_next, int32_t *wl_next_count) {
     const int64_t cnt = wl ? (int64_t)*wl_count : n_all;
+    const int lane = threadIdx.x & 31;
     int found = 0;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < cnt;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = wl ? (int64_t)wl[idx] : idx;
-        if (mate[v] != -1) continue;
-        const int32_t u = cand[v];
-        if (u < 0) continue;
-        if (cand[u] == (int32_t)v) {
-            mate[v] = u;
-            if (v < u) found++;
-        } else {
-            wl_next[atomicAdd(wl_next_count, 1)] = (int32_t)v;
+    // warp-uniform loop: one worklist atomic per warp and iteration
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < cnt;
+         b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = b0 + threadIdx.x;
+        bool push = false;
+        int32_t v = -1;
+        if (idx < cnt) {
+            v = wl ? wl[idx] : (int32_t)idx;
+            const int32_t u = mate[v] == -1 ? cand[v] : -1;
+            if (u >= 0) {
+                if (cand[u] == v) {
+                    mate[v] = u;
+                    if (v < u) found++;
+                } else {
+                    push = true;
+                }
+            }
+        }
+        const unsigned pm = __ballot_sync(FULL_MASK, push);
+        if (pm) {
+            int32_t at = 0;
+            if (lane == __ffs(pm) - 1) at = atomicAdd(wl_next_count, __popc(pm));
+            at = __shfl_sync(FULL_MASK, at, __ffs(pm) - 1);
+            if (push) wl_next[at + __popc(pm & ((1u << lane) - 1u))] = v;
         }
     }
 #pragma unroll
