@@ -83,10 +83,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2603_16103_gb300 import replicas
+    return replicas.env()
 
 
 def peaks():
@@ -329,15 +327,12 @@ def serving_form(B, torch, synth, args):
 
 def main():
     args = parse()
+    from paper_2603_16103_gb300 import replicas
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
+    replicas.init()
     if args.impl == "reference":
         reference_arm(args, ws, rank)
-        if ws > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
+        replicas.finish()
         return
 
     import numpy as np
@@ -374,9 +369,7 @@ def main():
     B.ngs_profile_enable(ctx.handle, True)
     clocks = ClockSampler(local)
     clocks.start()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     total_ms = 0.0
     launches = 0
@@ -392,18 +385,13 @@ def main():
         total_ms += ev0.elapsed_time(ev1)
         launches += stats["gpu_launches"]
     torch.cuda.synchronize()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    replicas.barrier()
     clk = clocks.stop()
     B.ngs_profile_enable(ctx.handle, False)
     prof = B.ngs_profile(ctx.handle)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(total_ms)
     ms_per_step = total_ms / args.steps
-    value = ws * n0 * args.steps / (total_ms / 1e3)
+    value = replicas.whole_job_rate(n0 * args.steps, total_ms / 1e3)
 
     # ---- roofline of the dominant kernel (event-timed live above)
     pk, src = peaks()
@@ -458,11 +446,13 @@ def main():
                 e2e_t += dt
         h2d = n0 * SPLAT_BYTES
         d2h = host.n * SPLAT_BYTES
-        e2e = {"value": ws * n0 * reps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        replicas.barrier()
+        e2e = {"value": replicas.whole_job_rate(n0 * reps, e2e_t), "unit": UNIT,
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
     forms = {}
-    if not args.no_forms:
+    if not args.no_forms and ws == 1:  # the forms are measured on one GPU
         forms["batched"] = batched_form(B, torch, synth, args)
         forms["serving"] = serving_form(B, torch, synth, args)
 
@@ -489,9 +479,7 @@ def main():
         out.update(forms)
         print(json.dumps(out), flush=True)
     ctx.close()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    replicas.finish()
 
 
 if __name__ == "__main__":
