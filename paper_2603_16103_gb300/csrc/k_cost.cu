@@ -13,8 +13,8 @@
 // keeps FP32 cancellation small; q_c(x_c) = |z|^2 exactly.
 // Mode 0 averages pi g(x_i) + (1-pi) g(x_j) (the component draw integrated
 // out); mode 1 takes g(x_i) if u_s < pi else g(x_j).
-// A merged covariance whose FP32 Cholesky pivots are tiny relative to its
-// diagonal (near-degenerate) is redone entirely in FP64.
+// A merged covariance whose FP32 Cholesky pivots fall below 1e-2 of the
+// matching diagonal entries (near-degenerate) is redone entirely in FP64.
 #include "ngs_device.cuh"
 #include "ngs_internal.h"
 
@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(256, 3)
                 float lg, float la, int policy, const float *__restrict__ xyz,
                 const float *__restrict__ ls, const float *__restrict__ rot,
                 const float *__restrict__ logit, float *__restrict__ cost_slot,
-                float *__restrict__ cost_out, unsigned long long *fp64_count) {
+                float *__restrict__ cost_out, unsigned long long *fp64_count,
+                int2 *__restrict__ fp64_list) {
     const float zz0 = zs[0] * zs[0] + zs[1] * zs[1] + zs[2] * zs[2];
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -307,7 +308,9 @@ __global__ void __launch_bounds__(256, 3)
         const float t22 = Sm[5] - L[3] * L[3] - L[4] * L[4];
         L[5] = sqrtf(fmaxf(t22, 0.f));
         il[2] = 1.0f / L[5];
-        bool flag = !(Sm[0] > 0.f) || !(t11 > 1e-5f * Sm[3]) || !(t22 > 1e-5f * Sm[5]);
+        // FP32 loses about eps32 / (pivot / diagonal) of the log-determinant: a
+        // ratio below 1e-2 (error above ~6e-6) sends the edge to FP64
+        bool flag = !(Sm[0] > 0.f) || !(t11 > 1e-2f * Sm[3]) || !(t22 > 1e-2f * Sm[5]);
         if (policy == 1) flag = flag || Ri.g(5).w < 1e-3f || Rj.g(5).w < 1e-3f;
         float dgeo;
         if (!flag) {
@@ -351,12 +354,43 @@ __global__ void __launch_bounds__(256, 3)
             }
             dgeo = acc / (float)S;
         } else {
-            dgeo = (float)dgeo_fp64(xyz, ls, rot, logit, i, j, S, zs, us, mode);
+            dgeo = 0.f;  // evaluated in FP64 by k_edge_cost64 from the list below
         }
-        unsigned fm = __ballot_sync(__activemask(), flag);
-        if (fm && (threadIdx.x & 31) == __ffs(fm) - 1) atomicAdd(fp64_count, (unsigned long long)__popc(fm));
+        // flagged edges go to the FP64 list (one atomic per warp)
+        const unsigned am = __activemask();
+        const unsigned fm = __ballot_sync(am, flag);
+        if (fm) {
+            const int lane = threadIdx.x & 31, first = __ffs(fm) - 1;
+            unsigned long long at = 0;
+            if (lane == first) at = atomicAdd(fp64_count, (unsigned long long)__popc(fm));
+            at = __shfl_sync(am, at, first);
+            if (flag) fp64_list[at + __popc(fm & ((1u << lane) - 1u))] = make_int2((int)e, __float_as_int(dapp));
+        }
+        if (flag) continue;
         const float c = lg * dgeo + la * dapp;
         cost_slot[sl] = c;
+        if (er.w >= 0) cost_slot[er.w] = c;
+        if (cost_out) cost_out[e] = c;
+    }
+}
+
+// FP64 evaluation of the flagged edges: D_geo in FP64, D_app as computed in
+// FP32 by the main kernel.
+__global__ void k_edge_cost64(const int2 *__restrict__ list, const unsigned long long *__restrict__ count,
+                              const int4 *__restrict__ erec, const float *__restrict__ zs,
+                              const float *__restrict__ us, int S, int mode, float lg, float la,
+                              const float *__restrict__ xyz, const float *__restrict__ ls,
+                              const float *__restrict__ rot, const float *__restrict__ logit,
+                              float *__restrict__ cost_slot, float *__restrict__ cost_out) {
+    const int64_t cnt = (int64_t)*count;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int2 it = list[t];
+        const int64_t e = it.x;
+        const int4 er = erec[e];
+        const float dgeo = (float)dgeo_fp64(xyz, ls, rot, logit, er.y, er.z, S, zs, us, mode);
+        const float c = lg * dgeo + la * __int_as_float(it.y);
+        cost_slot[er.x] = c;
         if (er.w >= 0) cost_slot[er.w] = c;
         if (cost_out) cost_out[e] = c;
     }
@@ -391,6 +425,7 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
     launch(c, "cost_prep", dim3(grid_stride_blocks(c, s.n, 256, 8)), dim3(256), 0, k_prep, s.xyz,
            s.ls, s.rot, s.logit, s.n, (const float *)zs, rec);
     unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c, c->b_status, 64);
+    int2 *list = ws<int2>(c, c->b_fp64list, m);
     NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, c->st));
     launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0, k_edge_cost,
            (const int4 *)(lex ? g.erec_lex : g.erec), m, (const float *)rec, (const float *)s.sh,
@@ -398,7 +433,15 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
            (const float *)(zs + 3 * S), S, c->prm.cost_mode, c->prm.lambda_geo,
            c->prm.lambda_app, c->prm.fp64_policy, (const float *)s.xyz, (const float *)s.ls,
            (const float *)s.rot, (const float *)s.logit, g.cost_slot, lex ? cost_out : nullptr,
-           cnt);
+           cnt, list);
+    // the flagged edges (few: near-degenerate merged covariances) in FP64; the
+    // grid covers the worst case, threads past the device count exit at once
+    launch(c, "edge_cost64", dim3(grid_stride_blocks(c, m, 128, 2)), dim3(128), 0, k_edge_cost64,
+           (const int2 *)list, (const unsigned long long *)cnt,
+           (const int4 *)(lex ? g.erec_lex : g.erec), (const float *)zs,
+           (const float *)(zs + 3 * S), S, c->prm.cost_mode, c->prm.lambda_geo,
+           c->prm.lambda_app, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
+           (const float *)s.logit, g.cost_slot, lex ? cost_out : nullptr);
     NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin + 1, cnt, 8, cudaMemcpyDeviceToHost, c->st));
 }
 

@@ -239,7 +239,7 @@ static void release_all(ngs_ctx *c) {
                       &c->b_cand, &c->b_candkey, &c->b_counts, &c->b_sel, &c->b_role, &c->b_keep,
                       &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
                       &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2,
-                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc};
+                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc, &c->b_fp64list};
     for (DevBuf *b : bufs) ws_free(c, *b);
     for (int k = 0; k < 5; k++) {
         ws_free(c, c->b_sA[k]);

@@ -113,6 +113,7 @@ struct ngs_ctx {
     DevBuf b_pairs, b_partner, b_nbr2, b_lexrec, b_sel2, b_cflag2, b_knnsc;
     DevBuf b_host_dev[5];        // device staging for ngs_simplify_host
     DevBuf b_sC[5];              // third splat array set (several scenes at once)
+    DevBuf b_fp64list;           // edges whose cost is evaluated in FP64
     DevBuf b_eng[32];            // per-scene tables and scratch of the multi-scene engine
 
     // pinned host scratch

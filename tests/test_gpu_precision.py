@@ -71,6 +71,12 @@ def test_precision_report(ngs, policy):
         rep = attr_errors(cur, p, ds.numpy())
         rep["edge_cost_rel"] = {"max": float(cerr.max()), "mean": float(cerr.mean()),
                                 "p99.9": float(np.quantile(cerr, 0.999))}
+        w = int(np.argmax(cerr))
+        lw, hw = int(lo[w]), int(hi[w])
+        rep["worst_edge"] = {"lo": lw, "hi": hw, "gpu": float(cost[w]), "fp64": float(rc[w]),
+                             "log_scale_lo": cur.log_scale[lw].tolist(),
+                             "log_scale_hi": cur.log_scale[hw].tolist(),
+                             "dist": float(np.linalg.norm(cur.xyz[lw].astype(np.float64) - cur.xyz[hw]))}
         rep["policy"] = policy
         rep["scene"] = "patches200k (5% degenerate, 1% duplicate centres), pass 0"
         print("PRECISION " + json.dumps(rep))
