@@ -280,6 +280,32 @@ int ngs_release_workspace(ngs_ctx *ctx);
  * the work queued on its current stream has finished.  Errors: CUDA. */
 int ngs_set_stream(ngs_ctx *ctx, void *stream);
 
+/* ---- performance tuning ----
+ *
+ * Parameters that change speed, never results: the kNN search is exact for
+ * any of them and the edge costs do not depend on the grid shape.  A ctx
+ * starts with the defaults; ngs_autotune measures candidates on a sample. */
+typedef struct {
+    int32_t knn_block_min;       /* points the kNN 3x3x3 cell block must hold when the
+                                    search picks its grid level (16..1024), default 64 */
+    int32_t cells_per_point;     /* density of the kNN cell table: 1, 2, 4 or 8 cells
+                                    per point (at most 8^9 cells), default 4 */
+    int32_t cost_blocks_per_sm;  /* edge-cost grid: 256-thread blocks per SM (1..64),
+                                    default 8 */
+} ngs_tuning;
+
+void ngs_default_tuning(ngs_tuning *tuning);
+int ngs_get_tuning(ngs_ctx *ctx, ngs_tuning *tuning);
+/* Errors: INVALID_ARG (a field out of range). */
+int ngs_set_tuning(ngs_ctx *ctx, const ngs_tuning *tuning);
+/* Time the kNN graph stage for knn_block_min in {48, 64, 96} x cells_per_point
+ * in {2, 4, 8}, then the edge-cost stage for cost_blocks_per_sm in {4, 8, 12},
+ * on `sample` (device splats, not modified; n >= 2), twice each with CUDA
+ * events on the ctx stream; keep the fastest (stage by stage) in the ctx.
+ * best (may be NULL) receives it, ms_best (may be NULL) the time of the two
+ * stages under it.  Synchronises.  Errors: INVALID_ARG, OOM, CUDA. */
+int ngs_autotune(ngs_ctx *ctx, const ngs_splats *sample, ngs_tuning *best, double *ms_best);
+
 /* ---- serving form ----
  *
  * A request loop for simplification jobs of different sizes and targets.

@@ -76,6 +76,14 @@ class ngs_stats(ctypes.Structure):
                 "eig_floor_hits": self.eig_floor_hits, "gpu_launches": self.gpu_launches}
 
 
+class ngs_tuning(ctypes.Structure):
+    _fields_ = [("knn_block_min", ctypes.c_int32), ("cells_per_point", ctypes.c_int32),
+                ("cost_blocks_per_sm", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class ngs_server_config(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("group_small", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("bytes_per_splat", ctypes.c_int64),
@@ -139,6 +147,11 @@ _SIGS = {
     "ngs_workspace_bytes": (ctypes.c_int64, [_P]),
     "ngs_release_workspace": (ctypes.c_int, [_P]),
     "ngs_set_stream": (ctypes.c_int, [_P, _P]),
+    "ngs_default_tuning": (None, [ctypes.POINTER(ngs_tuning)]),
+    "ngs_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ngs_tuning)]),
+    "ngs_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ngs_tuning)]),
+    "ngs_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), ctypes.POINTER(ngs_tuning),
+                                    ctypes.POINTER(ctypes.c_double)]),
     "ngs_server_default_config": (None, [ctypes.POINTER(ngs_server_config)]),
     "ngs_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ngs_params),
                                          ctypes.POINTER(ngs_server_config)]),
@@ -402,6 +415,26 @@ class Context:
         ds.n = s.n
         return st
 
+    def tuning(self) -> dict:
+        t = ngs_tuning()
+        _check(load().ngs_get_tuning(_P(self.handle), ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = ngs_tuning()
+        _check(load().ngs_get_tuning(_P(self.handle), ctypes.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _check(load().ngs_set_tuning(_P(self.handle), ctypes.byref(t)))
+
+    def autotune(self, sample: DeviceSplats):
+        """Measure the candidate tunings on `sample`; returns (tuning dict, ms)."""
+        t, ms = ngs_tuning(), ctypes.c_double()
+        s = sample.struct()
+        _check(load().ngs_autotune(_P(self.handle), ctypes.byref(s), ctypes.byref(t),
+                                   ctypes.byref(ms)))
+        return t.as_dict(), ms.value
+
     def batch_simplify(self, scenes, targets) -> dict:
         """Simplify several DeviceSplats in one call (each in place)."""
         structs = [ds.struct() for ds in scenes]
@@ -433,6 +466,12 @@ def _wrap_i32(ptr, count, device):
 
 
 # ---------------------------------------------------------------- serving form
+def ngs_default_tuning() -> ngs_tuning:
+    t = ngs_tuning()
+    load().ngs_default_tuning(ctypes.byref(t))
+    return t
+
+
 def ngs_server_default_config() -> ngs_server_config:
     c = ngs_server_config()
     load().ngs_server_default_config(ctypes.byref(c))

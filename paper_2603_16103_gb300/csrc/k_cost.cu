@@ -427,7 +427,8 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
     unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c, c->b_status, 64);
     int2 *list = ws<int2>(c, c->b_fp64list, m);
     NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, c->st));
-    launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0, k_edge_cost,
+    launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, c->tune.cost_blocks_per_sm)), dim3(256), 0,
+           k_edge_cost,
            (const int4 *)(lex ? g.erec_lex : g.erec), m, (const float *)rec, (const float *)s.sh,
            s.F, (const float *)zs,
            (const float *)(zs + 3 * S), S, c->prm.cost_mode, c->prm.lambda_geo,

@@ -209,7 +209,6 @@ __device__ __forceinline__ uint32_t interleave(uint32_t x, uint32_t y, uint32_t 
 }
 
 constexpr int KNN_QCAP = 16;   // per-lane candidate queue (shared memory)
-constexpr int KNN_BLOCK_MIN = 64;
 constexpr int KNN_BLOCK = 256;
 
 // Points in the 3x3x3 block of level-l cells around cell (cx, cy, cz).
@@ -297,7 +296,7 @@ __global__ void __launch_bounds__(KNN_BLOCK, 3)
                const uint32_t *__restrict__ sidx, const int32_t *__restrict__ ssid, int64_t n,
                const int32_t *__restrict__ Tall, const int32_t *__restrict__ lts,
                const int64_t *__restrict__ toff, const float *__restrict__ frames, int keff,
-               int out_by_cid, int32_t *__restrict__ nbr) {
+               int out_by_cid, int block_min, int32_t *__restrict__ nbr) {
     __shared__ uint64_t queue_all[KNN_BLOCK / 32][KNN_QCAP][32];
     const int lane = threadIdx.x & 31;
     uint64_t(*queue)[32] = queue_all[threadIdx.x >> 5];
@@ -319,13 +318,13 @@ __global__ void __launch_bounds__(KNN_BLOCK, 3)
     int l = lt;
     if (valid) {
         int bc = block_count(g, l, qx >> (10 - l), qy >> (10 - l), qz >> (10 - l));
-        while (l > 1 && bc < KNN_BLOCK_MIN) {
+        while (l > 1 && bc < block_min) {
             l--;
             bc = block_count(g, l, qx >> (10 - l), qy >> (10 - l), qz >> (10 - l));
         }
-        if (bc > 6 * KNN_BLOCK_MIN && l < 10) {
+        if (bc > 6 * block_min && l < 10) {
             int b2 = block_count(g, l + 1, qx >> (9 - l), qy >> (9 - l), qz >> (9 - l));
-            if (b2 >= KNN_BLOCK_MIN) l++;
+            if (b2 >= block_min) l++;
         }
     }
     const int sh = 10 - l;
@@ -448,9 +447,9 @@ void gather_points(ngs_ctx *c, const float *xyz, const int32_t *cid, const uint3
            xyz, cid, order, n, pts);
 }
 
-int knn_table_level(int64_t n) {
+int knn_table_level(int64_t n, int cells_per_point) {
     int lt = 1;
-    while (lt < 9 && ((int64_t)1 << (3 * lt)) < 4 * n) lt++;
+    while (lt < 9 && ((int64_t)1 << (3 * lt)) < (int64_t)cells_per_point * n) lt++;
     return lt;
 }
 
@@ -478,7 +477,7 @@ void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
     }
     hoff[0] = 0;
     for (int s = 0; s < S; s++) {
-        hlt[s] = knn_table_level(in.scene_n[s]);
+        hlt[s] = knn_table_level(in.scene_n[s], c->tune.cells_per_point);
         hoff[s + 1] = hoff[s] + ((int64_t)1 << (3 * hlt[s])) + 1;
     }
     const int64_t tlen = hoff[S];
@@ -497,7 +496,7 @@ void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
 #define KNN_LAUNCH(KM, NAME)                                                                   \
     launch(c, NAME, dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<KM>, in.pts, in.scode, in.sidx,   \
            in.ssid, n, cT, (const int32_t *)dlt, (const int64_t *)doff, in.frames, k_eff,      \
-           in.out_by_cid, nbr)
+           in.out_by_cid, c->tune.knn_block_min, nbr)
     if (k_eff <= 4) KNN_LAUNCH(4, "knn_k4");
     else if (k_eff <= 8) KNN_LAUNCH(8, "knn_k8");
     else if (k_eff <= 16) KNN_LAUNCH(16, "knn_k16");

@@ -610,6 +610,102 @@ extern "C" int64_t ngs_launch_count(ngs_ctx *c) { return c ? c->launches : 0; }
 
 extern "C" int64_t ngs_workspace_bytes(ngs_ctx *c) { return c ? c->ws_bytes : 0; }
 
+extern "C" void ngs_default_tuning(ngs_tuning *t) {
+    if (!t) return;
+    const Tuning d;
+    t->knn_block_min = d.knn_block_min;
+    t->cells_per_point = d.cells_per_point;
+    t->cost_blocks_per_sm = d.cost_blocks_per_sm;
+}
+
+extern "C" int ngs_get_tuning(ngs_ctx *c, ngs_tuning *t) {
+    if (!c || !t) return NGS_ERR_INVALID_ARG;
+    t->knn_block_min = c->tune.knn_block_min;
+    t->cells_per_point = c->tune.cells_per_point;
+    t->cost_blocks_per_sm = c->tune.cost_blocks_per_sm;
+    return NGS_OK;
+}
+
+extern "C" int ngs_set_tuning(ngs_ctx *c, const ngs_tuning *t) {
+    if (!c || !t) return NGS_ERR_INVALID_ARG;
+    const int cpp = t->cells_per_point;
+    if (t->knn_block_min < 16 || t->knn_block_min > 1024 ||
+        !(cpp == 1 || cpp == 2 || cpp == 4 || cpp == 8) || t->cost_blocks_per_sm < 1 ||
+        t->cost_blocks_per_sm > 64) {
+        ngs_set_error("ngs_set_tuning: field out of range");
+        return NGS_ERR_INVALID_ARG;
+    }
+    c->tune.knn_block_min = t->knn_block_min;
+    c->tune.cells_per_point = cpp;
+    c->tune.cost_blocks_per_sm = t->cost_blocks_per_sm;
+    return NGS_OK;
+}
+
+extern "C" int ngs_autotune(ngs_ctx *c, const ngs_splats *s, ngs_tuning *best, double *ms_best) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    check_splats(s, "ngs_autotune");
+    if (s->n < 2) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_autotune: the sample needs at least 2 splats");
+    cudaEvent_t e0, e1;
+    NGS_CHECK_CUDA(cudaEventCreate(&e0));
+    NGS_CHECK_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](auto &&fn) {
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 2; rep++) {
+            NGS_CHECK_CUDA(cudaEventRecord(e0, c->st));
+            fn();
+            NGS_CHECK_CUDA(cudaEventRecord(e1, c->st));
+            NGS_CHECK_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            NGS_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            best_ms = ms < best_ms ? ms : best_ms;
+        }
+        return best_ms;
+    };
+    try {
+        // stage 1: the kNN graph (Morton sort, cell table, search, edges)
+        const int bms[3] = {48, 64, 96}, cpps[3] = {2, 4, 8};
+        float t_graph = 1e30f;
+        Tuning tb = c->tune;
+        for (int bm : bms)
+            for (int cpp : cpps) {
+                c->tune.knn_block_min = bm;
+                c->tune.cells_per_point = cpp;
+                const float t = timed([&] { graph_canonical(c, s); });
+                if (t < t_graph) {
+                    t_graph = t;
+                    tb.knn_block_min = bm;
+                    tb.cells_per_point = cpp;
+                }
+            }
+        c->tune.knn_block_min = tb.knn_block_min;
+        c->tune.cells_per_point = tb.cells_per_point;
+        graph_canonical(c, s);
+        // stage 2: the edge costs on that graph
+        const int cbs[3] = {4, 8, 12};
+        float t_cost = 1e30f;
+        for (int cb : cbs) {
+            c->tune.cost_blocks_per_sm = cb;
+            const float t = timed([&] { edge_costs(c, view_of(s), c->g, 0, false, nullptr); });
+            if (t < t_cost) {
+                t_cost = t;
+                tb.cost_blocks_per_sm = cb;
+            }
+        }
+        c->tune = tb;
+        c->g_valid = false;
+        if (best) ngs_get_tuning(c, best);
+        if (ms_best) *ms_best = (double)t_graph + (double)t_cost;
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    API_END
+}
+
 extern "C" int ngs_set_stream(ngs_ctx *c, void *stream) {
     if (!c) return NGS_ERR_INVALID_ARG;
     API_BEGIN

@@ -89,8 +89,17 @@ struct GraphDev {
     int4 *erec_lex;         // edge records in lexicographic order
 };
 
+// Performance parameters (results do not depend on them), set by
+// ngs_set_tuning or ngs_autotune.
+struct Tuning {
+    int knn_block_min = 64;      // points the kNN 3x3x3 block must hold
+    int cells_per_point = 4;     // cell-table density (cells >= this x points)
+    int cost_blocks_per_sm = 8;  // edge-cost grid, 256-thread blocks per SM
+};
+
 struct ngs_ctx {
     ngs_params prm;
+    Tuning tune;
     cudaStream_t st;
     int device;
     int num_sms;
@@ -210,7 +219,7 @@ struct KnnInput {
     int out_by_cid;
     const int32_t *cid;
 };
-int knn_table_level(int64_t n);
+int knn_table_level(int64_t n, int cells_per_point = 4);
 // neighbours per splat in a pass over n splats: min(max(1, k), n - 1)
 inline int k_eff_of(int64_t n, int k) {
     int ke = k < 1 ? 1 : k;

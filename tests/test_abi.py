@@ -58,7 +58,7 @@ def test_struct_layouts_match_header():
     import tempfile
     from paper_2603_16103_gb300 import binding
     names = ["ngs_splats", "ngs_params", "ngs_graph", "ngs_stats", "ngs_server_config",
-             "ngs_job_info", "ngs_server_stats"]
+             "ngs_job_info", "ngs_server_stats", "ngs_tuning"]
     src = ('#include <stdio.h>\n#include "ngs.h"\nint main(){'
            + "".join(f'printf("%zu\\n", sizeof({n}));' for n in names) + "}\n")
     with tempfile.TemporaryDirectory() as d:
@@ -69,6 +69,12 @@ def test_struct_layouts_match_header():
         sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True,
                                                 check=True).stdout.split()]
     assert sizes == [ctypes.sizeof(getattr(binding, n)) for n in names]
+
+
+def test_default_tuning_host_only():
+    from paper_2603_16103_gb300 import binding
+    t = binding.ngs_default_tuning()
+    assert (t.knn_block_min, t.cells_per_point, t.cost_blocks_per_sm) == (64, 4, 8)
 
 
 def test_product_path_does_not_import_the_oracle():
