@@ -242,9 +242,42 @@ __device__ __forceinline__ int block_count(const GridCtx &g, int l, int32_t cx, 
     return tot;
 }
 
+// Descending bitonic sort of N register keys (static indices only).
+template <int N>
+__device__ __forceinline__ void sort_desc(uint64_t (&a)[N]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint64_t x = a[i], y = a[l];
+                    const bool sw = ((i & k) == 0) ? (x < y) : (x > y);
+                    a[i] = sw ? y : x;
+                    a[l] = sw ? x : y;
+                }
+            }
+}
+
+// Insert each lane's queued keys into its list, in warp-wide rounds.  A lane
+// whose list is still empty (all k_eff = KMAX slots unused) takes its queue
+// by one sorting network instead of one insertion per key: the result is the
+// same list (the queued keys, largest first, padded with the empty marker).
 template <int KMAX>
 __device__ __forceinline__ void flush_queue(uint64_t (*queue)[32], int lane, int &qlen,
-                                            TopK<KMAX> &tk) {
+                                            TopK<KMAX> &tk, int keff) {
+    const bool fresh = keff == KMAX && qlen > 0 && qlen <= KMAX && tk.key[KMAX - 1] == ~0ull;
+    if (fresh) {
+        uint64_t a[KMAX];
+#pragma unroll
+        for (int i = 0; i < KMAX; i++) a[i] = i < qlen ? queue[i][lane] : ~0ull;
+        sort_desc<KMAX>(a);
+#pragma unroll
+        for (int i = 0; i < KMAX; i++) tk.key[i] = a[i];
+        qlen = 0;
+    }
     const int rounds = __reduce_max_sync(FULL_MASK, qlen);
     for (int r = 0; r < rounds; r++) {
         if (r < qlen) {
@@ -379,9 +412,9 @@ __global__ void __launch_bounds__(KNN_BLOCK, 3)
                     if (kk < tk.kth()) queue[qlen++][lane] = kk;
                 }
             }
-            if (__any_sync(FULL_MASK, qlen == KNN_QCAP)) flush_queue<KMAX>(queue, lane, qlen, tk);
+            if (__any_sync(FULL_MASK, qlen == KNN_QCAP)) flush_queue<KMAX>(queue, lane, qlen, tk, keff);
         }
-        flush_queue<KMAX>(queue, lane, qlen, tk);
+        flush_queue<KMAX>(queue, lane, qlen, tk, keff);
         if (active) {
             // distance from q to the outside of the scanned block; a face on
             // the grid boundary has no point beyond it
