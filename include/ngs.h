@@ -292,6 +292,10 @@ typedef struct {
                                     per point (at most 8^9 cells), default 4 */
     int32_t cost_blocks_per_sm;  /* edge-cost grid: 256-thread blocks per SM (1..64),
                                     default 8 */
+    int32_t match_graph;         /* 1: the matching rounds after the first run as one
+                                    CUDA graph (a conditional WHILE node, no host round
+                                    trip per batch of rounds); 0: batches of rounds
+                                    launched and checked from the host.  Default 1 */
 } ngs_tuning;
 
 void ngs_default_tuning(ngs_tuning *tuning);

@@ -174,7 +174,131 @@ __global__ void k_write_pairs(int64_t n, const int32_t *__restrict__ partner,
     }
 }
 
+// Device-side control of the captured rounds.  State (int32): [0] worklist A
+// size, [1] worklist B size, [2] pairs of round A, [3] pairs of round B,
+// [4] rounds done, [5] pairs in all, [6] round limit reached, [7] pairs of
+// round 0.
+constexpr int MS_CNT_A = 0, MS_CNT_B = 1, MS_M_A = 2, MS_M_B = 3, MS_ROUNDS = 4, MS_TOTAL = 5,
+              MS_LIMIT = 6, MS_M0 = 7;
+
+__global__ void k_match_ctl0(cudaGraphConditionalHandle h, int32_t *st) {
+    st[MS_ROUNDS] = 1;
+    st[MS_TOTAL] = st[MS_M0];
+    st[MS_LIMIT] = 0;
+    cudaGraphSetConditional(h, st[MS_M0] > 0 ? 1u : 0u);
+}
+
+// after a body of two rounds: the first round that matched nothing ends the loop
+__global__ void k_match_ctl(cudaGraphConditionalHandle h, int32_t *st, int max_rounds) {
+    const int32_t ma = st[MS_M_A], mb = st[MS_M_B];
+    st[MS_TOTAL] += ma + mb;
+    unsigned more = 0;
+    if (ma == 0) {
+        st[MS_ROUNDS] += 1;
+    } else if (mb == 0) {
+        st[MS_ROUNDS] += 2;
+    } else {
+        st[MS_ROUNDS] += 2;
+        more = st[MS_ROUNDS] < max_rounds ? 1u : 0u;
+        if (!more) st[MS_LIMIT] = 1;
+    }
+    cudaGraphSetConditional(h, more);
+}
+
 }  // namespace
+
+// The rounds after the first as one CUDA graph: a WHILE conditional node
+// whose body runs two rounds (worklist A -> B -> A) and a control kernel that
+// ends the loop on the first round without a new pair.  No host round trip
+// until the loop ends.  Returns false (nothing launched) when the graph
+// cannot be built, in which case the caller runs the rounds from the host.
+static bool match_rounds_graph(ngs_ctx *c, const GraphDev &g, int32_t *mate, int32_t *cand,
+                               uint32_t *candkey, int32_t *const wl[2], int32_t *stt,
+                               unsigned grid, int max_rounds, int32_t *hstate) {
+    const int64_t n = g.n;
+    if (!c->cap_st && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->cap_st = nullptr;
+        return false;
+    }
+    cudaStream_t cs = c->cap_st;  // capture only records; the graph runs on c->st
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = false;
+    do {
+        if (cudaGraphCreate(&graph, 0) != cudaSuccess) break;
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, graph, 0, 0) != cudaSuccess) break;
+        if (cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            break;
+        k_match_ctl0<<<1, 1, 0, cs>>>(h, stt);
+        if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) break;
+        size_t nn = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess || nn != 1) break;
+        cudaGraphNode_t ctl0;
+        if (cudaGraphGetNodes(graph, &ctl0, &nn) != cudaSuccess) break;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        if (cudaGraphAddNode(&cnode, graph, &ctl0, nullptr, 1, &cp) != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            break;
+        cudaMemsetAsync(stt + MS_CNT_B, 0, 3 * sizeof(int32_t), cs);  // B size, both round counts
+        k_match_scan<<<grid, 256, 0, cs>>>(wl[0], stt + MS_CNT_A, n, g.k_eff, g.nbr,
+                                             (const float *)g.cost_slot, (const int32_t *)g.rev_ptr,
+                                             (const int32_t *)g.rev, g.cid, (const int32_t *)mate,
+                                             cand, candkey);
+        k_match_pair<<<grid, 256, 0, cs>>>(wl[0], stt + MS_CNT_A, n, (const int32_t *)cand, mate,
+                                             stt + MS_M_A, wl[1], stt + MS_CNT_B);
+        cudaMemsetAsync(stt + MS_CNT_A, 0, sizeof(int32_t), cs);
+        k_match_scan<<<grid, 256, 0, cs>>>(wl[1], stt + MS_CNT_B, n, g.k_eff, g.nbr,
+                                             (const float *)g.cost_slot, (const int32_t *)g.rev_ptr,
+                                             (const int32_t *)g.rev, g.cid, (const int32_t *)mate,
+                                             cand, candkey);
+        k_match_pair<<<grid, 256, 0, cs>>>(wl[1], stt + MS_CNT_B, n, (const int32_t *)cand, mate,
+                                             stt + MS_M_B, wl[0], stt + MS_CNT_A);
+        k_match_ctl<<<1, 1, 0, cs>>>(h, stt, max_rounds);
+        if (cudaStreamEndCapture(cs, &body) != cudaSuccess) break;
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
+        ok = true;
+    } while (false);
+    if (!ok) {
+        cudaStreamCaptureStatus cst;
+        if (cudaStreamIsCapturing(cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+            cudaGraph_t dummy = nullptr;
+            cudaStreamEndCapture(cs, &dummy);
+            if (dummy) cudaGraphDestroy(dummy);
+        }
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        return false;
+    }
+    int slot = -1;
+    cudaEvent_t a = nullptr;
+    if (c->prof) {
+        slot = prof_slot(c, "match_graph");
+        prof_begin(c, slot, &a);
+    }
+    const cudaError_t le = cudaGraphLaunch(exec, c->st);
+    if (c->prof) prof_end(c, slot, a);
+    cudaError_t se = cudaSuccess;
+    if (le == cudaSuccess) {
+        se = cudaMemcpyAsync(hstate, stt, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+        if (se == cudaSuccess) se = cudaStreamSynchronize(c->st);
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (le != cudaSuccess) NGS_FAIL(NGS_ERR_CUDA, "match graph launch: %s", cudaGetErrorString(le));
+    if (se != cudaSuccess) NGS_FAIL(NGS_ERR_CUDA, "match graph: %s", cudaGetErrorString(se));
+    return true;
+}
 
 int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
     const int64_t n = g.n;
@@ -192,6 +316,37 @@ int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
     launch(c, "match_init", dim3(grid), dim3(256), 0, k_match_init, n, mate, cand);
     int64_t matched = 0;
     int r = 0;
+    if (g.n_edges > 0 && c->tune.match_graph) {
+        int32_t *stt = ws<int32_t>(c, c->b_mstate, 16);
+        NGS_CHECK_CUDA(cudaMemsetAsync(stt, 0, 16 * sizeof(int32_t), c->st));
+        // round 0 over every vertex, then the captured loop
+        launch(c, "match_scan", dim3(grid), dim3(256), 0, k_match_scan, (const int32_t *)nullptr,
+               (const int32_t *)nullptr, n, g.k_eff, g.nbr, (const float *)g.cost_slot,
+               (const int32_t *)g.rev_ptr, (const int32_t *)g.rev, g.cid, (const int32_t *)mate,
+               cand, candkey);
+        launch(c, "match_pair", dim3(grid), dim3(256), 0, k_match_pair, (const int32_t *)nullptr,
+               (const int32_t *)nullptr, n, (const int32_t *)cand, mate, stt + MS_M0, wl[0],
+               stt + MS_CNT_A);
+        int32_t *hs = (int32_t *)(c->h_pin + 32);
+        if (match_rounds_graph(c, g, mate, cand, candkey, wl, stt, grid, max_rounds, hs)) {
+            if (hs[MS_LIMIT]) NGS_FAIL(NGS_ERR_TIMEOUT, "matching did not converge in %d rounds", max_rounds);
+            c->rounds = hs[MS_ROUNDS];
+            c->launches += 1 + 5 * (int64_t)((hs[MS_ROUNDS]) / 2);  // control + body kernels
+            return hs[MS_TOTAL];
+        }
+        // no graph: continue from round 1 on the host (round 0 is done)
+        NGS_CHECK_CUDA(cudaMemcpyAsync(counts, stt + MS_M0, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st));
+        NGS_CHECK_CUDA(cudaMemcpyAsync(wl_counts, stt + MS_CNT_A, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st));
+        int32_t *h0 = (int32_t *)(c->h_pin + 32);
+        NGS_CHECK_CUDA(cudaMemcpyAsync(h0, counts, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+        sync_stream(c);
+        matched = h0[0];
+        r = 1;
+        if (h0[0] == 0) {
+            c->rounds = 1;
+            return 0;
+        }
+    }
     if (g.n_edges > 0) {
         // rounds are launched in batches; a batch is checked once on the host.
         // Round 0 visits every vertex, later rounds only the worklist.

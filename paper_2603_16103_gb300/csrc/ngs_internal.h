@@ -95,6 +95,7 @@ struct Tuning {
     int knn_block_min = 64;      // points the kNN 3x3x3 block must hold
     int cells_per_point = 4;     // cell-table density (cells >= this x points)
     int cost_blocks_per_sm = 8;  // edge-cost grid, 256-thread blocks per SM
+    int match_graph = 1;         // matching rounds after the first as one CUDA graph
 };
 
 struct ngs_ctx {
@@ -123,6 +124,7 @@ struct ngs_ctx {
     DevBuf b_host_dev[5];        // device staging for ngs_simplify_host
     DevBuf b_sC[5];              // third splat array set (several scenes at once)
     DevBuf b_fp64list;           // edges whose cost is evaluated in FP64
+    DevBuf b_mstate;             // device-side state of the captured matching rounds
     DevBuf b_eng[32];            // per-scene tables and scratch of the multi-scene engine
 
     // pinned host scratch
@@ -135,6 +137,7 @@ struct ngs_ctx {
     std::vector<cudaEvent_t> ev_free;
     int64_t launches = 0;
     int64_t ws_bytes = 0;         // device workspace currently held
+    cudaStream_t cap_st = nullptr;  // private stream the graph is captured on
 
     // per-call counters
     int64_t fp64_edges = 0;
