@@ -78,6 +78,79 @@ __global__ void k_slot_fill(const int32_t *__restrict__ nbr, int64_t n, int k,
     }
 }
 
+// Row-local form for k dividing 32: a warp holds whole rows, so the edge
+// position of a canonical slot is the row's start (a scan over per-row
+// counts) plus the canonical slots before it in the row (a ballot), and no
+// per-slot flag array or n*k-element scan is needed.
+__global__ void k_slot_classify_rows(const int32_t *__restrict__ nbr, int64_t n, int k,
+                                     const int32_t *__restrict__ cid, int32_t *mirror,
+                                     int32_t *rowcnt, int32_t *revcnt) {
+    const int64_t m = n * k;
+    const int lane = threadIdx.x & 31;
+    const unsigned rowmask = k == 32 ? FULL_MASK : ((1u << k) - 1u);
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < m; b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = b0 + threadIdx.x;
+        bool canon = false;
+        if (s < m) {
+            const int32_t v = (int32_t)(s / k);
+            const int32_t u = nbr[s];
+            const int32_t *row = nbr + (int64_t)u * k;
+            int tp = -1;
+            if ((k & 3) == 0) {
+                for (int t = k - 4; t >= 0; t -= 4) {
+                    const int4 r = __ldg((const int4 *)(row + t));
+                    if (r.w == v) tp = t + 3;
+                    if (r.z == v) tp = t + 2;
+                    if (r.y == v) tp = t + 1;
+                    if (r.x == v) tp = t;
+                }
+            } else {
+                for (int t = k - 1; t >= 0; t--)
+                    if (row[t] == v) tp = t;
+            }
+            if (tp >= 0) {
+                mirror[s] = u * k + tp;
+                canon = cid_of(cid, v) < cid_of(cid, u);
+            } else {
+                mirror[s] = -1;
+                canon = true;
+                atomicAdd(&revcnt[u], 1);
+            }
+        }
+        const unsigned cm = __ballot_sync(FULL_MASK, canon);
+        const int first = lane - lane % k;  // first lane of this slot's row
+        if (s < m && lane == first) rowcnt[s / k] = __popc(cm & (rowmask << first));
+    }
+}
+
+__global__ void k_slot_fill_rows(const int32_t *__restrict__ nbr, int64_t n, int k,
+                                 const int32_t *__restrict__ cid, const int32_t *__restrict__ mirror,
+                                 const int32_t *__restrict__ rowpos,
+                                 const int32_t *__restrict__ rev_ptr, int32_t *revfill, int4 *erec,
+                                 int32_t *rev) {
+    const int64_t m = n * k;
+    const int lane = threadIdx.x & 31;
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < m; b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = b0 + threadIdx.x;
+        bool canon = false;
+        int32_t u = 0, mr = -1, v = 0;
+        if (s < m) {
+            v = (int32_t)(s / k);
+            u = nbr[s];
+            mr = mirror[s];
+            canon = mr < 0 || cid_of(cid, v) < cid_of(cid, u);
+        }
+        const unsigned cm = __ballot_sync(FULL_MASK, canon);
+        const int first = lane - lane % k;
+        if (canon) {
+            const int32_t pos = rowpos[v] + __popc(cm & ((1u << lane) - 1u) & ~((1u << first) - 1u));
+            const bool vlo = cid_of(cid, v) < cid_of(cid, u);
+            erec[pos] = make_int4((int32_t)s, vlo ? v : u, vlo ? u : v, mr);
+        }
+        if (s < m && mr < 0) rev[rev_ptr[u] + atomicAdd(&revfill[u], 1)] = (int32_t)s;
+    }
+}
+
 __global__ void k_zero2(int32_t *a, int32_t *b, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -127,11 +200,18 @@ void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
     g.rev_ptr = ws<int32_t>(c, c->b_rstart, n + 1);
     launch(c, "zero2", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_zero2, revcnt,
            revfill, n);
-    launch(c, "slot_classify", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0,
-           k_slot_classify, nbr, n, k, g.cid, g.mirror, canon, revcnt);
-    scan_i32(c, canon, epos, m);
+    const bool rows = 32 % k == 0;  // a warp holds whole rows
+    if (rows) {
+        launch(c, "slot_classify", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0,
+               k_slot_classify_rows, nbr, n, k, g.cid, g.mirror, canon, revcnt);
+        scan_i32(c, canon, epos, n);  // per-row canonical counts -> row starts
+    } else {
+        launch(c, "slot_classify", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0,
+               k_slot_classify, nbr, n, k, g.cid, g.mirror, canon, revcnt);
+        scan_i32(c, canon, epos, m);
+    }
     scan_i32(c, revcnt, g.rev_ptr, n);
-    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin, epos + m, 4, cudaMemcpyDeviceToHost, c->st));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin, epos + (rows ? n : m), 4, cudaMemcpyDeviceToHost, c->st));
     NGS_CHECK_CUDA(cudaMemcpyAsync((int32_t *)c->h_pin + 1, g.rev_ptr + n, 4,
                                    cudaMemcpyDeviceToHost, c->st));
     sync_stream(c);
@@ -139,9 +219,14 @@ void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
     const int64_t nrev = ((int32_t *)c->h_pin)[1];
     g.erec = ws<int4>(c, c->b_elo, g.n_edges);
     g.rev = ws<int32_t>(c, c->b_upc, nrev);
-    launch(c, "slot_fill", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0, k_slot_fill,
-           nbr, n, k, g.cid, (const int32_t *)g.mirror, (const int32_t *)canon,
-           (const int32_t *)epos, (const int32_t *)g.rev_ptr, revfill, g.erec, g.rev);
+    if (rows)
+        launch(c, "slot_fill", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0,
+               k_slot_fill_rows, nbr, n, k, g.cid, (const int32_t *)g.mirror,
+               (const int32_t *)epos, (const int32_t *)g.rev_ptr, revfill, g.erec, g.rev);
+    else
+        launch(c, "slot_fill", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0, k_slot_fill,
+               nbr, n, k, g.cid, (const int32_t *)g.mirror, (const int32_t *)canon,
+               (const int32_t *)epos, (const int32_t *)g.rev_ptr, revfill, g.erec, g.rev);
     g.cost_slot = ws<float>(c, c->b_cost, m);
 }
 
