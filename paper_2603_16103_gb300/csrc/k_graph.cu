@@ -82,34 +82,57 @@ __global__ void k_slot_fill(const int32_t *__restrict__ nbr, int64_t n, int k,
 // position of a canonical slot is the row's start (a scan over per-row
 // counts) plus the canonical slots before it in the row (a ballot), and no
 // per-slot flag array or n*k-element scan is needed.
-__global__ void k_slot_classify_rows(const int32_t *__restrict__ nbr, int64_t n, int k,
+template <int K>
+__global__ void k_slot_classify_rows(const int32_t *__restrict__ nbr, int64_t n,
                                      const int32_t *__restrict__ cid, int32_t *mirror,
                                      int32_t *rowcnt, int32_t *revcnt) {
-    const int64_t m = n * k;
+    // The K ids of a target row are read by K/4 lanes (16 bytes each, one
+    // contiguous 4K-byte row), 128/K rows per round, K/4 rounds for the 32
+    // slots of the warp; each lane then takes the position found for its own
+    // slot by a shuffle.
+    constexpr int LPR = K / 4;          // lanes per target row
+    constexpr int RPI = 32 / LPR;       // target rows per round
+    constexpr int ITERS = 32 / RPI;     // rounds (= K / 4)
+    const int64_t m = n * K;
     const int lane = threadIdx.x & 31;
-    const unsigned rowmask = k == 32 ? FULL_MASK : ((1u << k) - 1u);
+    const unsigned rowmask = K == 32 ? FULL_MASK : ((1u << K) - 1u);
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < m; b0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = b0 + threadIdx.x;
-        bool canon = false;
-        if (s < m) {
-            const int32_t v = (int32_t)(s / k);
-            const int32_t u = nbr[s];
-            const int32_t *row = nbr + (int64_t)u * k;
-            int tp = -1;
-            if ((k & 3) == 0) {
-                for (int t = k - 4; t >= 0; t -= 4) {
-                    const int4 r = __ldg((const int4 *)(row + t));
-                    if (r.w == v) tp = t + 3;
-                    if (r.z == v) tp = t + 2;
-                    if (r.y == v) tp = t + 1;
-                    if (r.x == v) tp = t;
-                }
-            } else {
-                for (int t = k - 1; t >= 0; t--)
-                    if (row[t] == v) tp = t;
+        const bool valid = s < m;
+        const int32_t v = (int32_t)(s / K);
+        const int32_t u = valid ? nbr[s] : 0;
+        const int64_t wbase = s - lane;  // slot of lane 0
+        int tpr[ITERS];
+#pragma unroll
+        for (int it = 0; it < ITERS; it++) {
+            const int j = it * RPI + lane / LPR;   // slot whose target row this lane reads
+            const int chunk = lane % LPR;
+            const int32_t uj = __shfl_sync(FULL_MASK, u, j);
+            const int32_t vj = (int32_t)((wbase + j) / K);
+            int found = -1;
+            if (wbase + j < m) {
+                const int4 r = __ldg((const int4 *)(nbr + (int64_t)uj * K) + chunk);
+                const int t0 = 4 * chunk;
+                if (r.w == vj) found = t0 + 3;
+                if (r.z == vj) found = t0 + 2;
+                if (r.y == vj) found = t0 + 1;
+                if (r.x == vj) found = t0;
             }
+            // a row holds v at most once: the group's maximum is the position
+#pragma unroll
+            for (int o = 1; o < LPR; o <<= 1) found = max(found, __shfl_xor_sync(FULL_MASK, found, o));
+            tpr[it] = found;
+        }
+        int tp = -1;
+#pragma unroll
+        for (int it = 0; it < ITERS; it++) {
+            const int x = __shfl_sync(FULL_MASK, tpr[it], (lane % RPI) * LPR);
+            if (lane / RPI == it) tp = x;
+        }
+        bool canon = false;
+        if (valid) {
             if (tp >= 0) {
-                mirror[s] = u * k + tp;
+                mirror[s] = u * K + tp;
                 canon = cid_of(cid, v) < cid_of(cid, u);
             } else {
                 mirror[s] = -1;
@@ -118,8 +141,8 @@ __global__ void k_slot_classify_rows(const int32_t *__restrict__ nbr, int64_t n,
             }
         }
         const unsigned cm = __ballot_sync(FULL_MASK, canon);
-        const int first = lane - lane % k;  // first lane of this slot's row
-        if (s < m && lane == first) rowcnt[s / k] = __popc(cm & (rowmask << first));
+        const int first = lane - lane % K;  // first lane of this slot's row
+        if (valid && lane == first) rowcnt[s / K] = __popc(cm & (rowmask << first));
     }
 }
 
@@ -200,10 +223,15 @@ void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
     g.rev_ptr = ws<int32_t>(c, c->b_rstart, n + 1);
     launch(c, "zero2", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_zero2, revcnt,
            revfill, n);
-    const bool rows = 32 % k == 0;  // a warp holds whole rows
+    const bool rows = k % 4 == 0 && 32 % k == 0;  // a warp holds whole rows of int4 chunks
     if (rows) {
-        launch(c, "slot_classify", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0,
-               k_slot_classify_rows, nbr, n, k, g.cid, g.mirror, canon, revcnt);
+        const dim3 gr(grid_stride_blocks(c, m, 256, 16)), bl(256);
+        switch (k) {
+        case 4: launch(c, "slot_classify", gr, bl, 0, k_slot_classify_rows<4>, nbr, n, g.cid, g.mirror, canon, revcnt); break;
+        case 8: launch(c, "slot_classify", gr, bl, 0, k_slot_classify_rows<8>, nbr, n, g.cid, g.mirror, canon, revcnt); break;
+        case 16: launch(c, "slot_classify", gr, bl, 0, k_slot_classify_rows<16>, nbr, n, g.cid, g.mirror, canon, revcnt); break;
+        default: launch(c, "slot_classify", gr, bl, 0, k_slot_classify_rows<32>, nbr, n, g.cid, g.mirror, canon, revcnt); break;
+        }
         scan_i32(c, canon, epos, n);  // per-row canonical counts -> row starts
     } else {
         launch(c, "slot_classify", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0,
