@@ -57,9 +57,9 @@ ALGO = {
 # DRAM traffic per launch from ncu captures, in bytes per splat of the pass
 # (the profiles/ summaries give the commands and the raw counters).
 NCU_TRAFFIC_PER_SPLAT = {
-    "knn_k16": 42.51,      # 42.50 MB over 999,792 queries (knn_grid_patches1m.md)
-    "edge_cost": 563.55,   # 563.43 MB over 999,792 splats (edge_cost_patches1m.md)
-    "merge": 342.97,       # 342.90 MB, pass of 999,792 splats (merge_patches1m.md)
+    "knn_k16": 42.37,        # 42.36 MB over 999,792 queries (knn_grid_patches1m.md)
+    "edge_cost": 561.7,      # 561.63 MB over 999,792 splats (edge_cost_patches1m.md)
+    "slot_classify": 105.8,  # 105.77 MB over 999,792 splats (slot_classify_patches1m.md)
 }
 
 
@@ -79,6 +79,8 @@ def parse():
                     help="skip the batched and serving measurements")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tuning (for profiling: no tuning launches)")
     return ap.parse_args()
 
 
@@ -355,7 +357,7 @@ def main():
     pristine = B.DeviceSplats.from_numpy(scene)
     work = pristine.clone()
     # speed-only parameters measured on this scene (results do not depend on them)
-    tuning, _ = ctx.autotune(pristine)
+    tuning = ctx.tuning() if args.no_autotune else ctx.autotune(pristine)[0]
 
     def restore():
         for a, b in zip(work.tensors(), pristine.tensors()):

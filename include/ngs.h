@@ -322,9 +322,9 @@ int ngs_autotune(ngs_ctx *ctx, const ngs_splats *sample, ngs_tuning *best, doubl
  * one ngs_batch_simplify, so jobs that arrive while others are on the GPU
  * join the next free slot's batch.  Every job's result is bit-identical to
  * ngs_simplify on it alone (the batched engine guarantees this per scene).
- * Large runs (priority_rows) take a high-priority stream so that the jobs
- * that set the latency tail are not slowed by small concurrent ones, which
- * fill the SMs the large run leaves idle.
+ * Runs of fewer than priority_rows rows take a high-priority stream: the
+ * SMs serve short jobs first, so a small job that arrives while a large one
+ * runs is not queued behind it.
  * slots = 1 without grouping is plain one-at-a-time processing.
  * Job splats are device arrays owned by the caller, simplified in place; they
  * must stay valid and untouched until the job has finished.
@@ -341,8 +341,8 @@ typedef struct {
     int64_t small_rows;           /* jobs up to this size may be grouped, 1e6  */
     int64_t group_rows;           /* rows of one group at most, 4e6             */
     double dry_run_ns_per_splat;  /* > 0: host-only scheduler run, default 0   */
-    int64_t priority_rows;        /* runs of at least this many rows go on a
-                                     high-priority stream, smaller ones on a
+    int64_t priority_rows;        /* runs of fewer rows than this go on a
+                                     high-priority stream, larger ones on a
                                      low-priority one (0: one priority), 1e6  */
 } ngs_server_config;
 

@@ -205,7 +205,9 @@ void worker(ngs_server *S, int w) {
 
         std::vector<int> rc(group.size(), NGS_OK);
         if (ctx) {
-            const bool high = S->cfg.priority_rows > 0 && rows >= S->cfg.priority_rows;
+            // short runs first (shortest-job-first on the SMs): a run below
+            // priority_rows rows takes the high-priority stream
+            const bool high = S->cfg.priority_rows > 0 && rows < S->cfg.priority_rows;
             const int r = ngs_set_stream(ctx, high ? st_hi : st_lo);
             if (r != NGS_OK)
                 for (int &x : rc) x = r;
