@@ -253,29 +253,56 @@ __global__ void __launch_bounds__(256, 3)
                 float *__restrict__ cost_out, unsigned long long *fp64_count,
                 int2 *__restrict__ fp64_list) {
     const float zz0 = zs[0] * zs[0] + zs[1] * zs[1] + zs[2] * zs[2];
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int F4 = F >> 2;
+    const float4 *sh4 = (const float4 *)sh;
+    // Warp-uniform loop over 32-edge chunks.  The appearance term is summed by
+    // 4 lanes per edge, each a quarter of the float4 chunks of both SH rows,
+    // so a load instruction reads 8 rows x 64 contiguous bytes instead of 32
+    // rows x 16 bytes (the gathers are bound by the L1 data pipe); each lane
+    // then evaluates its own edge's geometric term.
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = base + threadIdx.x;
+        const bool valid = e < m;
         // i = lower canonical id: the arithmetic is then independent of row order
-        const int4 er = __ldg(erec + e);
-        const int32_t sl = er.x;
-        const int64_t i = er.y, j = er.z;
-        const Rec Ri{(const float4 *)(rec + i * REC)}, Rj{(const float4 *)(rec + j * REC)};
-        // ---- appearance term
+        const int4 er = valid ? __ldg(erec + e) : make_int4(-1, 0, 0, -1);
         float dapp = 0.f;
         if ((F & 3) == 0) {
-            const float4 *fi = (const float4 *)(sh + i * F), *fj = (const float4 *)(sh + j * F);
-#pragma unroll 4
-            for (int t = 0; t < F / 4; t++) {
-                float4 a = __ldg(fi + t), b = __ldg(fj + t);
-                float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
-                dapp += dx * dx + dy * dy + dz * dz + dw * dw;
+            const int64_t wb = base + (threadIdx.x & ~31);
+            float dpart[4];
+#pragma unroll
+            for (int qd = 0; qd < 4; qd++) {
+                const int el = qd * 8 + (lane >> 2), sub = lane & 3;
+                const int32_t ii = __shfl_sync(FULL_MASK, er.y, el), jj = __shfl_sync(FULL_MASK, er.z, el);
+                float acc = 0.f;
+                if (wb + el < m) {
+                    const float4 *fi = sh4 + (int64_t)ii * F4, *fj = sh4 + (int64_t)jj * F4;
+                    for (int t = sub; t < F4; t += 4) {
+                        const float4 a = __ldg(fi + t), b = __ldg(fj + t);
+                        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+                        acc += dx * dx + dy * dy + dz * dz + dw * dw;
+                    }
+                }
+                acc += __shfl_xor_sync(FULL_MASK, acc, 1);
+                acc += __shfl_xor_sync(FULL_MASK, acc, 2);
+                dpart[qd] = acc;
             }
-        } else {
+            const int src = (lane & 7) * 4;
+            const float d0 = __shfl_sync(FULL_MASK, dpart[0], src), d1 = __shfl_sync(FULL_MASK, dpart[1], src);
+            const float d2 = __shfl_sync(FULL_MASK, dpart[2], src), d3 = __shfl_sync(FULL_MASK, dpart[3], src);
+            const int qd = lane >> 3;
+            dapp = qd == 0 ? d0 : (qd == 1 ? d1 : (qd == 2 ? d2 : d3));
+        } else if (valid) {
             for (int t = 0; t < F; t++) {
-                float df = sh[i * F + t] - sh[j * F + t];
+                float df = sh[(int64_t)er.y * F + t] - sh[(int64_t)er.z * F + t];
                 dapp += df * df;
             }
         }
+        if (!valid) continue;
+        const int32_t sl = er.x;
+        const int64_t i = er.y, j = er.z;
+        const Rec Ri{(const float4 *)(rec + i * REC)}, Rj{(const float4 *)(rec + j * REC)};
         // ---- MPMM moments (Eqs. vm_weights, vm_cov)
         const float4 i0 = Ri.g(0), j0 = Rj.g(0);
         const float ld = i0.w - j0.w;
@@ -360,7 +387,7 @@ __global__ void __launch_bounds__(256, 3)
         const unsigned am = __activemask();
         const unsigned fm = __ballot_sync(am, flag);
         if (fm) {
-            const int lane = threadIdx.x & 31, first = __ffs(fm) - 1;
+            const int first = __ffs(fm) - 1;
             unsigned long long at = 0;
             if (lane == first) at = atomicAdd(fp64_count, (unsigned long long)__popc(fm));
             at = __shfl_sync(am, at, first);
