@@ -25,8 +25,9 @@ def dev(ngs, scene):
 
 
 @pytest.mark.parametrize("n,kind,k", [(20000, "unit", 16), (9001, "patch", 16), (4000, "unit", 5),
-                                      (2000, "patch", 32), (40, "unit", 16), (17, "unit", 16),
-                                      (2, "unit", 16), (3, "unit", 16)])
+                                      (2000, "patch", 32), (3000, "unit", 4), (3500, "patch", 8),
+                                      (40, "unit", 16), (17, "unit", 16), (2, "unit", 16),
+                                      (3, "unit", 16), (6, "unit", 2)])
 def test_knn_and_edges(ngs, n, kind, k):
     scene = small_scene(n, seed=n, kind=kind)
     c = ngs.Context(k=k)
@@ -227,6 +228,21 @@ def test_simplify_equals_stepwise(ngs, ctx, n, ratio, kind):
     ref, passes = stepwise(ngs, ctx, scene, target)
     assert st["passes"] == passes
     assert ds.n == ref.n
+    for a, b in zip(ds.numpy(), ref.numpy()):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("k", [4, 8, 32, 5])
+def test_simplify_equals_stepwise_other_k(ngs, k):
+    """Every k the graph builder specialises (whole rows per warp for 4, 8, 32)
+    and one it does not (5)."""
+    scene = small_scene(6000, seed=60 + k, kind="patch")
+    target = O.target_count(scene.n, 0.25)
+    with ngs.Context(k=k) as c:
+        ds = dev(ngs, scene)
+        st = c.simplify(ds, target)
+        ref, passes = stepwise(ngs, c, scene, target)
+    assert st["passes"] == passes and ds.n == ref.n
     for a, b in zip(ds.numpy(), ref.numpy()):
         assert np.array_equal(a, b)
 
