@@ -513,6 +513,11 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     }
 
     // ---- survivors into Morton order within each scene (working set A)
+    // A single scene whose SH array is still being uploaded (ngs_simplify_host)
+    // gathers its SH rows only when first needed: before the first edge costs
+    // or write-back, so the upload overlaps the first graph stages.
+    bool defer_sh = !multi && c->sh_wait && (F & 3) == 0 && F <= 64;
+    uint32_t *order0 = nullptr;
     SplatView A, B;
     int32_t *cidA = nullptr, *cidB = nullptr;
     {
@@ -536,7 +541,14 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         }
         A = scratch(c, c->b_sA, nf, F);
         B = multi ? scratch(c, c->b_sC, nf, F) : scratch(c, c->b_sB, nf, F);
-        gather_rows(c, IN, order, A);
+        if (defer_sh) {
+            // the SH rows follow once their upload has finished (ensure_sh)
+            gather_rows_part(c, IN, order, A, false);
+            order0 = ws<uint32_t>(c, c->b_order0, nf);
+            NGS_CHECK_CUDA(cudaMemcpyAsync(order0, order, 4 * nf, cudaMemcpyDeviceToDevice, c->st));
+        } else {
+            gather_rows(c, IN, order, A);
+        }
         cidA = ws<int32_t>(c, c->b_cid, nf + 1);
         cidB = ws<int32_t>(c, c->b_cid2, nf + 1);
         launch(c, "gather_cid", dim3(grid_stride_blocks(c, nf, 256, 8)), dim3(256), 0,
@@ -554,8 +566,15 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     for (int s = 0; s <= S; s++) wstart[s] = kin[s];
     int32_t *sidA = ws<int32_t>(c, c->b_eng[E_SIDW], nf + 1);
 
+    auto ensure_sh = [&]() {
+        if (!defer_sh) return;
+        NGS_CHECK_CUDA(cudaStreamWaitEvent(c->st, c->sh_wait, 0));
+        gather_rows_part(c, IN, order0, A, true);
+        defer_sh = false;
+    };
     // write stopped scenes back (canonical order) and drop them from A
     auto extract = [&](bool all) {
+        ensure_sh();
         bool any = false, left = false;
         for (int s = 0; s < S; s++) {
             stop[s] = !out_done[s] && (all || !running[s]);
@@ -656,6 +675,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         knn_search(c, KnnInput{pts, pk, pv, ssid, frames, scene_n.data(), S, nA, 0, cidA},
                    g.k_eff, nbr);
         build_edges(c, nbr, g);
+        ensure_sh();
         edge_costs(c, A, g, (uint32_t)pass, false, nullptr);
         int32_t *partner = ws<int32_t>(c, c->b_partner, nA);
         int64_t np = 0;

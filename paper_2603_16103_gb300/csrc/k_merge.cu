@@ -523,14 +523,15 @@ __global__ void k_prefilter_flags(const float *__restrict__ logit, int64_t n,
         keep[v] = (double)logit[v] >= thr;
 }
 
+// chunks [ch0, ch0 + per) of each row: F/4 SH chunks, then the scalar fields
 __global__ void k_move_rows(Rows in, WRows out, int64_t n, int F, int mode,
-                            const int32_t *__restrict__ keep, const int32_t *__restrict__ idx) {
-    const int per = (F >> 2) + 1;
+                            const int32_t *__restrict__ keep, const int32_t *__restrict__ idx,
+                            int ch0, int per) {
     const int64_t total = n * per;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = t / per;
-        const int ch = (int)(t - v * per);
+        const int ch = ch0 + (int)(t - v * per);
         if (mode == 0) {
             if (keep[v]) move_chunk(in, v, out, idx[v], F, ch);
         } else if (mode == 1) {
@@ -657,7 +658,7 @@ static void move_rows(ngs_ctx *c, const SplatView &in, SplatView &out, int64_t n
     if ((in.F & 3) == 0 && in.F <= 64) {
         const int per = (in.F >> 2) + 1;
         launch(c, name, dim3(grid_stride_blocks(c, n * per, 256, 16)), dim3(256), 0, k_move_rows,
-               rows_of(in), wo, n, in.F, mode, keep, idx);
+               rows_of(in), wo, n, in.F, mode, keep, idx, 0, per);
     } else if (mode == 0) {
         launch(c, name, dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_compact, rows_of(in),
                wo, n, in.F, keep, idx);
@@ -681,4 +682,15 @@ void scatter_rows(ngs_ctx *c, const SplatView &in, const int32_t *dst, SplatView
 
 void gather_rows(ngs_ctx *c, const SplatView &in, const uint32_t *src, SplatView &out) {
     move_rows(c, in, out, out.n, 2, nullptr, (const int32_t *)src, "gather_rows");
+}
+
+void gather_rows_part(ngs_ctx *c, const SplatView &in, const uint32_t *src, SplatView &out,
+                      bool sh) {
+    const int64_t n = out.n;
+    if (n <= 0) return;
+    const int nch = in.F >> 2;
+    const int ch0 = sh ? 0 : nch, per = sh ? nch : 1;
+    launch(c, sh ? "gather_rows_sh" : "gather_rows", dim3(grid_stride_blocks(c, n * per, 256, 16)),
+           dim3(256), 0, k_move_rows, rows_of(in), wrows_of(out), n, in.F, 2,
+           (const int32_t *)nullptr, (const int32_t *)src, ch0, per);
 }

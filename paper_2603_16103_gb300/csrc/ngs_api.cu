@@ -239,7 +239,7 @@ static void release_all(ngs_ctx *c) {
                       &c->b_cand, &c->b_candkey, &c->b_counts, &c->b_sel, &c->b_role, &c->b_keep,
                       &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
                       &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2,
-                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc, &c->b_fp64list, &c->b_mstate};
+                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc, &c->b_fp64list, &c->b_mstate, &c->b_order0};
     for (DevBuf *b : bufs) ws_free(c, *b);
     for (int k = 0; k < 5; k++) {
         ws_free(c, c->b_sA[k]);
@@ -279,6 +279,12 @@ extern "C" int ngs_destroy(ngs_ctx *c) {
     for (auto e : c->ev_free) cudaEventDestroy(e);
     if (c->h_pin) cudaFreeHost(c->h_pin);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
+    if (c->up_st) {
+        cudaStreamSynchronize(c->up_st);
+        cudaStreamDestroy(c->up_st);
+        cudaEventDestroy(c->up_ev);
+        cudaEventDestroy(c->up_ready);
+    }
     delete c;
     return NGS_OK;
 }
@@ -560,9 +566,30 @@ extern "C" int ngs_simplify_host(ngs_ctx *c, ngs_splats *h, int64_t target, ngs_
     const size_t sz[5] = {12, 12, 16, 4, 4 * (size_t)F};
     float *hp[5] = {h->xyz, h->log_scale, h->rot, h->opacity_logit, h->sh};
     float *dp[5] = {d.xyz, d.log_scale, d.rot, d.opacity_logit, d.sh};
-    for (int k = 0; k < 5; k++)
+    // The SH array (most of the bytes) goes up on a second stream; the engine
+    // waits for it only before its first edge costs, so the upload overlaps
+    // the pre-filter, sorting and first graph stages.
+    if (!c->up_st) {
+        NGS_CHECK_CUDA(cudaStreamCreateWithFlags(&c->up_st, cudaStreamNonBlocking));
+        NGS_CHECK_CUDA(cudaEventCreateWithFlags(&c->up_ev, cudaEventDisableTiming));
+        NGS_CHECK_CUDA(cudaEventCreateWithFlags(&c->up_ready, cudaEventDisableTiming));
+    }
+    NGS_CHECK_CUDA(cudaEventRecord(c->up_ready, c->st));  // staging buffers exist
+    NGS_CHECK_CUDA(cudaStreamWaitEvent(c->up_st, c->up_ready, 0));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dp[4], hp[4], sz[4] * n, cudaMemcpyHostToDevice, c->up_st));
+    NGS_CHECK_CUDA(cudaEventRecord(c->up_ev, c->up_st));
+    for (int k = 0; k < 4; k++)
         NGS_CHECK_CUDA(cudaMemcpyAsync(dp[k], hp[k], sz[k] * n, cudaMemcpyHostToDevice, c->st));
-    engine_simplify(c, &d, &target, 1, st);
+    c->sh_wait = c->up_ev;
+    try {
+        engine_simplify(c, &d, &target, 1, st);
+    } catch (...) {
+        c->sh_wait = nullptr;
+        cudaStreamWaitEvent(c->st, c->up_ev, 0);  // the staging buffer stays busy until then
+        throw;
+    }
+    c->sh_wait = nullptr;
+    NGS_CHECK_CUDA(cudaStreamWaitEvent(c->st, c->up_ev, 0));
     for (int k = 0; k < 5; k++)
         NGS_CHECK_CUDA(cudaMemcpyAsync(hp[k], dp[k], sz[k] * d.n, cudaMemcpyDeviceToHost, c->st));
     sync_stream(c);

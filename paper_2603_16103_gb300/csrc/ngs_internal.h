@@ -138,6 +138,11 @@ struct ngs_ctx {
     int64_t launches = 0;
     int64_t ws_bytes = 0;         // device workspace currently held
     cudaStream_t cap_st = nullptr;  // private stream the graph is captured on
+    cudaStream_t up_st = nullptr;   // second upload stream of ngs_simplify_host
+    cudaEvent_t up_ev = nullptr;    // SH upload finished
+    cudaEvent_t up_ready = nullptr; // staging buffers allocated on st
+    cudaEvent_t sh_wait = nullptr;  // set for one engine call: SH input not yet on the device
+    DevBuf b_order0;                 // initial Morton permutation kept for the deferred SH gather
 
     // per-call counters
     int64_t fp64_edges = 0;
@@ -299,6 +304,8 @@ void compact_rows(ngs_ctx *c, const SplatView &in, const int32_t *keep, const in
 // Scatter rows: out[dst[v]] = in[v].
 void scatter_rows(ngs_ctx *c, const SplatView &in, const int32_t *dst, SplatView &out);
 // Gather rows: out[v] = in[src[v]].
+// Only the SH rows (sh) or only the other fields (!sh); F a multiple of 4, F <= 64.
+void gather_rows_part(ngs_ctx *c, const SplatView &in, const uint32_t *src, SplatView &out, bool sh);
 void gather_rows(ngs_ctx *c, const SplatView &in, const uint32_t *src, SplatView &out);
 
 // Host-side common random numbers for pass `pass` (SplitMix64 + Box-Muller):
