@@ -16,6 +16,11 @@
  *   - sampling: x = mu_c + Sigma_c^{1/2} z (symmetric square root), common z
  *     per pass from SplitMix64 + Box-Muller; mode 0 integrates the component
  *     draw out (pi g(x_i) + (1-pi) g(x_j)), mode 1 draws it with u < pi;
+ *   - mode 2 keeps mode 0's draws but replaces the sampled -log q_m(x) by its
+ *     exact mean under p~, 1/2 log det(2 pi Sigma_m) + 3/2 (q_m carries p~'s
+ *     own mean and covariance, App. A), so only the entropy of p~ is sampled;
+ *   - mode 3 is the MSE surrogate of the Sec. 4 ablation, chosen here as
+ *     |mu_i - mu_j|^2 + ||Sigma_i - Sigma_j||_F^2 (deterministic);
  *   - merged splat at slot min(i,j), stable order otherwise;
  *   - merged covariance -> (log-scale, quaternion) by cyclic Jacobi, eigen-
  *     values floored at eig_floor, canonical eigenvector signs, w >= 0;
@@ -424,10 +429,28 @@ static void sample_point(const gauss_t *g, const float *z, double *x) {
         x[a] = g->mu[a] + g->R[a * 3 + 0] * t[0] + g->R[a * 3 + 1] * t[1] + g->R[a * 3 + 2] * t[2];
 }
 
+/* MSE geometric surrogate (the "w/o I-divergence" ablation of Sec. 4): squared
+ * distance of the centres plus the squared Frobenius norm of the covariance
+ * difference. */
+static double dgeo_mse(const gauss_t *gi, const gauss_t *gj) {
+    double r = 0;
+    for (int a = 0; a < 3; a++) {
+        double d = gi->mu[a] - gj->mu[a];
+        r += d * d;
+    }
+    for (int t = 0; t < 9; t++) {
+        double d = gi->Sig[t] - gj->Sig[t];
+        r += d * d;
+    }
+    return r;
+}
+
 /* Eq. mc_kl_estimator for one pair: KL(p~_ij || q_m) estimated with S common
- * samples.  Returns +inf if the merged covariance is not positive definite. */
+ * samples (modes 0-2), or the MSE surrogate (mode 3).  Returns +inf if the
+ * merged covariance is not positive definite (modes 0-2). */
 static double dgeo_gauss(const gauss_t *gi, const gauss_t *gj, int S, const float *z,
                          const float *u, int mode) {
+    if (mode == 3) return dgeo_mse(gi, gj);
     double pi, pj, lpi, lpj;
     mass_ratio(gi, gj, &pi, &pj, &lpi, &lpj);
     double mum[3], Sm[9], L[9];
@@ -438,13 +461,15 @@ static double dgeo_gauss(const gauss_t *gi, const gauss_t *gj, int S, const floa
     for (int s = 0; s < S; s++) {
         const float *zs = z + 3 * s;
         double xi[3], xj[3];
-        if (mode == 0) {
+        if (mode == 0 || mode == 2) {
             sample_point(gi, zs, xi);
             sample_point(gj, zs, xj);
-            double gxi = logsumexp2(lpi + h_splat(gi, xi), lpj + h_splat(gj, xi)) -
-                         h_chol(mum, L, logdet_m, xi);
-            double gxj = logsumexp2(lpi + h_splat(gi, xj), lpj + h_splat(gj, xj)) -
-                         h_chol(mum, L, logdet_m, xj);
+            /* -E_p~[log q_m] in closed form: the expected Mahalanobis term of a
+             * Gaussian under its own moments is 3 (three dimensions) */
+            double hmi = mode == 0 ? h_chol(mum, L, logdet_m, xi) : -0.5 * logdet_m - 1.5;
+            double hmj = mode == 0 ? h_chol(mum, L, logdet_m, xj) : -0.5 * logdet_m - 1.5;
+            double gxi = logsumexp2(lpi + h_splat(gi, xi), lpj + h_splat(gj, xi)) - hmi;
+            double gxj = logsumexp2(lpi + h_splat(gi, xj), lpj + h_splat(gj, xj)) - hmj;
             acc += pi * gxi + pj * gxj;
         } else {
             const gauss_t *gc = ((double)u[s] < pi) ? gi : gj;

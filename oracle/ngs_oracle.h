@@ -48,7 +48,9 @@ int64_t orc_union_edges(int64_t n, int k_eff, const int32_t *nbr, int32_t *lo, i
 void orc_mc_draws(uint64_t seed, uint32_t pass, int S, float *z, float *u);
 
 /* Sec. 3.2 merge cost C = lambda_geo * D_geo + lambda_app * D_app per edge.
- * mode 0: component-stratified CRN estimator; mode 1: literal mixture draw.
+ * mode 0: component-stratified CRN estimator; mode 1: literal mixture draw;
+ * mode 2: mode 0 with the cross-entropy term in closed form; mode 3: MSE
+ * surrogate |mu_i - mu_j|^2 + ||Sigma_i - Sigma_j||_F^2.
  * dgeo/dapp may be NULL. */
 void orc_edge_costs(int64_t n, const double *xyz, const double *log_scale, const double *rot,
                     const double *logit, const double *sh, int F,
@@ -100,7 +102,7 @@ void orc_mpmm_moments(double wi, const double *mui, const double *Si, const doub
 double orc_kl_gauss(const double *mui, const double *Si, const double *muj, const double *Sj);
 double orc_idiv_gauss(double mi, const double *mui, const double *Si,
                       double mj, const double *muj, const double *Sj);
-/* D_geo of one pair given splat parameters (mode 0/1), S samples z,u. */
+/* D_geo of one pair given splat parameters (mode 0..3), S samples z,u. */
 double orc_dgeo_pair(const double *xyz_i, const double *ls_i, const double *rot_i, double logit_i,
                      const double *xyz_j, const double *ls_j, const double *rot_j, double logit_j,
                      int S, const float *z, const float *u, int mode);

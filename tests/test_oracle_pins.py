@@ -233,7 +233,7 @@ def _gh_kl(si, sj, order=40):
     return total
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_dgeo_large_sample_matches_quadrature(mode):
     rng = np.random.default_rng(7)
     for t in range(3):
@@ -260,6 +260,70 @@ def test_dgeo_identical_is_zero_and_symmetric():
               rng.normal())
         a, b = O.dgeo_pair(si, sj, z, u, 0), O.dgeo_pair(sj, si, z, u, 0)
         assert abs(a - b) <= 1e-10 * max(1.0, abs(a))
+
+
+def test_dgeo_closed_cross_entropy_identical_pair_exact():
+    """Mode 2 on two copies of one splat: p~ = q_m = N_i, the entropy draws give
+    -1/2 |z_s|^2 - 1/2 log det(2 pi Sigma) each and the closed-form cross-entropy
+    adds 1/2 log det(2 pi Sigma) + 3/2, so the estimate is 3/2 - mean |z|^2 / 2
+    exactly (and tends to 0 as S grows, E|z|^2 = 3)."""
+    rng = np.random.default_rng(81)
+    for S in (1, 3, 64):
+        z, u = O.mc_draws(11, S, S)
+        z64 = np.asarray(z, np.float64).reshape(-1, 3)
+        want = 1.5 - 0.5 * np.mean(np.sum(z64 * z64, axis=1))
+        for _ in range(20):
+            si = (rng.normal(size=3), rng.normal(-4.5, 0.6, 3), rng.normal(size=4), rng.normal())
+            got = O.dgeo_pair(si, si, z, u, 2)
+            assert abs(got - want) < 1e-11 * max(1.0, abs(want)), (got, want)
+    z, u = O.mc_draws(12, 0, 200000)
+    assert abs(O.dgeo_pair(si, si, z, u, 2)) < 0.02
+
+
+def test_dgeo_closed_cross_entropy_symmetric_and_same_mean():
+    """Mode 2 is symmetric in (i, j) for common draws and estimates the same KL
+    as mode 0.  Its spread across draw sets is the larger one: in mode 0 the
+    sampled log q_m(x) moves with log p~(x) (both fall off as |z|^2 / 2), so
+    their difference cancels most of the noise that mode 2 keeps."""
+    rng = np.random.default_rng(82)
+    z, u = O.mc_draws(5, 0, 8)
+    for _ in range(50):
+        si = (rng.normal(size=3) * 0.01, rng.normal(-4.5, 0.5, 3), rng.normal(size=4), rng.normal())
+        sj = (si[0] + rng.normal(size=3) * 0.01, rng.normal(-4.5, 0.5, 3), rng.normal(size=4),
+              rng.normal())
+        a, b = O.dgeo_pair(si, sj, z, u, 2), O.dgeo_pair(sj, si, z, u, 2)
+        assert abs(a - b) <= 1e-10 * max(1.0, abs(a))
+    si = ((0.0, 0.0, 0.0), (-4.2, -4.6, -5.0), (1.0, 0.2, -0.3, 0.1), 0.4)
+    sj = ((0.012, -0.004, 0.006), (-4.8, -4.3, -4.4), (0.3, -1.0, 0.5, 0.2), -0.2)
+    est = {m: [O.dgeo_pair(si, sj, *O.mc_draws(900, b, 4), m) for b in range(400)] for m in (0, 2)}
+    assert np.std(est[0]) < np.std(est[2])
+    assert abs(np.mean(est[2]) - np.mean(est[0])) < 4 * math.hypot(np.std(est[0]), np.std(est[2])) / 20
+
+
+def test_dgeo_mse_surrogate_definition():
+    """Mode 3: |mu_i - mu_j|^2 + ||Sigma_i - Sigma_j||_F^2 with the covariances
+    built here through scipy's rotation; independent of the draws and of the
+    opacities; zero on identical splats; translation alone gives |d|^2; a
+    shared rotation leaves the scale term unchanged."""
+    rng = np.random.default_rng(83)
+    for t in range(60):
+        si = (rng.normal(size=3), rng.normal(-2.0, 0.8, 3), rng.normal(size=4), rng.normal())
+        sj = (rng.normal(size=3), rng.normal(-2.0, 0.8, 3), rng.normal(size=4), rng.normal())
+        want = (np.sum((np.asarray(si[0]) - sj[0]) ** 2) +
+                np.sum((sigma_of(si[1], si[2]) - sigma_of(sj[1], sj[2])) ** 2))
+        z, u = O.mc_draws(t, 0, 1 + t % 5)
+        got = O.dgeo_pair(si, sj, z, u, 3)
+        assert abs(got - want) <= 1e-12 * max(1.0, want)
+        assert got == O.dgeo_pair(sj, si, z, u, 3)
+        assert got == O.dgeo_pair(si, (sj[0], sj[1], sj[2], sj[3] + 3.0), *O.mc_draws(7, 1, 2), 3)
+        assert O.dgeo_pair(si, si, z, u, 3) == 0.0
+        d = rng.normal(size=3)
+        moved = (np.asarray(si[0]) + d, si[1], si[2], si[3])
+        assert abs(O.dgeo_pair(si, moved, z, u, 3) - np.sum(d * d)) <= 1e-12 * np.sum(d * d)
+        ls_j = rng.normal(-2.0, 0.8, 3)
+        same_rot = (si[0], ls_j, si[2], si[3])
+        want = np.sum((np.exp(2 * np.asarray(si[1])) - np.exp(2 * ls_j)) ** 2)
+        assert abs(O.dgeo_pair(si, same_rot, z, u, 3) - want) <= 1e-12 * max(1.0, want)
 
 
 def test_edge_cost_appearance_term_and_weights():
