@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the batched and serving measurements")
+                    help="skip the batched, serving and cost-variant measurements")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--no-autotune", action="store_true",
@@ -256,6 +256,60 @@ def batched_form(B, torch, synth, args):
             "sequential": res["sequential"],
             "speedup": res["sequential"]["ms"] / res["batched"]["ms"], "tuning": tuning,
             "identical_outputs": identical, "steps": args.form_steps}
+
+
+COST_VARIANTS = [
+    ("kl_stratified_S1", dict(cost_mode=0, mc_samples=1)),
+    ("kl_stratified_S8", dict(cost_mode=0, mc_samples=8)),
+    ("kl_stratified_S128", dict(cost_mode=0, mc_samples=128)),
+    ("kl_literal_S1", dict(cost_mode=1, mc_samples=1)),
+    ("kl_closed_xent_S1", dict(cost_mode=2, mc_samples=1)),
+    ("kl_closed_xent_S8", dict(cost_mode=2, mc_samples=8)),
+    ("mse_surrogate", dict(cost_mode=3)),
+    ("no_prefilter", dict(prefilter=0)),
+]
+
+
+def cost_variants_form(B, torch, pristine, target, tuning, args):
+    """The cost-stage swaps on the headline scene: the edge-cost call
+    (ngs_edge_costs on the first pass's graph, pre-filtered input) and the whole
+    loop (ngs_simplify) per variant; S = 128 edge costs only."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, params in COST_VARIANTS:
+        ctx = B.Context(**params)
+        ctx.set_tuning(**tuning)
+        ds = pristine.clone()
+        if params.get("prefilter", 1):
+            ctx.prefilter(ds)
+        g, _, _, _ = ctx.build_graph(ds)
+        times = []
+        for it in range(4):
+            ms, _ = _timed(torch, stream, lambda: ctx.edge_costs(ds, g, 0))
+            if it:
+                times.append(ms)
+        ec = statistics.median(times)
+        row = {"edge_cost_ms": ec, "edges": int(g.n_edges),
+               "edges_per_s": g.n_edges / (ec / 1e3)}
+        del ds, g
+        if params.get("mc_samples", 1) <= 8:
+            work = pristine.clone()
+            times = []
+            for it in range(1 + args.form_steps):
+                for a, b in zip(work.tensors(), pristine.tensors()):
+                    a.copy_(b)
+                work.n = pristine.n
+                ms, st = _timed(torch, stream, lambda: ctx.simplify(work, target))
+                if it:
+                    times.append(ms)
+            ms = statistics.median(times)
+            row.update({"step_ms": ms, "value": pristine.n / (ms / 1e3), "unit": UNIT,
+                        "passes": st["passes"], "n_output": work.n})
+            del work
+        ctx.close()
+        res[name] = row
+    torch.cuda.empty_cache()
+    return res
 
 
 def serving_form(B, torch, synth, args):
@@ -462,6 +516,7 @@ def main():
     if not args.no_forms and ws == 1:  # the forms are measured on one GPU
         forms["batched"] = batched_form(B, torch, synth, args)
         forms["serving"] = serving_form(B, torch, synth, args)
+        forms["cost_variants"] = cost_variants_form(B, torch, pristine, target, tuning, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

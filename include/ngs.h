@@ -66,9 +66,15 @@ typedef struct {
 /* Method parameters (Algorithm 1 inputs r, k, tau, cp; Sec. 4 defaults).
  *   k           kNN size (Sec. 3.1; default 16; 1..NGS_MAX_K)
  *   mc_samples  S, Monte Carlo samples per edge (App. A; default 1)
- *   cost_mode   0: component-stratified common-random-number estimator
- *               (pi g(x_i) + (1-pi) g(x_j)); 1: the literal mixture draw
- *               (component i when u < pi).  Default 0.
+ *   cost_mode   D_geo of the edge cost (default 0):
+ *               0: KL(p~ || q_m) by the component-stratified common-random-
+ *                  number estimator (pi g(x_i) + (1-pi) g(x_j), App. A);
+ *               1: the same KL by the literal mixture draw (component i
+ *                  when u < pi);
+ *               2: as 0 with -E[log q_m] in closed form (1/2 log det
+ *                  2 pi Sigma_m + 3/2), only the entropy of p~ sampled;
+ *               3: MSE surrogate |mu_i - mu_j|^2 + ||Sigma_i - Sigma_j||_F^2
+ *                  (the "w/o I-divergence" ablation, Sec. 4); draws unused.
  *   tau         opacity pre-filter threshold (Algorithm 1; default 0.005)
  *   lambda_geo, lambda_app  weights of D_geo and D_app in the cost
  *               (Eq. Equ:cost has both at 1; default 1, 1)
@@ -77,7 +83,8 @@ typedef struct {
  *   fp64_policy 0: merged covariance eigendecomposition in FP64 and FP64
  *               log-det for near-degenerate merged covariances (default);
  *               1: additionally FP64 cost terms for edges with a
- *               near-degenerate endpoint
+ *               near-degenerate endpoint; 2: FP64 eigendecomposition only
+ *               for ill-conditioned merged covariances
  *   prefilter   1: ngs_simplify first applies the opacity pre-filter
  *   eig_floor   lower bound on merged covariance eigenvalues (default 1e-30)
  */

@@ -12,7 +12,11 @@
 //   a_c  = log sqrt(det Sigma_m / det Sigma_c),  q_c = Mahalanobis^2 under c,
 // keeps FP32 cancellation small; q_c(x_c) = |z|^2 exactly.
 // Mode 0 averages pi g(x_i) + (1-pi) g(x_j) (the component draw integrated
-// out); mode 1 takes g(x_i) if u_s < pi else g(x_j).
+// out); mode 1 takes g(x_i) if u_s < pi else g(x_j).  Mode 2 is mode 0 with
+// the cross-entropy term in closed form: -E[log q_m] = 1/2 log det(2 pi Sigma_m)
+// + 3/2, so q_m(x)/2 above becomes 3/2 and only the entropy is sampled.
+// Mode 3 is the MSE surrogate |mu_i - mu_j|^2 + ||Sigma_i - Sigma_j||_F^2
+// (the Sec. 4 ablation), evaluated in FP32 with no FP64 path.
 // A merged covariance whose FP32 Cholesky pivots fall below 1e-2 of the
 // matching diagonal entries (near-degenerate) is redone entirely in FP64.
 #include "ngs_device.cuh"
@@ -166,6 +170,15 @@ __device__ __noinline__ double dgeo_fp64(const float *xyz, const float *ls, cons
     G64 gi, gj;
     splat64(xyz, ls, rot, logit, i, gi);
     splat64(xyz, ls, rot, logit, j, gj);
+    if (mode == 3) {
+        double r = 0;
+        for (int a = 0; a < 3; a++) r += (gi.mu[a] - gj.mu[a]) * (gi.mu[a] - gj.mu[a]);
+        for (int t = 0; t < 6; t++) {
+            const double dd = gi.Sig[t] - gj.Sig[t];
+            r += (t == 0 || t == 3 || t == 5 ? 1.0 : 2.0) * dd * dd;
+        }
+        return r;
+    }
     double ld = gi.lw - gj.lw;
     double lpi = -softplus_d(-ld), lpj = -softplus_d(ld);
     double pi = exp(lpi), pj = exp(lpj);
@@ -217,9 +230,9 @@ __device__ __noinline__ double dgeo_fp64(const float *xyz, const float *ls, cons
             double qj = side == 1 ? zz : maha64_splat(gj, vj);
             double y0 = vm[0] / l00, y1 = (vm[1] - l10 * y0) / l11, y2 = (vm[2] - l20 * y0 - l21 * y1) / l22;
             double qm = y0 * y0 + y1 * y1 + y2 * y2;
-            gvals[side] = lse2_d(lpi + ai - 0.5 * qi, lpj + aj - 0.5 * qj) + 0.5 * qm;
+            gvals[side] = lse2_d(lpi + ai - 0.5 * qi, lpj + aj - 0.5 * qj) + (mode == 2 ? 1.5 : 0.5 * qm);
         }
-        if (mode == 0) acc += pi * gvals[0] + pj * gvals[1];
+        if (mode != 1) acc += pi * gvals[0] + pj * gvals[1];
         else acc += ((double)us[s] < pi) ? gvals[0] : gvals[1];
     }
     return acc / S;
@@ -243,10 +256,11 @@ __device__ __forceinline__ void load_R(const Rec &r, float *R, float *invs) {
     invs[0] = c.y; invs[1] = c.z; invs[2] = c.w;
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(256, 3)
     k_edge_cost(const int4 *__restrict__ erec, int64_t m, const float *__restrict__ rec,
                 const float *__restrict__ sh, int F,
-                const float *__restrict__ zs, const float *__restrict__ us, int S, int mode,
+                const float *__restrict__ zs, const float *__restrict__ us, int S,
                 float lg, float la, int policy, const float *__restrict__ xyz,
                 const float *__restrict__ ls, const float *__restrict__ rot,
                 const float *__restrict__ logit, float *__restrict__ cost_slot,
@@ -303,6 +317,21 @@ __global__ void __launch_bounds__(256, 3)
         const int32_t sl = er.x;
         const int64_t i = er.y, j = er.z;
         const Rec Ri{(const float4 *)(rec + i * REC)}, Rj{(const float4 *)(rec + j * REC)};
+        if (MODE == 3) {
+            const float4 i0 = Ri.g(0), j0 = Rj.g(0), i4 = Ri.g(4), i5 = Ri.g(5), j4 = Rj.g(4),
+                         j5 = Rj.g(5);
+            const float dx = i0.x - j0.x, dy = i0.y - j0.y, dz = i0.z - j0.z;
+            // Sigma (00 01 02 11 12 22): off-diagonal entries count twice
+            const float e00 = i4.x - j4.x, e01 = i4.y - j4.y, e02 = i4.z - j4.z;
+            const float e11 = i4.w - j4.w, e12 = i5.x - j5.x, e22 = i5.y - j5.y;
+            const float dgeo = dx * dx + dy * dy + dz * dz + e00 * e00 + e11 * e11 + e22 * e22 +
+                               2.f * (e01 * e01 + e02 * e02 + e12 * e12);
+            const float c = lg * dgeo + la * dapp;
+            cost_slot[sl] = c;
+            if (er.w >= 0) cost_slot[er.w] = c;
+            if (cost_out) cost_out[e] = c;
+            continue;
+        }
         // ---- MPMM moments (Eqs. vm_weights, vm_cov)
         const float4 i0 = Ri.g(0), j0 = Rj.g(0);
         const float ld = i0.w - j0.w;
@@ -369,15 +398,15 @@ __global__ void __launch_bounds__(256, 3)
                 float v1[3] = {d[0] + yi[0], d[1] + yi[1], d[2] + yi[2]};
                 float v2[3] = {pj * d[0] + yi[0], pj * d[1] + yi[1], pj * d[2] + yi[2]};
                 const float qj = maha_splat(Rn, invs_j, v1);
-                const float qm = maha_chol(L, il, v2);
-                const float gi = lse2(ci - 0.5f * zz, cj - 0.5f * qj) + 0.5f * qm;
+                const float gi = lse2(ci - 0.5f * zz, cj - 0.5f * qj) +
+                                 (MODE == 2 ? 1.5f : 0.5f * maha_chol(L, il, v2));
                 // x = x_j
                 float w1[3] = {yj[0] - d[0], yj[1] - d[1], yj[2] - d[2]};
                 float w2[3] = {yj[0] - pi * d[0], yj[1] - pi * d[1], yj[2] - pi * d[2]};
                 const float qi = maha_splat(Rm, invs_i, w1);
-                const float qm2 = maha_chol(L, il, w2);
-                const float gj = lse2(ci - 0.5f * qi, cj - 0.5f * zz) + 0.5f * qm2;
-                acc += mode == 0 ? (pi * gi + pj * gj) : (us[s] < pi ? gi : gj);
+                const float gj = lse2(ci - 0.5f * qi, cj - 0.5f * zz) +
+                                 (MODE == 2 ? 1.5f : 0.5f * maha_chol(L, il, w2));
+                acc += MODE != 1 ? (pi * gi + pj * gj) : (us[s] < pi ? gi : gj);
             }
             dgeo = acc / (float)S;
         } else {
@@ -454,11 +483,14 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
     unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c, c->b_status, 64);
     int2 *list = ws<int2>(c, c->b_fp64list, m);
     NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, c->st));
+    const int mode = c->prm.cost_mode;
+    auto kern = mode == 1 ? k_edge_cost<1> : mode == 2 ? k_edge_cost<2> : mode == 3 ? k_edge_cost<3>
+                                                                                    : k_edge_cost<0>;
     launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, c->tune.cost_blocks_per_sm)), dim3(256), 0,
-           k_edge_cost,
+           kern,
            (const int4 *)(lex ? g.erec_lex : g.erec), m, (const float *)rec, (const float *)s.sh,
            s.F, (const float *)zs,
-           (const float *)(zs + 3 * S), S, c->prm.cost_mode, c->prm.lambda_geo,
+           (const float *)(zs + 3 * S), S, c->prm.lambda_geo,
            c->prm.lambda_app, c->prm.fp64_policy, (const float *)s.xyz, (const float *)s.ls,
            (const float *)s.rot, (const float *)s.logit, g.cost_slot, lex ? cost_out : nullptr,
            cnt, list);

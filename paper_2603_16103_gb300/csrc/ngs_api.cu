@@ -192,7 +192,7 @@ extern "C" void ngs_default_params(ngs_params *p) {
 static int check_params(const ngs_params *p) {
     if (p->k < 1 || p->k > NGS_MAX_K) return 0;
     if (p->mc_samples < 1 || p->mc_samples > NGS_MAX_S) return 0;
-    if (p->cost_mode < 0 || p->cost_mode > 1) return 0;
+    if (p->cost_mode < 0 || p->cost_mode > 3) return 0;
     if (!(p->tau >= 0.0 && p->tau < 1.0)) return 0;
     if (p->max_passes < 0 || p->max_passes > NGS_STATS_MAX_PASSES) return 0;
     if (p->fp64_policy < 0 || p->fp64_policy > 2) return 0;

@@ -76,7 +76,8 @@ def test_batch_log_uniform_sizes(ngs):
 
 
 @pytest.mark.parametrize("params", [dict(prefilter=0), dict(fp64_policy=2, k=8),
-                                    dict(cost_mode=1, mc_samples=4)])
+                                    dict(cost_mode=1, mc_samples=4), dict(cost_mode=2, mc_samples=2),
+                                    dict(cost_mode=3)])
 def test_batch_params(ngs, params):
     scenes = [small_scene(n, seed=20 + n % 7, kind=kind)
               for n, kind in [(6000, "patch"), (2500, "unit"), (12000, "patch")]]
