@@ -80,11 +80,12 @@ typedef struct {
  *               (Eq. Equ:cost has both at 1; default 1, 1)
  *   seed        seed of the per-pass common random numbers
  *   max_passes  upper bound on simplification passes (default 64)
- *   fp64_policy 0: merged covariance eigendecomposition in FP64 and FP64
- *               log-det for near-degenerate merged covariances (default);
+ *   fp64_policy 0: merged covariance eigendecomposition finished in
+ *               float-float (about 48-bit) arithmetic, and FP64 log-det for
+ *               near-degenerate merged covariances (default);
  *               1: additionally FP64 cost terms for edges with a
- *               near-degenerate endpoint; 2: FP64 eigendecomposition only
- *               for ill-conditioned merged covariances
+ *               near-degenerate endpoint; 2: the float-float finish only for
+ *               ill-conditioned merged covariances
  *   prefilter   1: ngs_simplify first applies the opacity pre-filter
  *   eig_floor   lower bound on merged covariance eigenvalues (default 1e-30)
  */

@@ -12,8 +12,9 @@
 //   Sigma_m = V diag(lambda) V^T -> log-scale = log(max(lambda, floor)) / 2,
 //             rotation = V as a unit quaternion.
 // The eigendecomposition starts with an FP32 cyclic Jacobi and is finished
-// in FP64 (Sigma_m assembled in FP64, one FP64 Jacobi sweep warm-started
-// from the re-orthonormalised FP32 eigenvectors).  Canonical form: eigenvalues descending,
+// in float-float arithmetic (Sigma_m assembled in float-float, one Jacobi
+// sweep warm-started from the re-orthonormalised FP32 eigenvectors; see
+// finish_ff).  Canonical form: eigenvalues descending,
 // each eigenvector's largest-magnitude component positive, det V = +1,
 // quaternion with w >= 0.
 #include "ngs_device.cuh"
@@ -90,94 +91,175 @@ __device__ __forceinline__ T diag2(const T *A) {
     return A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
 }
 
-// 1/sqrt(x) for x of order one (a squared norm of a nearly unit vector): an
-// FP32 estimate (relative error below 2^-22) refined by one FP64 Newton step,
-// which leaves a relative error below 1e-13.
-__device__ __forceinline__ double rsqrt64(double x) {
-    const double y = (double)rsqrtf((float)x);
-    return y * (1.5 - 0.5 * x * y * y);
-}
+// ---------------------------------------------------------------- float-float
+// Extended precision on the FP32 pipes: a value is the unevaluated sum h + l
+// of two floats with |l| <= ulp(h) / 2 (Dekker 1971), about 48 significant
+// bits.  Built from the error-free transformations TwoSum (Knuth), Fast2Sum
+// (Dekker, |a| >= |b|) and TwoProduct with a fused multiply-add.  Explicit
+// _rn intrinsics keep the compiler from contracting or reassociating them.
+struct ff {
+    float h, l;
+};
 
-__device__ __forceinline__ void quat_rot64(const float *q, double *R) {
-    double w = q[0], x = q[1], y = q[2], z = q[3];
-    const double inv = rsqrt64(w * w + x * x + y * y + z * z);
-    w *= inv; x *= inv; y *= inv; z *= inv;
-    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
-    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+__device__ __forceinline__ ff ff_fast2(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// exact product of two floats
+__device__ __forceinline__ ff ff_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// x + y; absolute error about 2^-46 (|x| + |y|)
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    const ff s = ff_two_sum(x.h, y.h);
+    return ff_fast2(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+// x * b for a float b
+__device__ __forceinline__ ff ff_mulf(ff x, float b) {
+    const float p = __fmul_rn(x.h, b);
+    return ff_fast2(p, __fmaf_rn(x.l, b, __fmaf_rn(x.h, b, -p)));
+}
+// x * y
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = __fmul_rn(x.h, y.h);
+    const float e = __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, __fmaf_rn(x.h, y.h, -p)));
+    return ff_fast2(p, e);
+}
+__device__ __forceinline__ bool ff_gt(ff x, ff y) { return x.h > y.h || (x.h == y.h && x.l > y.l); }
 
-// One FP64 Jacobi sweep on a nearly diagonal symmetric B (upper triangle
-// b[0..5] = 00 01 02 11 12 22), V <- V J, B <- J^T B J.  When the
-// off-diagonal entry is tiny against the diagonal gap the rotation is the
-// small-angle one, t = b_pq / (b_qq - b_pp) (in FP32: its relative error only
-// scales the residual), c = 1 - t^2/2, s = t c, orthogonal to O(t^4); other
-// rotations use the exact formula in FP64.  Only the entries the rotation
-// changes are updated: b_pp, b_qq, b_rp, b_rq (r the third index).
-__device__ __forceinline__ void refine_sweep64(double *b, double *V) {
+// Extended-precision finish of the eigendecomposition of Sigma_m.
+//   * Q: the FP32 Jacobi eigenvectors, re-orthonormalised by Gram-Schmidt in
+//     FP32, so Q^T Q = I + E with |E| ~ 1e-7.
+//   * Sigma_m assembled in float-float from the FP32 inputs (rotations, s^2,
+//     pi, and the exact centre difference), B = Q^T Sigma_m Q in float-float.
+//   * One Jacobi sweep on the nearly diagonal B: rotation angles in FP32, the
+//     updates of B in float-float, V = Q J in FP32.
+// The congruence with a nearly orthonormal Q moves every eigenvalue by a
+// relative |E| at most (Ostrowski's theorem), so small eigenvalues keep about
+// FP32 relative accuracy however ill-conditioned Sigma_m is; the float-float
+// assembly and rotation are what remove the cancellation of the FP32 pass.
+__device__ __forceinline__ void finish_ff(const float *Ri, const float *Rj, const float *s2i,
+                                          const float *s2j, float pi, float pj, const float *mi,
+                                          const float *mj, float *V, ff *lam) {
+    // Gram-Schmidt of the columns of V
+    float Q[9];
+    {
+        const float n0 = rsqrtf(V[0] * V[0] + V[3] * V[3] + V[6] * V[6]);
+        Q[0] = V[0] * n0; Q[3] = V[3] * n0; Q[6] = V[6] * n0;
+        const float dp = Q[0] * V[1] + Q[3] * V[4] + Q[6] * V[7];
+        float c1[3] = {V[1] - dp * Q[0], V[4] - dp * Q[3], V[7] - dp * Q[6]};
+        const float n1 = rsqrtf(c1[0] * c1[0] + c1[1] * c1[1] + c1[2] * c1[2]);
+        Q[1] = c1[0] * n1; Q[4] = c1[1] * n1; Q[7] = c1[2] * n1;
+        Q[2] = Q[3] * Q[7] - Q[6] * Q[4];
+        Q[5] = Q[6] * Q[1] - Q[0] * Q[7];
+        Q[8] = Q[0] * Q[4] - Q[3] * Q[1];
+    }
+    // Sigma_m, upper triangle (00 01 02 11 12 22)
+    ff d[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) d[a] = ff_two_sum(mi[a], -mj[a]);
+    const ff pp = ff_prod(pi, pj);
+    ff S[6];
+    {
+        int idx = 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = a; b < 3; b++, idx++) {
+                ff si = ff_mulf(ff_prod(Ri[3 * a], s2i[0]), Ri[3 * b]);
+                ff sj = ff_mulf(ff_prod(Rj[3 * a], s2j[0]), Rj[3 * b]);
+#pragma unroll
+                for (int k = 1; k < 3; k++) {
+                    si = ff_add(si, ff_mulf(ff_prod(Ri[3 * a + k], s2i[k]), Ri[3 * b + k]));
+                    sj = ff_add(sj, ff_mulf(ff_prod(Rj[3 * a + k], s2j[k]), Rj[3 * b + k]));
+                }
+                ff v = ff_add(ff_mulf(si, pi), ff_mulf(sj, pj));
+                S[idx] = ff_add(v, ff_mul(ff_mul(pp, d[a]), d[b]));
+            }
+    }
+    // T = Sigma_m Q, B = Q^T T (upper triangle)
+    const int sym[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+    ff T[9], B[6];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            ff t = ff_mulf(S[sym[3 * a]], Q[b]);
+            t = ff_add(t, ff_mulf(S[sym[3 * a + 1]], Q[3 + b]));
+            T[3 * a + b] = ff_add(t, ff_mulf(S[sym[3 * a + 2]], Q[6 + b]));
+        }
+    {
+        int idx = 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = a; b < 3; b++, idx++) {
+                ff t = ff_mulf(T[b], Q[a]);
+                t = ff_add(t, ff_mulf(T[3 + b], Q[3 + a]));
+                B[idx] = ff_add(t, ff_mulf(T[6 + b], Q[6 + a]));
+            }
+    }
+    // one sweep, V <- Q J
+#pragma unroll
+    for (int k = 0; k < 9; k++) V[k] = Q[k];
 #pragma unroll
     for (int pq = 0; pq < 3; pq++) {
         const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
         // upper-triangle slots of (p,p), (q,q), (p,q), (r,p), (r,q), r = 3 - p - q
         const int ipp = p == 0 ? 0 : 3, iqq = q == 1 ? 3 : 5;
         const int ipq = pq == 0 ? 1 : (pq == 1 ? 2 : 4);
-        const int irp = pq == 0 ? 2 : 1;  // (2,0) / (1,0) / (0,1)
-        const int irq = pq == 2 ? 2 : 4;  // (2,1) / (1,2) / (0,2)
-        const double apq = b[ipq];
-        if (apq == 0.0) continue;
-        const double app = b[ipp], aqq = b[iqq];
-        const double diff = aqq - app;
-        double c, s;
-        if (fabs(apq) < 1e-4 * fabs(diff)) {
-            const double t = (double)((float)apq / (float)diff);
-            c = 1.0 - 0.5 * t * t;
+        const int irp = pq == 0 ? 2 : 1;
+        const int irq = pq == 2 ? 2 : 4;
+        const ff apq = B[ipq];
+        if (apq.h == 0.f) continue;
+        const ff app = B[ipp], aqq = B[iqq];
+        const float diff = ff_add(aqq, {-app.h, -app.l}).h;
+        float c, s;
+        if (fabsf(apq.h) < 1e-4f * fabsf(diff)) {
+            // small angle: t = b_pq / (b_qq - b_pp), c = 1 - t^2/2, s = t c
+            const float t = apq.h / diff;
+            c = 1.0f - 0.5f * t * t;
             s = t * c;
         } else {
-            const double tau = diff / (2.0 * apq);
-            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+            const float tau = diff / (2.0f * apq.h);
+            const float t = (tau >= 0.f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+            c = rsqrtf(1.0f + t * t);
             s = t * c;
         }
-        const double cc = c * c, ss = s * s, cs2 = 2.0 * c * s;
-        const double arp = b[irp], arq = b[irq];
-        b[ipp] = cc * app - cs2 * apq + ss * aqq;
-        b[iqq] = ss * app + cs2 * apq + cc * aqq;
-        b[ipq] = 0.0;
-        b[irp] = c * arp - s * arq;
-        b[irq] = s * arp + c * arq;
+        const ff cc = ff_prod(c, c), ss = ff_prod(s, s), cs2 = ff_prod(2.0f * c, s);
+        const ff arp = B[irp], arq = B[irq];
+        const ff mid = ff_mul(cs2, apq);
+        B[ipp] = ff_add(ff_add(ff_mul(cc, app), {-mid.h, -mid.l}), ff_mul(ss, aqq));
+        B[iqq] = ff_add(ff_add(ff_mul(ss, app), mid), ff_mul(cc, aqq));
+        B[ipq] = {0.f, 0.f};
+        B[irp] = ff_add(ff_mulf(arp, c), ff_mulf(arq, -s));
+        B[irq] = ff_add(ff_mulf(arp, s), ff_mulf(arq, c));
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const double vkp = V[3 * k + p], vkq = V[3 * k + q];
+            const float vkp = V[3 * k + p], vkq = V[3 * k + q];
             V[3 * k + p] = c * vkp - s * vkq;
             V[3 * k + q] = s * vkp + c * vkq;
         }
     }
-}
-
-// Sigma = R diag(s2) R^T in FP64 from an FP64 rotation and FP32 squared
-// scales, upper triangle (00 01 02 11 12 22)
-__device__ __forceinline__ void rot_cov6_64(const double *R, const float *s2, double *S6) {
-    double Rs[9];
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) Rs[3 * a + k] = R[3 * a + k] * (double)s2[k];
-    int idx = 0;
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int b = a; b < 3; b++, idx++)
-            S6[idx] = Rs[3 * a] * R[3 * b] + Rs[3 * a + 1] * R[3 * b + 1] + Rs[3 * a + 2] * R[3 * b + 2];
+    lam[0] = B[0];
+    lam[1] = B[3];
+    lam[2] = B[5];
 }
 
 // canonical eigen form + quaternion (w >= 0)
-__device__ void canonical_quat(double *lam, double *V, float *q_out) {
+__device__ void canonical_quat(ff *lam, float *V, float *q_out) {
     // sort descending (3-element network), permuting columns
 #define SWAPC(a, b)                                                           \
-    if (lam[b] > lam[a]) {                                                    \
-        double t = lam[a]; lam[a] = lam[b]; lam[b] = t;                       \
+    if (ff_gt(lam[b], lam[a])) {                                              \
+        const ff t = lam[a]; lam[a] = lam[b]; lam[b] = t;                     \
         for (int r = 0; r < 3; r++) {                                         \
-            double u = V[3 * r + a]; V[3 * r + a] = V[3 * r + b]; V[3 * r + b] = u; \
+            float u = V[3 * r + a]; V[3 * r + a] = V[3 * r + b]; V[3 * r + b] = u; \
         }                                                                     \
     }
     SWAPC(0, 1)
@@ -187,14 +269,12 @@ __device__ void canonical_quat(double *lam, double *V, float *q_out) {
     for (int cidx = 0; cidx < 3; cidx++) {
         int best = 0;
         for (int r = 1; r < 3; r++)
-            if (fabs(V[3 * r + cidx]) > fabs(V[3 * best + cidx])) best = r;
+            if (fabsf(V[3 * r + cidx]) > fabsf(V[3 * best + cidx])) best = r;
         if (V[3 * best + cidx] < 0)
             for (int r = 0; r < 3; r++) V[3 * r + cidx] = -V[3 * r + cidx];
     }
     // det V = +-1: its sign in FP32
-    float Vf[9];
-#pragma unroll
-    for (int k = 0; k < 9; k++) Vf[k] = (float)V[k];
+    const float *Vf = V;
     const float det = Vf[0] * (Vf[4] * Vf[8] - Vf[5] * Vf[7]) - Vf[1] * (Vf[3] * Vf[8] - Vf[5] * Vf[6]) +
                       Vf[2] * (Vf[3] * Vf[7] - Vf[4] * Vf[6]);
     if (det < 0.f)
@@ -336,81 +416,26 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
         if (offdiag2(A) <= 1e-14f * diag2(A)) break;
         jacobi_sweep<float>(A, V);
     }
-    double lam[3], V64[9];
+    ff lam[3];
     const float lmin = fminf(fminf(A[0], A[4]), A[8]), lmax = fmaxf(fmaxf(A[0], A[4]), A[8]);
-    const bool fp64 = policy != 2 || !(lmin > 1e-4f * lmax);
-    if (fp64) {
-        // FP64 finish: Sigma_m assembled in FP64 (rotations normalised in FP64,
-        // s^2 and pi taken from their FP32 values), rotated into the
-        // re-orthonormalised FP32 eigenbasis, then one FP64 Jacobi sweep.
-        double Ri64[9], Rj64[9], Si6[6], Sj6[6], S64[9];
-        quat_rot64(qi, Ri64);
-        quat_rot64(qj, Rj64);
-        rot_cov6_64(Ri64, s2i, Si6);
-        rot_cov6_64(Rj64, s2j, Sj6);
-        const double pid = (double)pi, pjd = (double)pj, ppd64 = pid * pjd;
-        const double dd[3] = {(double)mi[0] - mj[0], (double)mi[1] - mj[1], (double)mi[2] - mj[2]};
-        {
-            int idx = 0;
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-#pragma unroll
-                for (int b = a; b < 3; b++, idx++) {
-                    const double v = pid * Si6[idx] + pjd * Sj6[idx] + ppd64 * dd[a] * dd[b];
-                    S64[3 * a + b] = v;
-                    S64[3 * b + a] = v;
-                }
-        }
-        // Gram-Schmidt of the FP32 eigenvectors (columns of V)
-        double Q[9];
-#pragma unroll
-        for (int k = 0; k < 9; k++) Q[k] = V[k];
-        {
-            const double n0 = rsqrt64(Q[0] * Q[0] + Q[3] * Q[3] + Q[6] * Q[6]);
-            Q[0] *= n0; Q[3] *= n0; Q[6] *= n0;
-            const double dp = Q[0] * Q[1] + Q[3] * Q[4] + Q[6] * Q[7];
-            Q[1] -= dp * Q[0]; Q[4] -= dp * Q[3]; Q[7] -= dp * Q[6];
-            const double n1 = rsqrt64(Q[1] * Q[1] + Q[4] * Q[4] + Q[7] * Q[7]);
-            Q[1] *= n1; Q[4] *= n1; Q[7] *= n1;
-            Q[2] = Q[3] * Q[7] - Q[6] * Q[4];
-            Q[5] = Q[6] * Q[1] - Q[0] * Q[7];
-            Q[8] = Q[0] * Q[4] - Q[3] * Q[1];
-        }
-        // B = Q^T S64 Q (nearly diagonal), upper triangle
-        double T[9], B[6];
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-#pragma unroll
-            for (int b = 0; b < 3; b++)
-                T[3 * a + b] = S64[3 * a] * Q[b] + S64[3 * a + 1] * Q[3 + b] + S64[3 * a + 2] * Q[6 + b];
-        {
-            int idx = 0;
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-#pragma unroll
-                for (int b = a; b < 3; b++, idx++)
-                    B[idx] = Q[a] * T[b] + Q[3 + a] * T[3 + b] + Q[6 + a] * T[6 + b];
-        }
-        refine_sweep64(B, Q);
-        lam[0] = B[0]; lam[1] = B[3]; lam[2] = B[5];
-#pragma unroll
-        for (int k = 0; k < 9; k++) V64[k] = Q[k];
+    if (policy != 2 || !(lmin > 1e-4f * lmax)) {
+        finish_ff(Ri, Rj, s2i, s2j, pi, pj, mi, mj, V, lam);
     } else {
-        lam[0] = A[0]; lam[1] = A[4]; lam[2] = A[8];
-#pragma unroll
-        for (int k = 0; k < 9; k++) V64[k] = V[k];
+        lam[0] = {A[0], 0.f};
+        lam[1] = {A[4], 0.f};
+        lam[2] = {A[8], 0.f};
     }
     float q[4];
-    canonical_quat(lam, V64, q);
+    canonical_quat(lam, V, q);
     int hits = 0;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        double l = lam[a];
-        if (!(l > eig_floor)) {
-            l = eig_floor;
+        float l = lam[a].h + lam[a].l;
+        if (!((double)lam[a].h + (double)lam[a].l > eig_floor)) {
+            l = (float)eig_floor;
             hits = 1;
         }
-        out.ls[3 * o + a] = 0.5f * logf((float)l);
+        out.ls[3 * o + a] = 0.5f * logf(l);
     }
 #pragma unroll
     for (int k = 0; k < 4; k++) out.rot[4 * o + k] = q[k];

@@ -63,6 +63,38 @@ __global__ void k_scan_partials(int32_t *part, int64_t nb) {
     if (threadIdx.x == 0) part[nb] = carry;
 }
 
+// Same result with 16-byte accesses: the tile is taken in SCAN_ITEMS / 4
+// rounds of 4 consecutive items per thread, so every warp load and store
+// covers 512 contiguous bytes (in and out 16-byte aligned; in == out allowed).
+__global__ void k_scan_apply_v4(const int32_t *in, int32_t *out, int64_t n, const int32_t *part) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int carry = part[blockIdx.x];
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS / 4; r++) {
+        const int64_t i0 = base + (int64_t)r * (4 * SCAN_THREADS) + 4 * threadIdx.x;
+        int4 v = make_int4(0, 0, 0, 0);
+        if (i0 + 3 < n) {
+            v = *(const int4 *)(in + i0);
+        } else if (i0 < n) {
+            v.x = in[i0];
+            if (i0 + 1 < n) v.y = in[i0 + 1];
+            if (i0 + 2 < n) v.z = in[i0 + 2];
+        }
+        int tot;
+        const int ex = block_excl_scan(v.x + v.y + v.z + v.w, &tot) + carry;
+        const int4 o = make_int4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
+        if (i0 + 3 < n) {
+            *(int4 *)(out + i0) = o;
+        } else if (i0 < n) {
+            out[i0] = o.x;
+            if (i0 + 1 < n) out[i0 + 1] = o.y;
+            if (i0 + 2 < n) out[i0 + 2] = o.z;
+        }
+        carry += tot;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = part[gridDim.x];
+}
+
 __global__ void k_scan_apply(const int32_t *in, int32_t *out, int64_t n, const int32_t *part) {
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS];
@@ -231,8 +263,12 @@ void scan_i32(ngs_ctx *c, const int32_t *in, int32_t *out, int64_t n) {
     int32_t *part = ws<int32_t>(c, c->b_scan_part, nb + 1);
     launch(c, "scan_reduce", dim3((unsigned)nb), dim3(SCAN_THREADS), 0, k_scan_reduce, in, n, part);
     launch(c, "scan_partials", dim3(1), dim3(1024), 0, k_scan_partials, part, nb);
-    launch(c, "scan_apply", dim3((unsigned)nb), dim3(SCAN_THREADS), 0, k_scan_apply, in, out, n,
-           (const int32_t *)part);
+    if ((((uintptr_t)in | (uintptr_t)out) & 15) == 0)
+        launch(c, "scan_apply", dim3((unsigned)nb), dim3(SCAN_THREADS), 0, k_scan_apply_v4, in, out,
+               n, (const int32_t *)part);
+    else
+        launch(c, "scan_apply", dim3((unsigned)nb), dim3(SCAN_THREADS), 0, k_scan_apply, in, out, n,
+               (const int32_t *)part);
 }
 
 void radix_sort_u32(ngs_ctx *c, uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp,

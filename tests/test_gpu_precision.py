@@ -85,5 +85,8 @@ def test_precision_report(ngs, policy):
         assert rep["opacity_rel"]["max"] <= 1e-5
         assert rep["mu_rel"]["max"] <= 1e-5
         assert rep["mu_err_over_fp32_spacing"]["max"] <= 4
+        # the extended-precision eigen finish keeps small eigenvalues accurate
+        # (sorted log-scales); policy 2 skips it for well-conditioned merges
+        assert rep["log_scale_abs"]["max"] <= (1e-5 if policy != 2 else 1e-4)
     finally:
         c.close()
