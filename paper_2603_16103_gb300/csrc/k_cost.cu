@@ -257,7 +257,7 @@ __device__ __forceinline__ void load_R(const Rec &r, float *R, float *invs) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
     k_edge_cost(const int4 *__restrict__ erec, int64_t m, const float *__restrict__ rec,
                 const float *__restrict__ sh, int F,
                 const float *__restrict__ zs, const float *__restrict__ us, int S,

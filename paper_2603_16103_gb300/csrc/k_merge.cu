@@ -427,12 +427,13 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
     }
     float q[4];
     canonical_quat(lam, V, q);
+    const float floor_f = (float)eig_floor;
     int hits = 0;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         float l = lam[a].h + lam[a].l;
-        if (!((double)lam[a].h + (double)lam[a].l > eig_floor)) {
-            l = (float)eig_floor;
+        if (!(l > floor_f)) {
+            l = floor_f;
             hits = 1;
         }
         out.ls[3 * o + a] = 0.5f * logf(l);
@@ -601,8 +602,8 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
     }
     int32_t *keep = ws<int32_t>(c, c->b_keep, n + 1);
     int32_t *pos = ws<int32_t>(c, c->b_pos, n + 1);
-    int32_t *mflag = ws<int32_t>(c, c->b_flag, 2 * (n + 1));
-    int32_t *mpos = mflag + (n + 1);
+    int32_t *mflag = ws<int32_t>(c, c->b_flag, 2 * (n + 4));
+    int32_t *mpos = mflag + ((n + 4) & ~(int64_t)3);  // 16-byte aligned for the vector scan
     const unsigned grid = grid_stride_blocks(c, n, 256, 8);
     launch(c, "keep_flags", dim3(grid), dim3(256), 0, k_keep_flags, n, role, keep, mflag);
     scan_i32(c, keep, pos, n);
