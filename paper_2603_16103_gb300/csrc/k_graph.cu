@@ -3,7 +3,9 @@
 // directed neighbour u = nbr[s] of v.  The undirected edge {v,u} exists when
 // u is in v's list or v is in u's list.
 //   * A slot is mutual when v is also in u's list; mirror[s] is then the
-//     partner slot, otherwise -1.
+//     partner slot, otherwise -1.  (The row form, for k dividing 32, stores a
+//     slot code instead that also carries which endpoint is lower; see
+//     k_slot_classify_rows.)
 //   * Each undirected edge has exactly one canonical slot: a non-mutual slot,
 //     or the mutual slot whose row has the lower canonical id.  erec[] lists
 //     one record (slot, lo row, hi row, mirror slot) per canonical slot in
@@ -129,13 +131,16 @@ __global__ void k_slot_classify_rows(const int32_t *__restrict__ nbr, int64_t n,
             const int x = __shfl_sync(FULL_MASK, tpr[it], (lane % RPI) * LPR);
             if (lane / RPI == it) tp = x;
         }
+        // slot code for the fill: partner slot (mutual, v the lower id), -3
+        // (mutual, not canonical), -1 / -2 (not mutual, v lower / higher)
         bool canon = false;
         if (valid) {
+            const bool vlo = cid_of(cid, v) < cid_of(cid, u);
             if (tp >= 0) {
-                mirror[s] = u * K + tp;
-                canon = cid_of(cid, v) < cid_of(cid, u);
+                mirror[s] = vlo ? u * K + tp : -3;
+                canon = vlo;
             } else {
-                mirror[s] = -1;
+                mirror[s] = vlo ? -1 : -2;
                 canon = true;
                 atomicAdd(&revcnt[u], 1);
             }
@@ -146,8 +151,9 @@ __global__ void k_slot_classify_rows(const int32_t *__restrict__ nbr, int64_t n,
     }
 }
 
+// Fill from the slot codes of k_slot_classify_rows: no canonical-id loads.
 __global__ void k_slot_fill_rows(const int32_t *__restrict__ nbr, int64_t n, int k,
-                                 const int32_t *__restrict__ cid, const int32_t *__restrict__ mirror,
+                                 const int32_t *__restrict__ code,
                                  const int32_t *__restrict__ rowpos,
                                  const int32_t *__restrict__ rev_ptr, int32_t *revfill, int4 *erec,
                                  int32_t *rev) {
@@ -156,21 +162,21 @@ __global__ void k_slot_fill_rows(const int32_t *__restrict__ nbr, int64_t n, int
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < m; b0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = b0 + threadIdx.x;
         bool canon = false;
-        int32_t u = 0, mr = -1, v = 0;
+        int32_t u = 0, c = -3, v = 0;
         if (s < m) {
             v = (int32_t)(s / k);
             u = nbr[s];
-            mr = mirror[s];
-            canon = mr < 0 || cid_of(cid, v) < cid_of(cid, u);
+            c = code[s];
+            canon = c != -3;
         }
         const unsigned cm = __ballot_sync(FULL_MASK, canon);
         const int first = lane - lane % k;
         if (canon) {
             const int32_t pos = rowpos[v] + __popc(cm & ((1u << lane) - 1u) & ~((1u << first) - 1u));
-            const bool vlo = cid_of(cid, v) < cid_of(cid, u);
-            erec[pos] = make_int4((int32_t)s, vlo ? v : u, vlo ? u : v, mr);
+            const bool vlo = c >= 0 || c == -1;
+            erec[pos] = make_int4((int32_t)s, vlo ? v : u, vlo ? u : v, c >= 0 ? c : -1);
         }
-        if (s < m && mr < 0) rev[rev_ptr[u] + atomicAdd(&revfill[u], 1)] = (int32_t)s;
+        if (c == -1 || c == -2) rev[rev_ptr[u] + atomicAdd(&revfill[u], 1)] = (int32_t)s;
     }
 }
 
@@ -249,7 +255,7 @@ void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
     g.rev = ws<int32_t>(c, c->b_upc, nrev);
     if (rows)
         launch(c, "slot_fill", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0,
-               k_slot_fill_rows, nbr, n, k, g.cid, (const int32_t *)g.mirror,
+               k_slot_fill_rows, nbr, n, k, (const int32_t *)g.mirror,
                (const int32_t *)epos, (const int32_t *)g.rev_ptr, revfill, g.erec, g.rev);
     else
         launch(c, "slot_fill", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0, k_slot_fill,

@@ -79,7 +79,7 @@ struct GraphDev {
     int k_eff;
     const int32_t *cid;     // canonical ids (nullptr = identity)
     const int32_t *nbr;     // n*k directed neighbours (slot s = v*k + t)
-    int32_t *mirror;        // n*k partner slot of a mutual edge, else -1
+    int32_t *mirror;        // n*k partner slot of a mutual edge, else -1 (row form: slot code)
     int4 *erec;             // |E| edge records (slot, lo row, hi row, mirror slot)
     int32_t *rev_ptr;       // n+1 offsets into rev
     int32_t *rev;           // non-mutual slots pointing at each vertex
