@@ -58,9 +58,10 @@ ALGO = {
 # (the profiles/ summaries give the commands and the raw counters).
 NCU_TRAFFIC_PER_SPLAT = {
     "knn_k16": 42.37,        # 42.36 MB over 999,792 queries (knn_grid_patches1m.md)
-    "edge_cost": 561.7,      # 561.63 MB over 999,792 splats (edge_cost_patches1m.md)
-    "slot_classify": 105.8,  # 105.77 MB over 999,792 splats (slot_classify_patches1m.md)
-    "merge": 342.6,          # 342.49 MB, pass of 999,792 splats (merge_patches1m.md)
+    "edge_cost": 548.4,      # 548.31 MB over 999,792 splats (edge_cost_patches1m.md)
+    "slot_classify": 104.8,  # 104.76 MB over 999,792 splats (slot_classify_patches1m.md)
+    "slot_fill": 251.1,      # 251.06 MB over 999,792 splats (slot_classify_patches1m.md)
+    "merge": 341.3,          # 341.17 MB, pass of 999,792 splats (merge_patches1m.md)
 }
 
 
