@@ -117,6 +117,13 @@ __global__ void k_compact_running(SrcRows a, SrcRows b, int64_t n, int F,
     }
 }
 
+// hdst[s] = pos[at[s]] into pinned host memory (read after a stream sync)
+__global__ void k_pos_at(const int32_t *__restrict__ pos, const int64_t *__restrict__ at, int m,
+                         int32_t *hdst) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < m) hdst[s] = pos[at[s]];
+}
+
 __global__ void k_fill_sid(const int64_t *__restrict__ start, int S, int64_t n, int32_t *sid) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
@@ -396,8 +403,7 @@ SrcRows rows(const SplatView &v) { return SrcRows{v.xyz, v.ls, v.rot, v.logit, v
 template <class T>
 T *upload(ngs_ctx *c, DevBuf &b, const T *h, size_t count) {
     T *d = (T *)ws_get(c, b, sizeof(T) * (count ? count : 1));
-    if (count)
-        NGS_CHECK_CUDA(cudaMemcpyAsync(d, h, sizeof(T) * count, cudaMemcpyHostToDevice, c->st));
+    put_small(c, d, h, sizeof(T) * count);
     return d;
 }
 
@@ -480,9 +486,9 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     // kept rows per scene: scene s keeps [pos[in0[s]], pos[in0[s+1]])
     std::vector<int64_t> kin(S + 1);
     {
-        std::vector<int32_t> hp(S + 1);
-        for (int s = 0; s <= S; s++)
-            NGS_CHECK_CUDA(cudaMemcpyAsync(&hp[s], pos + in0[s], 4, cudaMemcpyDeviceToHost, c->st));
+        int32_t *hp = (int32_t *)(c->h_pin + 64);  // pinned, S + 1 <= 4097 entries
+        launch(c, "kept_counts", dim3(blocks_for(S + 1, 256)), dim3(256), 0, k_pos_at,
+               (const int32_t *)pos, din0, S + 1, hp);
         sync_stream(c);
         for (int s = 0; s <= S; s++) kin[s] = hp[s];
     }
@@ -506,7 +512,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
             launch(c, "frames_final", dim3(blocks_for(S, 128)), dim3(128), 0, k_frames_final,
                    (const uint32_t *)acc, S, frames, bad);
         }
-        NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin + 4, bad, 4, cudaMemcpyDeviceToHost, c->st));
+        get_small(c, c->h_pin + 4, bad, 4);
         sync_stream(c);
         const uint32_t nbad = *(uint32_t *)(c->h_pin + 4);
         if (nbad) NGS_FAIL(NGS_ERR_INVALID_ARG, "%u non-finite centre coordinates", nbad);
@@ -541,12 +547,15 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         }
         A = scratch(c, c->b_sA, nf, F);
         B = multi ? scratch(c, c->b_sC, nf, F) : scratch(c, c->b_sB, nf, F);
+        // the rows' scales and rotations may still be uploading (ngs_simplify_host)
+        if (c->rest_wait) NGS_CHECK_CUDA(cudaStreamWaitEvent(c->st, c->rest_wait, 0));
         if (defer_sh) {
             // the SH rows follow once their upload has finished (ensure_sh)
             gather_rows_part(c, IN, order, A, false);
             order0 = ws<uint32_t>(c, c->b_order0, nf);
             NGS_CHECK_CUDA(cudaMemcpyAsync(order0, order, 4 * nf, cudaMemcpyDeviceToDevice, c->st));
         } else {
+            if (c->sh_wait) NGS_CHECK_CUDA(cudaStreamWaitEvent(c->st, c->sh_wait, 0));
             gather_rows(c, IN, order, A);
         }
         cidA = ws<int32_t>(c, c->b_cid, nf + 1);
@@ -574,7 +583,6 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     };
     // write stopped scenes back (canonical order) and drop them from A
     auto extract = [&](bool all) {
-        ensure_sh();
         bool any = false, left = false;
         for (int s = 0; s < S; s++) {
             stop[s] = !out_done[s] && (all || !running[s]);
@@ -582,6 +590,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
             left = left || (!out_done[s] && !stop[s]);
         }
         if (!any) return;
+        ensure_sh();
         const int64_t nA = A.n;
         if (nA > 0) {
             const int64_t *dws = upload(c, c->b_eng[E_WS], wstart.data(), S + 1);

@@ -471,12 +471,11 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
     const int S = c->prm.mc_samples;
     c->h_pin[1] = 0;  // FP64-path edge count of this call (filled below)
     if (m <= 0) return;
-    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    // the host buffer may go out of scope on return (put_small stages it)
     std::vector<float> h(4 * (size_t)S);
     host_mc_draws(c->prm.seed, pass, S, h.data(), h.data() + 3 * S);
     float *zs = ws<float>(c, c->b_rng, 4 * S);
-    NGS_CHECK_CUDA(cudaMemcpyAsync(zs, h.data(), sizeof(float) * 4 * S, cudaMemcpyHostToDevice,
-                                   c->st));
+    put_small(c, zs, h.data(), sizeof(float) * 4 * (size_t)S);
     float *rec = ws<float>(c, c->b_rec, s.n * REC);
     launch(c, "cost_prep", dim3(grid_stride_blocks(c, s.n, 256, 8)), dim3(256), 0, k_prep, s.xyz,
            s.ls, s.rot, s.logit, s.n, (const float *)zs, rec);
@@ -502,7 +501,7 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
            (const float *)(zs + 3 * S), S, c->prm.cost_mode, c->prm.lambda_geo,
            c->prm.lambda_app, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
            (const float *)s.logit, g.cost_slot, lex ? cost_out : nullptr);
-    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin + 1, cnt, 8, cudaMemcpyDeviceToHost, c->st));
+    get_small(c, c->h_pin + 1, cnt, 8);
 }
 
 void costs_to_slots(ngs_ctx *c, GraphDev &g, const float *cost_lex) {

@@ -245,9 +245,8 @@ void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
         scan_i32(c, canon, epos, m);
     }
     scan_i32(c, revcnt, g.rev_ptr, n);
-    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin, epos + (rows ? n : m), 4, cudaMemcpyDeviceToHost, c->st));
-    NGS_CHECK_CUDA(cudaMemcpyAsync((int32_t *)c->h_pin + 1, g.rev_ptr + n, 4,
-                                   cudaMemcpyDeviceToHost, c->st));
+    get_small(c, c->h_pin, epos + (rows ? n : m), 4);
+    get_small(c, (int32_t *)c->h_pin + 1, g.rev_ptr + n, 4);
     sync_stream(c);
     g.n_edges = ((int32_t *)c->h_pin)[0];
     const int64_t nrev = ((int32_t *)c->h_pin)[1];

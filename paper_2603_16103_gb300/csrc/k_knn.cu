@@ -517,8 +517,8 @@ void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
     uint8_t *small = ws<uint8_t>(c, c->b_knnsc, 16 * (S + 1) + 256);
     int32_t *dlt = (int32_t *)small;
     int64_t *doff = (int64_t *)(small + ((4 * (size_t)S + 15) & ~(size_t)15));
-    NGS_CHECK_CUDA(cudaMemcpyAsync(dlt, hlt, 4 * S, cudaMemcpyHostToDevice, c->st));
-    NGS_CHECK_CUDA(cudaMemcpyAsync(doff, hoff, 8 * (S + 1), cudaMemcpyHostToDevice, c->st));
+    put_small(c, dlt, hlt, 4 * (size_t)S);
+    put_small(c, doff, hoff, 8 * (size_t)(S + 1));
     int32_t *T = ws<int32_t>(c, c->b_nodes, tlen + 1);
     NGS_CHECK_CUDA(cudaMemsetAsync(T, 0, sizeof(int32_t) * tlen, c->st));
     launch(c, "cell_count", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_cell_count,

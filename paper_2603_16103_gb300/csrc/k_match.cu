@@ -181,6 +181,11 @@ __global__ void k_write_pairs(int64_t n, const int32_t *__restrict__ partner,
 constexpr int MS_CNT_A = 0, MS_CNT_B = 1, MS_M_A = 2, MS_M_B = 3, MS_ROUNDS = 4, MS_TOTAL = 5,
               MS_LIMIT = 6, MS_M0 = 7;
 
+// the loop state into pinned host memory (see get_small)
+__global__ void k_get_state(int32_t *hstate, const int32_t *st) {
+    if (threadIdx.x < 8) hstate[threadIdx.x] = st[threadIdx.x];
+}
+
 __global__ void k_match_ctl0(cudaGraphConditionalHandle h, int32_t *st) {
     st[MS_ROUNDS] = 1;
     st[MS_TOTAL] = st[MS_M0];
@@ -290,7 +295,8 @@ static bool match_rounds_graph(ngs_ctx *c, const GraphDev &g, int32_t *mate, int
     if (c->prof) prof_end(c, slot, a);
     cudaError_t se = cudaSuccess;
     if (le == cudaSuccess) {
-        se = cudaMemcpyAsync(hstate, stt, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+        k_get_state<<<1, 32, 0, c->st>>>(hstate, stt);
+        se = cudaGetLastError();
         if (se == cudaSuccess) se = cudaStreamSynchronize(c->st);
     }
     cudaGraphExecDestroy(exec);
@@ -338,7 +344,7 @@ int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
         NGS_CHECK_CUDA(cudaMemcpyAsync(counts, stt + MS_M0, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st));
         NGS_CHECK_CUDA(cudaMemcpyAsync(wl_counts, stt + MS_CNT_A, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st));
         int32_t *h0 = (int32_t *)(c->h_pin + 32);
-        NGS_CHECK_CUDA(cudaMemcpyAsync(h0, counts, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+        get_small(c, h0, counts, sizeof(int32_t));
         sync_stream(c);
         matched = h0[0];
         r = 1;
@@ -365,8 +371,7 @@ int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
                        (const int32_t *)cand, mate, counts + r, wl[r & 1], wl_counts + r);
             }
             int32_t *hc = (int32_t *)(c->h_pin + 32);
-            NGS_CHECK_CUDA(cudaMemcpyAsync(hc, counts + r - batch, sizeof(int32_t) * batch,
-                                           cudaMemcpyDeviceToHost, c->st));
+            get_small(c, hc, counts + r - batch, sizeof(int32_t) * batch);
             sync_stream(c);
             for (int b = 0; b < batch; b++) {
                 matched += hc[b];
@@ -428,7 +433,7 @@ int64_t partner_to_pairs(ngs_ctx *c, const int32_t *partner, const int32_t *cid,
     const unsigned grid = grid_stride_blocks(c, n, 256, 8);
     launch(c, "lo_flags", dim3(grid), dim3(256), 0, k_lo_flags, n, partner, cid, flag);
     scan_i32(c, flag, pos, n);
-    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin, pos + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+    get_small(c, c->h_pin, pos + n, sizeof(int32_t));
     launch(c, "write_pairs", dim3(grid), dim3(256), 0, k_write_pairs, n, partner,
            (const int32_t *)flag, (const int32_t *)pos, pairs_out);
     sync_stream(c);

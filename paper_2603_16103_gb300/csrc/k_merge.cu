@@ -608,8 +608,8 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
     launch(c, "keep_flags", dim3(grid), dim3(256), 0, k_keep_flags, n, role, keep, mflag);
     scan_i32(c, keep, pos, n);
     scan_i32(c, mflag, mpos, n);
-    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin, pos + n, 4, cudaMemcpyDeviceToHost, c->st));
-    NGS_CHECK_CUDA(cudaMemcpyAsync((int32_t *)c->h_pin + 1, mpos + n, 4, cudaMemcpyDeviceToHost, c->st));
+    get_small(c, c->h_pin, pos + n, 4);
+    get_small(c, (int32_t *)c->h_pin + 1, mpos + n, 4);
     sync_stream(c);
     const int64_t nout = ((int32_t *)c->h_pin)[0];
     const int64_t npairs = ((int32_t *)c->h_pin)[1];
@@ -626,7 +626,7 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
         launch(c, "merge", dim3(grid_stride_blocks(c, npairs, 128, 16)), dim3(128), 0, k_merge, ri,
                wo, (const int32_t *)list, npairs, in.F, role, (const int32_t *)pos,
                c->prm.eig_floor, c->prm.fp64_policy, hits);
-    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin + 2, hits, 8, cudaMemcpyDeviceToHost, c->st));
+    get_small(c, c->h_pin + 2, hits, 8);
     if (cid) {
         int32_t *cflag = ws<int32_t>(c, c->b_cflag, n + 1);
         int32_t *cscan = ws<int32_t>(c, c->b_cscan, n + 1);
@@ -649,7 +649,7 @@ bool pairs_to_role(ngs_ctx *c, const int32_t *pairs, int64_t npairs, int64_t n, 
     if (npairs > 0)
         launch(c, "pairs_role", dim3(grid_stride_blocks(c, npairs, 256, 8)), dim3(256), 0,
                k_pairs_role, pairs, npairs, n, role, err);
-    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin + 3, err, 4, cudaMemcpyDeviceToHost, c->st));
+    get_small(c, c->h_pin + 3, err, 4);
     sync_stream(c);
     return *(int32_t *)(c->h_pin + 3) == 0;
 }
@@ -672,7 +672,7 @@ int64_t prefilter_flags(ngs_ctx *c, const float *logit, int64_t n, double tau, i
            (const uint32_t *)med, l_tau, keep);
     int32_t *pos = ws<int32_t>(c, c->b_pos, n + 1);
     scan_i32(c, keep, pos, n);
-    NGS_CHECK_CUDA(cudaMemcpyAsync(c->h_pin, pos + n, 4, cudaMemcpyDeviceToHost, c->st));
+    get_small(c, c->h_pin, pos + n, 4);
     sync_stream(c);
     return *(int32_t *)c->h_pin;
 }

@@ -1,5 +1,7 @@
 // Device-wide primitives: exclusive scan, stable LSD radix sort and radix
 // select.  Deterministic three-phase designs (no inter-block waiting).
+#include <cstring>
+
 #include "ngs_device.cuh"
 #include "ngs_internal.h"
 
@@ -114,6 +116,26 @@ __global__ void k_scan_apply(const int32_t *in, int32_t *out, int64_t n, const i
         ex += v[r];
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = part[gridDim.x];
+}
+
+// ---------------------------------------------------------------- small uploads
+// A few bytes from the host travel as a kernel parameter instead of a copy:
+// a host-to-device copy waits behind any large upload already queued on the
+// copy engine (the SH array of ngs_simplify_host), a kernel does not.
+constexpr size_t PUT_MAX = 3072;
+struct PutPayload {
+    unsigned char b[PUT_MAX];
+};
+
+__global__ void k_put(unsigned char *dst, const PutPayload p, int bytes) {
+    for (int i = threadIdx.x; i < bytes; i += blockDim.x) dst[i] = p.b[i];
+}
+
+// The reverse for small results: a kernel stores them into pinned host
+// memory (device-accessible), so a read-back does not queue behind a large
+// upload on the copy engines either.
+__global__ void k_get(unsigned char *hdst, const unsigned char *__restrict__ src, int bytes) {
+    for (int i = threadIdx.x; i < bytes; i += blockDim.x) hdst[i] = src[i];
 }
 
 // ---------------------------------------------------------------- radix sort
@@ -326,4 +348,21 @@ void iota_u32(ngs_ctx *c, uint32_t *a, int64_t n) {
 void gather_u32(ngs_ctx *c, const uint32_t *src, const uint32_t *idx, int64_t n, uint32_t *out) {
     launch(c, "gather_u32", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_gather_u32,
            src, idx, n, out);
+}
+
+void put_small(ngs_ctx *c, void *dst, const void *src, size_t bytes) {
+    if (bytes == 0) return;
+    if (bytes > PUT_MAX) {
+        NGS_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->st));
+        return;
+    }
+    PutPayload p;
+    memcpy(p.b, src, bytes);
+    launch(c, "put", dim3(1), dim3(256), 0, k_put, (unsigned char *)dst, p, (int)bytes);
+}
+
+void get_small(ngs_ctx *c, void *hdst, const void *dsrc, size_t bytes) {
+    if (bytes == 0) return;
+    launch(c, "get", dim3(1), dim3(256), 0, k_get, (unsigned char *)hdst,
+           (const unsigned char *)dsrc, (int)bytes);
 }

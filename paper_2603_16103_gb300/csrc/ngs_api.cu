@@ -283,7 +283,8 @@ extern "C" int ngs_destroy(ngs_ctx *c) {
         cudaStreamSynchronize(c->up_st);
         cudaStreamDestroy(c->up_st);
         cudaEventDestroy(c->up_ev);
-        cudaEventDestroy(c->up_ready);
+        cudaEventDestroy(c->up_first);
+        cudaEventDestroy(c->up_rest);
     }
     delete c;
     return NGS_OK;
@@ -342,7 +343,7 @@ static void copy_rows_d2d(ngs_ctx *c, const SplatView &src, SplatView &dst, int6
 
 
 static void check_finite_frame(ngs_ctx *c, const float *frame) {
-    NGS_CHECK_CUDA(cudaMemcpyAsync((float *)(c->h_pin + 4), frame + 4, 4, cudaMemcpyDeviceToHost, c->st));
+    get_small(c, c->h_pin + 4, frame + 4, 4);
     sync_stream(c);
     uint32_t bad = *(uint32_t *)(c->h_pin + 4);
     if (bad) NGS_FAIL(NGS_ERR_INVALID_ARG, "%u non-finite centre coordinates", bad);
@@ -566,29 +567,37 @@ extern "C" int ngs_simplify_host(ngs_ctx *c, ngs_splats *h, int64_t target, ngs_
     const size_t sz[5] = {12, 12, 16, 4, 4 * (size_t)F};
     float *hp[5] = {h->xyz, h->log_scale, h->rot, h->opacity_logit, h->sh};
     float *dp[5] = {d.xyz, d.log_scale, d.rot, d.opacity_logit, d.sh};
-    // The SH array (most of the bytes) goes up on a second stream; the engine
-    // waits for it only before its first edge costs, so the upload overlaps
-    // the pre-filter, sorting and first graph stages.
+    // Uploads in the order the engine needs them, so that the link is not
+    // shared while the first kernels wait: opacities and centres on the ctx
+    // stream (pre-filter, Morton frame and keys), then on a second stream the
+    // log-scales and rotations (first needed by the row gather after the sort)
+    // and the SH array, most of the bytes (first needed by the edge costs).
+    // The engine waits for each only where it first reads it.
     if (!c->up_st) {
         NGS_CHECK_CUDA(cudaStreamCreateWithFlags(&c->up_st, cudaStreamNonBlocking));
         NGS_CHECK_CUDA(cudaEventCreateWithFlags(&c->up_ev, cudaEventDisableTiming));
-        NGS_CHECK_CUDA(cudaEventCreateWithFlags(&c->up_ready, cudaEventDisableTiming));
+        NGS_CHECK_CUDA(cudaEventCreateWithFlags(&c->up_first, cudaEventDisableTiming));
+        NGS_CHECK_CUDA(cudaEventCreateWithFlags(&c->up_rest, cudaEventDisableTiming));
     }
-    NGS_CHECK_CUDA(cudaEventRecord(c->up_ready, c->st));  // staging buffers exist
-    NGS_CHECK_CUDA(cudaStreamWaitEvent(c->up_st, c->up_ready, 0));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dp[3], hp[3], sz[3] * n, cudaMemcpyHostToDevice, c->st));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dp[0], hp[0], sz[0] * n, cudaMemcpyHostToDevice, c->st));
+    NGS_CHECK_CUDA(cudaEventRecord(c->up_first, c->st));  // also: the staging buffers exist
+    NGS_CHECK_CUDA(cudaStreamWaitEvent(c->up_st, c->up_first, 0));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dp[1], hp[1], sz[1] * n, cudaMemcpyHostToDevice, c->up_st));
+    NGS_CHECK_CUDA(cudaMemcpyAsync(dp[2], hp[2], sz[2] * n, cudaMemcpyHostToDevice, c->up_st));
+    NGS_CHECK_CUDA(cudaEventRecord(c->up_rest, c->up_st));
     NGS_CHECK_CUDA(cudaMemcpyAsync(dp[4], hp[4], sz[4] * n, cudaMemcpyHostToDevice, c->up_st));
     NGS_CHECK_CUDA(cudaEventRecord(c->up_ev, c->up_st));
-    for (int k = 0; k < 4; k++)
-        NGS_CHECK_CUDA(cudaMemcpyAsync(dp[k], hp[k], sz[k] * n, cudaMemcpyHostToDevice, c->st));
+    c->rest_wait = c->up_rest;
     c->sh_wait = c->up_ev;
     try {
         engine_simplify(c, &d, &target, 1, st);
     } catch (...) {
-        c->sh_wait = nullptr;
-        cudaStreamWaitEvent(c->st, c->up_ev, 0);  // the staging buffer stays busy until then
+        c->sh_wait = c->rest_wait = nullptr;
+        cudaStreamWaitEvent(c->st, c->up_ev, 0);  // the staging buffers stay busy until then
         throw;
     }
-    c->sh_wait = nullptr;
+    c->sh_wait = c->rest_wait = nullptr;
     NGS_CHECK_CUDA(cudaStreamWaitEvent(c->st, c->up_ev, 0));
     for (int k = 0; k < 5; k++)
         NGS_CHECK_CUDA(cudaMemcpyAsync(hp[k], dp[k], sz[k] * d.n, cudaMemcpyDeviceToHost, c->st));

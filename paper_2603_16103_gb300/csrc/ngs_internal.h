@@ -140,7 +140,9 @@ struct ngs_ctx {
     cudaStream_t cap_st = nullptr;  // private stream the graph is captured on
     cudaStream_t up_st = nullptr;   // second upload stream of ngs_simplify_host
     cudaEvent_t up_ev = nullptr;    // SH upload finished
-    cudaEvent_t up_ready = nullptr; // staging buffers allocated on st
+    cudaEvent_t up_first = nullptr; // opacity and centres uploaded (on st)
+    cudaEvent_t up_rest = nullptr;  // log-scales and rotations uploaded
+    cudaEvent_t rest_wait = nullptr;  // set for one engine call: scales/rotations not yet on the device
     cudaEvent_t sh_wait = nullptr;  // set for one engine call: SH input not yet on the device
     DevBuf b_order0;                 // initial Morton permutation kept for the deferred SH gather
 
@@ -196,6 +198,12 @@ void scan_i32(ngs_ctx *c, const int32_t *in, int32_t *out, int64_t n);
 void radix_sort_u32(ngs_ctx *c, uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp,
                     uint32_t *vals_tmp, int64_t n, int bits);
 void iota_u32(ngs_ctx *c, uint32_t *a, int64_t n);
+// Host bytes to device memory on the ctx stream; small sizes go as a kernel
+// parameter (no copy engine).  The source may be reused on return.
+void put_small(ngs_ctx *c, void *dst, const void *src, size_t bytes);
+// Device bytes into pinned host memory (c->h_pin) by a kernel on the ctx
+// stream; valid on the host after the stream is synchronised.
+void get_small(ngs_ctx *c, void *hdst, const void *dsrc, size_t bytes);
 // out[i] = src[idx[i]]
 void gather_u32(ngs_ctx *c, const uint32_t *src, const uint32_t *idx, int64_t n, uint32_t *out);
 // k-th smallest (0-based) of n 32-bit orderable keys -> *d_out (device).
