@@ -119,9 +119,9 @@ __global__ void k_scan_apply(const int32_t *in, int32_t *out, int64_t n, const i
 }
 
 // ---------------------------------------------------------------- small uploads
-// A few bytes from the host travel as a kernel parameter instead of a copy:
-// a host-to-device copy waits behind any large upload already queued on the
-// copy engine (the SH array of ngs_simplify_host), a kernel does not.
+// A few bytes from the host travel as a kernel parameter instead of through a
+// copy engine, so they never share one with a large transfer in flight (the
+// SH upload of ngs_simplify_host runs on a second stream meanwhile).
 constexpr size_t PUT_MAX = 3072;
 struct PutPayload {
     unsigned char b[PUT_MAX];
@@ -132,8 +132,7 @@ __global__ void k_put(unsigned char *dst, const PutPayload p, int bytes) {
 }
 
 // The reverse for small results: a kernel stores them into pinned host
-// memory (device-accessible), so a read-back does not queue behind a large
-// upload on the copy engines either.
+// memory (device-accessible), again without a copy engine.
 __global__ void k_get(unsigned char *hdst, const unsigned char *__restrict__ src, int bytes) {
     for (int i = threadIdx.x; i < bytes; i += blockDim.x) hdst[i] = src[i];
 }
