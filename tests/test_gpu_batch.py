@@ -124,3 +124,15 @@ def test_batch_sh_dim_not_multiple_of_4(ngs, sh_dim):
         s.sh = np.ascontiguousarray(s.sh[:, :sh_dim])
     targets = [O.target_count(s.n, 0.25) for s in scenes]
     _check_batch(ngs, scenes, targets)
+
+
+def test_batch_many_small_scenes(ngs):
+    """450 scenes of 120-400 splats: the per-scene tables no longer fit a
+    kernel parameter and go up by a copy; every scene still equals its run
+    alone."""
+    rng = np.random.default_rng(77)
+    sizes = rng.integers(120, 400, 450)
+    scenes = [small_scene(int(n), seed=500 + i, kind="patch" if i % 3 else "unit")
+              for i, n in enumerate(sizes)]
+    targets = [O.target_count(s.n, 0.25) for s in scenes]
+    _check_batch(ngs, scenes, targets)

@@ -73,7 +73,7 @@ def test_edge_costs(ngs, ctx):
 
 def test_edge_costs_degenerate_and_modes(ngs):
     scene = small_scene(9001, seed=7, kind="patch")
-    for mode, S in ((0, 1), (0, 4), (1, 1), (1, 3), (2, 1), (2, 8), (3, 1)):
+    for mode, S in ((0, 1), (0, 4), (1, 1), (1, 3), (2, 1), (2, 8), (3, 1), (0, 128)):
         c = ngs.Context(cost_mode=mode, mc_samples=S, seed=11)
         try:
             ds = dev(ngs, scene)
