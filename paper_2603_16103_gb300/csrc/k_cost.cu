@@ -25,13 +25,11 @@
 namespace {
 
 constexpr float LOG_2PI_F = 1.8378770664093453f;
-constexpr int REC = 32;  // floats per per-splat record
+constexpr int REC = 16;  // floats per per-splat record
 
-// record layout
-enum {
-    R_MU = 0, R_LW = 3, R_R = 4, R_INVS = 13, R_SIG = 16, R_SUMLS = 22, R_SRATIO = 23,
-    R_Y0 = 24, R_S = 28
-};
+// record layout: (mu, log w), R row-major, 1 / s.  The edge kernel derives
+// s, Sigma and Sigma^{1/2} z from these (fewer bytes through L1 per edge).
+enum { R_MU = 0, R_LW = 3, R_R = 4, R_INVS = 13 };
 
 __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float *R) {
     float inv = rsqrtf(w * w + x * x + y * y + z * z);
@@ -53,42 +51,23 @@ __device__ __forceinline__ void sym_sqrt_apply(const float *R, const float *s, c
 
 __global__ void k_prep(const float *__restrict__ xyz, const float *__restrict__ ls,
                        const float *__restrict__ rot, const float *__restrict__ logit, int64_t n,
-                       const float *__restrict__ zs, float *__restrict__ rec) {
+                       float *__restrict__ rec) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         float r[REC];
-        float R[9], s[3], l[3];
+        float R[9], sc[3], l[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             r[R_MU + a] = xyz[3 * v + a];
             l[a] = ls[3 * v + a];
-            s[a] = expf(l[a]);
+            sc[a] = expf(l[a]);
         }
         quat_rot(rot[4 * v], rot[4 * v + 1], rot[4 * v + 2], rot[4 * v + 3], R);
-        float sum_ls = l[0] + l[1] + l[2];
-        r[R_LW] = 1.5f * LOG_2PI_F - softplusf(-logit[v]) + sum_ls;
+        r[R_LW] = 1.5f * LOG_2PI_F - softplusf(-logit[v]) + (l[0] + l[1] + l[2]);
 #pragma unroll
         for (int k = 0; k < 9; k++) r[R_R + k] = R[k];
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            r[R_INVS + a] = 1.0f / s[a];
-            r[R_S + a] = s[a];
-        }
-        float s2[3] = {s[0] * s[0], s[1] * s[1], s[2] * s[2]};
-        int idx = 0;
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-#pragma unroll
-            for (int b = a; b < 3; b++)
-                r[R_SIG + idx++] = R[3 * a] * s2[0] * R[3 * b] + R[3 * a + 1] * s2[1] * R[3 * b + 1] +
-                                   R[3 * a + 2] * s2[2] * R[3 * b + 2];
-        r[R_SUMLS] = sum_ls;
-        r[R_SRATIO] = fminf(fminf(s[0], s[1]), s[2]) / fmaxf(fmaxf(s[0], s[1]), s[2]);
-        float y[3];
-        sym_sqrt_apply(R, s, zs, y);
-        r[R_Y0] = y[0]; r[R_Y0 + 1] = y[1]; r[R_Y0 + 2] = y[2];
-        r[27] = 0.f;
-        r[31] = 0.f;
+        for (int a = 0; a < 3; a++) r[R_INVS + a] = 1.0f / sc[a];
         float4 *dst = (float4 *)(rec + (int64_t)v * REC);
 #pragma unroll
         for (int k = 0; k < REC / 4; k++) dst[k] = make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
@@ -240,9 +219,19 @@ __device__ __noinline__ double dgeo_fp64(const float *xyz, const float *ls, cons
 
 // ---------------------------------------------------------------- edge kernel
 // Record layout in float4 groups: G0 = (mu, log w), G1..G3 = R (row-major)
-// then inv_s in G3.yzw, G4/G5 = Sigma (6) + sum log s + min/max scale ratio,
-// G6 = Sigma^{1/2} z_0, G7 = s.  Fields are loaded where they are used to
-// keep the live register set small.
+// then inv_s in G3.yzw.
+
+// Sigma = R diag(s^2) R^T, upper triangle (00 01 02 11 12 22)
+__device__ __forceinline__ void cov6(const float *R, const float *s, float *S6) {
+    const float s2[3] = {s[0] * s[0], s[1] * s[1], s[2] * s[2]};
+    int idx = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = a; b < 3; b++)
+            S6[idx++] = R[3 * a] * s2[0] * R[3 * b] + R[3 * a + 1] * s2[1] * R[3 * b + 1] +
+                        R[3 * a + 2] * s2[2] * R[3 * b + 2];
+}
 struct Rec {
     const float4 *p;
     __device__ __forceinline__ float4 g(int k) const { return __ldg(p + k); }
@@ -266,7 +255,6 @@ __global__ void __launch_bounds__(256, 4)
                 const float *__restrict__ logit, float *__restrict__ cost_slot,
                 float *__restrict__ cost_out, unsigned long long *fp64_count,
                 int2 *__restrict__ fp64_list) {
-    const float zz0 = zs[0] * zs[0] + zs[1] * zs[1] + zs[2] * zs[2];
     const int lane = threadIdx.x & 31;
     const int F4 = F >> 2;
     const float4 *sh4 = (const float4 *)sh;
@@ -317,15 +305,28 @@ __global__ void __launch_bounds__(256, 4)
         const int32_t sl = er.x;
         const int64_t i = er.y, j = er.z;
         const Rec Ri{(const float4 *)(rec + i * REC)}, Rj{(const float4 *)(rec + j * REC)};
+        const float4 i0 = Ri.g(0), j0 = Rj.g(0);
+        float Rm[9], invs_i[3], Rn[9], invs_j[3];
+        load_R(Ri, Rm, invs_i);
+        load_R(Rj, Rn, invs_j);
+        float si[3], sj[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            si[a] = 1.0f / invs_i[a];
+            sj[a] = 1.0f / invs_j[a];
+        }
+        const float d[3] = {i0.x - j0.x, i0.y - j0.y, i0.z - j0.z};
         if (MODE == 3) {
-            const float4 i0 = Ri.g(0), j0 = Rj.g(0), i4 = Ri.g(4), i5 = Ri.g(5), j4 = Rj.g(4),
-                         j5 = Rj.g(5);
-            const float dx = i0.x - j0.x, dy = i0.y - j0.y, dz = i0.z - j0.z;
+            float Si[6], Sj[6];
+            cov6(Rm, si, Si);
+            cov6(Rn, sj, Sj);
             // Sigma (00 01 02 11 12 22): off-diagonal entries count twice
-            const float e00 = i4.x - j4.x, e01 = i4.y - j4.y, e02 = i4.z - j4.z;
-            const float e11 = i4.w - j4.w, e12 = i5.x - j5.x, e22 = i5.y - j5.y;
-            const float dgeo = dx * dx + dy * dy + dz * dz + e00 * e00 + e11 * e11 + e22 * e22 +
-                               2.f * (e01 * e01 + e02 * e02 + e12 * e12);
+            float dgeo = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+#pragma unroll
+            for (int t = 0; t < 6; t++) {
+                const float e = Si[t] - Sj[t];
+                dgeo += (t == 0 || t == 3 || t == 5 ? 1.f : 2.f) * e * e;
+            }
             const float c = lg * dgeo + la * dapp;
             cost_slot[sl] = c;
             if (er.w >= 0) cost_slot[er.w] = c;
@@ -333,23 +334,21 @@ __global__ void __launch_bounds__(256, 4)
             continue;
         }
         // ---- MPMM moments (Eqs. vm_weights, vm_cov)
-        const float4 i0 = Ri.g(0), j0 = Rj.g(0);
         const float ld = i0.w - j0.w;
         const float lpi = -softplusf(-ld), lpj = -softplusf(ld);
         const float pi = __expf(lpi), pj = __expf(lpj);
-        const float d[3] = {i0.x - j0.x, i0.y - j0.y, i0.z - j0.z};
         const float ppd = pi * pj;
         float Sm[6];
         {
-            const float4 i4 = Ri.g(4), i5 = Ri.g(5), j4 = Rj.g(4), j5 = Rj.g(5);
-            const float si[6] = {i4.x, i4.y, i4.z, i4.w, i5.x, i5.y};
-            const float sj[6] = {j4.x, j4.y, j4.z, j4.w, j5.x, j5.y};
+            float Si[6], Sj[6];
+            cov6(Rm, si, Si);
+            cov6(Rn, sj, Sj);
             int idx = 0;
 #pragma unroll
             for (int a = 0; a < 3; a++)
 #pragma unroll
                 for (int b = a; b < 3; b++, idx++)
-                    Sm[idx] = pi * si[idx] + pj * sj[idx] + ppd * d[a] * d[b];
+                    Sm[idx] = pi * Si[idx] + pj * Sj[idx] + ppd * d[a] * d[b];
         }
         // ---- Cholesky of Sigma_m (00 01 02 11 12 22)
         float L[6], il[3];
@@ -367,33 +366,27 @@ __global__ void __launch_bounds__(256, 4)
         // FP32 loses about eps32 / (pivot / diagonal) of the log-determinant: a
         // ratio below 1e-2 (error above ~6e-6) sends the edge to FP64
         bool flag = !(Sm[0] > 0.f) || !(t11 > 1e-2f * Sm[3]) || !(t22 > 1e-2f * Sm[5]);
-        if (policy == 1) flag = flag || Ri.g(5).w < 1e-3f || Rj.g(5).w < 1e-3f;
+        if (policy == 1) {
+            // smallest / largest scale of either endpoint below 1e-3
+            const float ri = fminf(fminf(invs_i[0], invs_i[1]), invs_i[2]) /
+                             fmaxf(fmaxf(invs_i[0], invs_i[1]), invs_i[2]);
+            const float rj = fminf(fminf(invs_j[0], invs_j[1]), invs_j[2]) /
+                             fmaxf(fmaxf(invs_j[0], invs_j[1]), invs_j[2]);
+            flag = flag || ri < 1e-3f || rj < 1e-3f;
+        }
         float dgeo;
         if (!flag) {
-            float Rm[9], invs_i[3], invs_j[3];
-            load_R(Ri, Rm, invs_i);
-            float Rn[9];
-            load_R(Rj, Rn, invs_j);
             // a_c = log sqrt(det Sm / det Sigma_c) as a product of O(1) ratios
             const float ai = logf((L[0] * invs_i[0]) * (L[2] * invs_i[1]) * (L[5] * invs_i[2]));
             const float aj = logf((L[0] * invs_j[0]) * (L[2] * invs_j[1]) * (L[5] * invs_j[2]));
             const float ci = lpi + ai, cj = lpj + aj;
             float acc = 0.f;
             for (int s = 0; s < S; s++) {
-                float yi[3], yj[3], zz;
-                if (s == 0) {
-                    const float4 a = Ri.g(6), b = Rj.g(6);
-                    yi[0] = a.x; yi[1] = a.y; yi[2] = a.z;
-                    yj[0] = b.x; yj[1] = b.y; yj[2] = b.z;
-                    zz = zz0;
-                } else {
-                    const float z[3] = {zs[3 * s], zs[3 * s + 1], zs[3 * s + 2]};
-                    const float4 a = Ri.g(7), b = Rj.g(7);
-                    const float sa[3] = {a.x, a.y, a.z}, sb[3] = {b.x, b.y, b.z};
-                    sym_sqrt_apply(Rm, sa, z, yi);
-                    sym_sqrt_apply(Rn, sb, z, yj);
-                    zz = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
-                }
+                const float z[3] = {zs[3 * s], zs[3 * s + 1], zs[3 * s + 2]};
+                const float zz = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
+                float yi[3], yj[3];
+                sym_sqrt_apply(Rm, si, z, yi);
+                sym_sqrt_apply(Rn, sj, z, yj);
                 // x = x_i
                 float v1[3] = {d[0] + yi[0], d[1] + yi[1], d[2] + yi[2]};
                 float v2[3] = {pj * d[0] + yi[0], pj * d[1] + yi[1], pj * d[2] + yi[2]};
@@ -478,7 +471,7 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
     put_small(c, zs, h.data(), sizeof(float) * 4 * (size_t)S);
     float *rec = ws<float>(c, c->b_rec, s.n * REC);
     launch(c, "cost_prep", dim3(grid_stride_blocks(c, s.n, 256, 8)), dim3(256), 0, k_prep, s.xyz,
-           s.ls, s.rot, s.logit, s.n, (const float *)zs, rec);
+           s.ls, s.rot, s.logit, s.n, rec);
     unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c, c->b_status, 64);
     int2 *list = ws<int2>(c, c->b_fp64list, m);
     NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, c->st));
