@@ -46,8 +46,11 @@ SPLAT_BYTES = 4 * (3 + 3 + 4 + 1 + 48)   # 236 B per splat, SH degree 3
 KNN_OPS_PER_QUERY = 64 * 9
 ALGO = {
     "knn_k16": ("alu", lambda n, e, p: n * KNN_OPS_PER_QUERY, "Gop/s"),
-    "edge_cost": ("hbm", lambda n, e, p: n * SPLAT_BYTES + e * 12, "GB/s"),
-    "cost_prep": ("hbm", lambda n, e, p: n * (SPLAT_BYTES + 128), "GB/s"),
+    # each splat's 64-byte record and 192-byte SH row read once, per edge its
+    # 16-byte record read and two 4-byte slot costs written
+    "edge_cost": ("hbm", lambda n, e, p: n * (64 + 192) + e * 24, "GB/s"),
+    # centre, log-scales, rotation and opacity (44 B) read, 64-byte record written
+    "cost_prep": ("hbm", lambda n, e, p: n * (44 + 64), "GB/s"),
     "merge": ("hbm", lambda n, e, p: p * 3 * SPLAT_BYTES, "GB/s"),
     "copy_kept": ("hbm", lambda n, e, p: (n - 2 * p) * 2 * SPLAT_BYTES, "GB/s"),
     "slot_classify": ("hbm", lambda n, e, p: n * 16 * 4 * 2, "GB/s"),
