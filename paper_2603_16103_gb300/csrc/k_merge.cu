@@ -376,8 +376,9 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
     if ((F & 3) == 0) {
         const float4 *fi = (const float4 *)(in.sh + i * F), *fj = (const float4 *)(in.sh + j * F);
         float4 *fo = (float4 *)(out.sh + o * F);
+        // read-only loads: the compiler may issue them ahead of the stores
         for (int t = 0; t < F / 4; t++) {
-            float4 a = fi[t], b = fj[t];
+            const float4 a = __ldg(fi + t), b = __ldg(fj + t);
             fo[t] = make_float4(pi * a.x + pj * b.x, pi * a.y + pj * b.y, pi * a.z + pj * b.z,
                                 pi * a.w + pj * b.w);
         }
