@@ -315,18 +315,18 @@ __device__ __forceinline__ void copy_row(const Rows &in, int64_t a, const WRows 
                                          int F) {
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        out.xyz[3 * b + k] = in.xyz[3 * a + k];
-        out.ls[3 * b + k] = in.ls[3 * a + k];
+        out.xyz[3 * b + k] = __ldg(in.xyz + 3 * a + k);
+        out.ls[3 * b + k] = __ldg(in.ls + 3 * a + k);
     }
 #pragma unroll
-    for (int k = 0; k < 4; k++) out.rot[4 * b + k] = in.rot[4 * a + k];
-    out.logit[b] = in.logit[a];
+    for (int k = 0; k < 4; k++) out.rot[4 * b + k] = __ldg(in.rot + 4 * a + k);
+    out.logit[b] = __ldg(in.logit + a);
     if ((F & 3) == 0) {
         const float4 *s = (const float4 *)(in.sh + a * F);
         float4 *d = (float4 *)(out.sh + b * F);
-        for (int t = 0; t < F / 4; t++) d[t] = s[t];
+        for (int t = 0; t < F / 4; t++) d[t] = __ldg(s + t);
     } else {
-        for (int t = 0; t < F; t++) out.sh[b * F + t] = in.sh[a * F + t];
+        for (int t = 0; t < F; t++) out.sh[b * F + t] = __ldg(in.sh + a * F + t);
     }
 }
 
@@ -340,13 +340,22 @@ __device__ __forceinline__ void move_chunk(const Rows &in, int64_t a, const WRow
     if (ch < nch) {
         ((float4 *)(out.sh + b * F))[ch] = __ldg((const float4 *)(in.sh + a * F) + ch);
     } else {
+        // read-only loads first, so the eleven fields are in flight together
+        float x[3], l[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            out.xyz[3 * b + k] = in.xyz[3 * a + k];
-            out.ls[3 * b + k] = in.ls[3 * a + k];
+            x[k] = __ldg(in.xyz + 3 * a + k);
+            l[k] = __ldg(in.ls + 3 * a + k);
         }
-        *(float4 *)(out.rot + 4 * b) = *(const float4 *)(in.rot + 4 * a);
-        out.logit[b] = in.logit[a];
+        const float4 r = __ldg((const float4 *)(in.rot + 4 * a));
+        const float o = __ldg(in.logit + a);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            out.xyz[3 * b + k] = x[k];
+            out.ls[3 * b + k] = l[k];
+        }
+        *(float4 *)(out.rot + 4 * b) = r;
+        out.logit[b] = o;
     }
 }
 
