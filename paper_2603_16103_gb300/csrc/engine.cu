@@ -52,18 +52,28 @@ __host__ __device__ __forceinline__ int parts_of(int F) { return (F & 3) ? 1 : (
 
 __device__ __forceinline__ void move_part(const SrcRows &a, int64_t ra, const SrcRows &b, int64_t rb,
                                           int F, int ch) {
+    // source and destination never overlap: read-only loads, issued before
+    // the stores
     if ((F & 3) == 0 && ch < (F >> 2)) {
-        ((float4 *)(b.sh + rb * F))[ch] = ((const float4 *)(a.sh + ra * F))[ch];
+        ((float4 *)(b.sh + rb * F))[ch] = __ldg((const float4 *)(a.sh + ra * F) + ch);
     } else {
+        float x[3], l[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            b.xyz[3 * rb + k] = a.xyz[3 * ra + k];
-            b.ls[3 * rb + k] = a.ls[3 * ra + k];
+            x[k] = __ldg(a.xyz + 3 * ra + k);
+            l[k] = __ldg(a.ls + 3 * ra + k);
         }
-        *(float4 *)(b.rot + 4 * rb) = *(const float4 *)(a.rot + 4 * ra);
-        b.logit[rb] = a.logit[ra];
+        const float4 r = __ldg((const float4 *)(a.rot + 4 * ra));
+        const float o = __ldg(a.logit + ra);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            b.xyz[3 * rb + k] = x[k];
+            b.ls[3 * rb + k] = l[k];
+        }
+        *(float4 *)(b.rot + 4 * rb) = r;
+        b.logit[rb] = o;
         if (F & 3)
-            for (int t = 0; t < F; t++) b.sh[rb * F + t] = a.sh[ra * F + t];
+            for (int t = 0; t < F; t++) b.sh[rb * F + t] = __ldg(a.sh + ra * F + t);
     }
 }
 

@@ -363,12 +363,14 @@ __device__ __forceinline__ void move_chunk(const Rows &in, int64_t a, const WRow
 // was raised to the floor
 __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out, int64_t o, int F,
                           double eig_floor, int policy) {
-    float li = in.logit[i], lj = in.logit[j];
+    // every input field through the read-only path, so no load waits behind
+    // an output store
+    float li = __ldg(in.logit + i), lj = __ldg(in.logit + j);
     float lsi[3], lsj[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        lsi[a] = in.ls[3 * i + a];
-        lsj[a] = in.ls[3 * j + a];
+        lsi[a] = __ldg(in.ls + 3 * i + a);
+        lsj[a] = __ldg(in.ls + 3 * j + a);
     }
     const float lwi = 1.5f * LOG_2PI_F - softplusf(-li) + (lsi[0] + lsi[1] + lsi[2]);
     const float lwj = 1.5f * LOG_2PI_F - softplusf(-lj) + (lsj[0] + lsj[1] + lsj[2]);
@@ -377,8 +379,8 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
     float mi[3], mj[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        mi[a] = in.xyz[3 * i + a];
-        mj[a] = in.xyz[3 * j + a];
+        mi[a] = __ldg(in.xyz + 3 * i + a);
+        mj[a] = __ldg(in.xyz + 3 * j + a);
         out.xyz[3 * o + a] = pi * mi[a] + pj * mj[a];
     }
     // appearance
@@ -392,7 +394,8 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
                                 pi * a.w + pj * b.w);
         }
     } else {
-        for (int t = 0; t < F; t++) out.sh[o * F + t] = pi * in.sh[i * F + t] + pj * in.sh[j * F + t];
+        for (int t = 0; t < F; t++)
+            out.sh[o * F + t] = pi * __ldg(in.sh + i * F + t) + pj * __ldg(in.sh + j * F + t);
     }
     // opacity union in the log-transmittance form
     const float logT = -softplusf(li) - softplusf(lj);
@@ -401,8 +404,8 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
     float qi[4], qj[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        qi[k] = in.rot[4 * i + k];
-        qj[k] = in.rot[4 * j + k];
+        qi[k] = __ldg(in.rot + 4 * i + k);
+        qj[k] = __ldg(in.rot + 4 * j + k);
     }
     float Ri[9], Rj[9], s2i[3], s2j[3], Si[9], Sj[9], A[9], V[9];
     quat_to_rot<float>(qi, Ri);
