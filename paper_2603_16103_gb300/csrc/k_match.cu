@@ -47,6 +47,10 @@ __device__ __forceinline__ void consider(int32_t u, float cst, const int32_t *__
     }
 }
 
+// K > 0: the list width k_eff = K, a multiple of 4; the slots are read as
+// 16-byte vectors and the loop is unrolled, so the ids, costs and partner
+// states of a vertex's slots are all in flight at once.  K = 0: any width.
+template <int K>
 __global__ void k_match_scan(const int32_t *__restrict__ wl, const int32_t *__restrict__ wl_count,
                              int64_t n_all, int kk, const int32_t *__restrict__ nbr,
                              const float *__restrict__ cost_slot,
@@ -65,14 +69,62 @@ __global__ void k_match_scan(const int32_t *__restrict__ wl, const int32_t *__re
         int32_t best = -1;
         uint32_t bk = 0xffffffffu;
         const int64_t base = v * kk;
-        for (int t = 0; t < kk; t++)
-            consider(nbr[base + t], cost_slot[base + t], cid, mate, all_free, best, bk);
-        for (int32_t r = rev_ptr[v]; r < rev_ptr[v + 1]; r++) {
-            int32_t s = rev[r];
-            consider(s / kk, cost_slot[s], cid, mate, all_free, best, bk);
+        if (K > 0) {
+            // ids and costs, then every partner state, then the choice
+            constexpr int KK = K > 0 ? K : 4;
+            int32_t us[KK], ms[KK];
+            float cs[KK];
+            const int4 *nb4 = (const int4 *)(nbr + base);
+            const float4 *cs4 = (const float4 *)(cost_slot + base);
+#pragma unroll
+            for (int t4 = 0; t4 < K / 4; t4++) {
+                const int4 u4 = __ldg(nb4 + t4);
+                const float4 c4 = __ldg(cs4 + t4);
+                us[4 * t4] = u4.x; us[4 * t4 + 1] = u4.y; us[4 * t4 + 2] = u4.z; us[4 * t4 + 3] = u4.w;
+                cs[4 * t4] = c4.x; cs[4 * t4 + 1] = c4.y; cs[4 * t4 + 2] = c4.z; cs[4 * t4 + 3] = c4.w;
+            }
+#pragma unroll
+            for (int t = 0; t < KK; t++) ms[t] = all_free ? -1 : __ldg(mate + us[t]);
+#pragma unroll
+            for (int t = 0; t < KK; t++)
+                if (ms[t] == -1) consider(us[t], cs[t], cid, mate, true, best, bk);
+        } else {
+            for (int t = 0; t < kk; t++)
+                consider(nbr[base + t], cost_slot[base + t], cid, mate, all_free, best, bk);
+        }
+        // in-slots four at a time: slots, then costs and partner states
+        const int32_t r1 = rev_ptr[v + 1];
+        for (int32_t r = rev_ptr[v]; r < r1; r += 4) {
+            int32_t ss[4], uu[4], mm[4];
+            float cc[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) ss[q] = r + q < r1 ? __ldg(rev + r + q) : -1;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                uu[q] = ss[q] >= 0 ? ss[q] / kk : 0;
+                cc[q] = ss[q] >= 0 ? __ldg(cost_slot + ss[q]) : 0.f;
+                mm[q] = (ss[q] < 0) ? 0 : (all_free ? -1 : __ldg(mate + uu[q]));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (mm[q] == -1) consider(uu[q], cc[q], cid, mate, true, best, bk);
         }
         cand[v] = best;
         candkey[v] = bk;
+    }
+}
+
+using ScanKernel = void (*)(const int32_t *, const int32_t *, int64_t, int, const int32_t *,
+                           const float *, const int32_t *, const int32_t *, const int32_t *,
+                           const int32_t *, int32_t *, uint32_t *);
+
+ScanKernel scan_kernel(int k) {
+    switch (k) {
+    case 4: return k_match_scan<4>;
+    case 8: return k_match_scan<8>;
+    case 16: return k_match_scan<16>;
+    case 32: return k_match_scan<32>;
+    default: return k_match_scan<0>;
     }
 }
 
@@ -227,6 +279,7 @@ static bool match_rounds_graph(ngs_ctx *c, const GraphDev &g, int32_t *mate, int
         return false;
     }
     cudaStream_t cs = c->cap_st;  // capture only records; the graph runs on c->st
+    const ScanKernel scan = scan_kernel(g.k_eff);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool ok = false;
@@ -255,14 +308,14 @@ static bool match_rounds_graph(ngs_ctx *c, const GraphDev &g, int32_t *mate, int
                                           cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             break;
         cudaMemsetAsync(stt + MS_CNT_B, 0, 3 * sizeof(int32_t), cs);  // B size, both round counts
-        k_match_scan<<<grid, 256, 0, cs>>>(wl[0], stt + MS_CNT_A, n, g.k_eff, g.nbr,
+        scan<<<grid, 256, 0, cs>>>(wl[0], stt + MS_CNT_A, n, g.k_eff, g.nbr,
                                              (const float *)g.cost_slot, (const int32_t *)g.rev_ptr,
                                              (const int32_t *)g.rev, g.cid, (const int32_t *)mate,
                                              cand, candkey);
         k_match_pair<<<grid, 256, 0, cs>>>(wl[0], stt + MS_CNT_A, n, (const int32_t *)cand, mate,
                                              stt + MS_M_A, wl[1], stt + MS_CNT_B);
         cudaMemsetAsync(stt + MS_CNT_A, 0, sizeof(int32_t), cs);
-        k_match_scan<<<grid, 256, 0, cs>>>(wl[1], stt + MS_CNT_B, n, g.k_eff, g.nbr,
+        scan<<<grid, 256, 0, cs>>>(wl[1], stt + MS_CNT_B, n, g.k_eff, g.nbr,
                                              (const float *)g.cost_slot, (const int32_t *)g.rev_ptr,
                                              (const int32_t *)g.rev, g.cid, (const int32_t *)mate,
                                              cand, candkey);
@@ -326,7 +379,7 @@ int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
         int32_t *stt = ws<int32_t>(c, c->b_mstate, 16);
         NGS_CHECK_CUDA(cudaMemsetAsync(stt, 0, 16 * sizeof(int32_t), c->st));
         // round 0 over every vertex, then the captured loop
-        launch(c, "match_scan", dim3(grid), dim3(256), 0, k_match_scan, (const int32_t *)nullptr,
+        launch(c, "match_scan", dim3(grid), dim3(256), 0, scan_kernel(g.k_eff), (const int32_t *)nullptr,
                (const int32_t *)nullptr, n, g.k_eff, g.nbr, (const float *)g.cost_slot,
                (const int32_t *)g.rev_ptr, (const int32_t *)g.rev, g.cid, (const int32_t *)mate,
                cand, candkey);
@@ -364,7 +417,7 @@ int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
             for (int b = 0; b < batch; b++, r++) {
                 const int32_t *in_wl = r == 0 ? nullptr : wl[(r - 1) & 1];
                 const int32_t *in_cnt = r == 0 ? nullptr : wl_counts + (r - 1);
-                launch(c, "match_scan", dim3(grid), dim3(256), 0, k_match_scan, in_wl, in_cnt, n,
+                launch(c, "match_scan", dim3(grid), dim3(256), 0, scan_kernel(g.k_eff), in_wl, in_cnt, n,
                        g.k_eff, g.nbr, (const float *)g.cost_slot, (const int32_t *)g.rev_ptr,
                        (const int32_t *)g.rev, g.cid, (const int32_t *)mate, cand, candkey);
                 launch(c, "match_pair", dim3(grid), dim3(256), 0, k_match_pair, in_wl, in_cnt, n,
