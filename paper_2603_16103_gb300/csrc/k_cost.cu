@@ -280,10 +280,27 @@ __global__ void __launch_bounds__(256, 4)
                 float acc = 0.f;
                 if (wb + el < m) {
                     const float4 *fi = sh4 + (int64_t)ii * F4, *fj = sh4 + (int64_t)jj * F4;
-                    for (int t = sub; t < F4; t += 4) {
-                        const float4 a = __ldg(fi + t), b = __ldg(fj + t);
-                        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
-                        acc += dx * dx + dy * dy + dz * dz + dw * dw;
+                    if (F4 <= 12) {
+                        // up to 3 chunks of each row, all loads in flight together
+                        float4 a[3], b[3];
+#pragma unroll
+                        for (int u = 0; u < 3; u++) {
+                            const int t = sub + 4 * u;
+                            a[u] = t < F4 ? __ldg(fi + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            b[u] = t < F4 ? __ldg(fj + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 3; u++) {
+                            const float dx = a[u].x - b[u].x, dy = a[u].y - b[u].y;
+                            const float dz = a[u].z - b[u].z, dw = a[u].w - b[u].w;
+                            acc += dx * dx + dy * dy + dz * dz + dw * dw;
+                        }
+                    } else {
+                        for (int t = sub; t < F4; t += 4) {
+                            const float4 a = __ldg(fi + t), b = __ldg(fj + t);
+                            const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+                            acc += dx * dx + dy * dy + dz * dz + dw * dw;
+                        }
                     }
                 }
                 acc += __shfl_xor_sync(FULL_MASK, acc, 1);
