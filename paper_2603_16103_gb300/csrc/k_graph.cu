@@ -162,21 +162,26 @@ __global__ void k_slot_fill_rows(const int32_t *__restrict__ nbr, int64_t n, int
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < m; b0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = b0 + threadIdx.x;
         bool canon = false;
-        int32_t u = 0, c = -3, v = 0;
+        int32_t u = 0, c = -3, v = 0, rp = 0, rv = 0;
         if (s < m) {
             v = (int32_t)(s / k);
-            u = nbr[s];
-            c = code[s];
+            u = __ldg(nbr + s);
+            c = __ldg(code + s);
+            rp = __ldg(rowpos + v);      // loaded before they are known to be needed
+            rv = __ldg(rev_ptr + u);
             canon = c != -3;
         }
+        const bool in_rev = c == -1 || c == -2;
+        int32_t at = 0;
+        if (in_rev) at = atomicAdd(&revfill[u], 1);
         const unsigned cm = __ballot_sync(FULL_MASK, canon);
         const int first = lane - lane % k;
         if (canon) {
-            const int32_t pos = rowpos[v] + __popc(cm & ((1u << lane) - 1u) & ~((1u << first) - 1u));
+            const int32_t pos = rp + __popc(cm & ((1u << lane) - 1u) & ~((1u << first) - 1u));
             const bool vlo = c >= 0 || c == -1;
             erec[pos] = make_int4((int32_t)s, vlo ? v : u, vlo ? u : v, c >= 0 ? c : -1);
         }
-        if (c == -1 || c == -2) rev[rev_ptr[u] + atomicAdd(&revfill[u], 1)] = (int32_t)s;
+        if (in_rev) rev[rv + at] = (int32_t)s;
     }
 }
 
