@@ -452,8 +452,21 @@ __global__ void k_cid_to_pos(const int32_t *__restrict__ cid, int64_t n, int32_t
         pos_of_cid[cid[p]] = (int32_t)p;
 }
 
+// a: a 16-byte aligned workspace array
 __global__ void k_map_ids(int32_t *a, int64_t m, const int32_t *__restrict__ pos_of_cid) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+    // four ids per thread (16-byte accesses, four gathers in flight), then the tail
+    const int64_t m4 = m >> 2;
+    int4 *a4 = (int4 *)a;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int4 x = a4[i];
+        x.x = __ldg(pos_of_cid + x.x);
+        x.y = __ldg(pos_of_cid + x.y);
+        x.z = __ldg(pos_of_cid + x.z);
+        x.w = __ldg(pos_of_cid + x.w);
+        a4[i] = x;
+    }
+    for (int64_t i = 4 * m4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)
         a[i] = pos_of_cid[a[i]];
 }
