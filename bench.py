@@ -55,16 +55,19 @@ ALGO = {
     "copy_kept": ("hbm", lambda n, e, p: (n - 2 * p) * 2 * SPLAT_BYTES, "GB/s"),
     "slot_classify": ("hbm", lambda n, e, p: n * 16 * 4 * 2, "GB/s"),
     "slot_fill": ("hbm", lambda n, e, p: n * 16 * 4 + e * 16, "GB/s"),
+    # round 0 of the matching: each vertex's 16 slot ids and costs read, its choice written
+    "match_scan": ("hbm", lambda n, e, p: n * (16 * 8 + 8), "GB/s"),
 }
 
 # DRAM traffic per launch from ncu captures, in bytes per splat of the pass
 # (the profiles/ summaries give the commands and the raw counters).
 NCU_TRAFFIC_PER_SPLAT = {
     "knn_k16": 42.37,        # 42.36 MB over 999,792 queries (knn_grid_patches1m.md)
-    "edge_cost": 548.4,      # 548.31 MB over 999,792 splats (edge_cost_patches1m.md)
+    "edge_cost": 480.6,      # 480.52 MB over 999,792 splats (edge_cost_patches1m.md)
     "slot_classify": 104.8,  # 104.76 MB over 999,792 splats (slot_classify_patches1m.md)
-    "slot_fill": 251.1,      # 251.06 MB over 999,792 splats (slot_classify_patches1m.md)
-    "merge": 341.3,          # 341.17 MB, pass of 999,792 splats (merge_patches1m.md)
+    "slot_fill": 250.6,      # 250.57 MB over 999,792 splats (slot_classify_patches1m.md)
+    "merge": 331.2,          # 331.16 MB, pass of 999,792 splats (merge_patches1m.md)
+    "match_scan": 154.8,     # 154.81 MB over 999,792 splats, round 0 (match_scan_patches1m.md)
 }
 
 
