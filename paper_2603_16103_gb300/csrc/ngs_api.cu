@@ -711,7 +711,15 @@ extern "C" int ngs_autotune(ngs_ctx *c, const ngs_splats *s, ngs_tuning *best, d
             for (int cpp : cpps) {
                 c->tune.knn_block_min = bm;
                 c->tune.cells_per_point = cpp;
-                const float t = timed([&] { graph_canonical(c, s); });
+                // the sample and its first half and quarter: later passes run on
+                // fewer splats, where the cell-table level (and so the best
+                // density) differs
+                float t = timed([&] { graph_canonical(c, s); });
+                for (int64_t part = s->n / 2; part >= 4096 && part >= s->n / 4; part /= 2) {
+                    ngs_splats sub = *s;
+                    sub.n = part;
+                    t += timed([&] { graph_canonical(c, &sub); });
+                }
                 if (t < t_graph) {
                     t_graph = t;
                     tb.knn_block_min = bm;
