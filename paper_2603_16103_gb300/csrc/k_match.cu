@@ -387,7 +387,9 @@ int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
                (const int32_t *)nullptr, n, (const int32_t *)cand, mate, stt + MS_M0, wl[0],
                stt + MS_CNT_A);
         int32_t *hs = (int32_t *)(c->h_pin + 32);
-        if (match_rounds_graph(c, g, mate, cand, candkey, wl, stt, grid, max_rounds, hs)) {
+        // the later rounds' worklists are smaller: one wave of 4 blocks per SM
+        const unsigned grid_later = std::min<unsigned>(grid, (unsigned)c->num_sms * 4);
+        if (match_rounds_graph(c, g, mate, cand, candkey, wl, stt, grid_later, max_rounds, hs)) {
             if (hs[MS_LIMIT]) NGS_FAIL(NGS_ERR_TIMEOUT, "matching did not converge in %d rounds", max_rounds);
             c->rounds = hs[MS_ROUNDS];
             c->launches += 1 + 5 * (int64_t)((hs[MS_ROUNDS]) / 2);  // control + body kernels
