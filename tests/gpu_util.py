@@ -69,3 +69,23 @@ def small_scene(n, seed=0, kind="unit"):
     if kind == "unit":
         return synth.surfaces_unit_cube(n, seed=seed)
     return synth.patches_cube(n, seed=seed, frac_degenerate=0.05, frac_duplicate=0.01)
+
+
+COST_RTOL = 2e-5     # |C_gpu - C_fp64| <= COST_RTOL * (1 + |C|), see design notes
+ATTR_RTOL = 1e-5     # merged attributes vs FP64
+
+
+def stepwise(ngs, ctx, scene, target, max_passes=64):
+    """Algorithm 1 through the per-step C-ABI calls."""
+    ds = ngs.DeviceSplats.from_numpy(scene)
+    ctx.prefilter(ds)
+    p = 0
+    while ds.n > target and ds.n > 1 and p < max_passes:
+        g, nbr, lo, hi = ctx.build_graph(ds)
+        cost = ctx.edge_costs(ds, g, p)
+        pairs = ctx.select_pairs(g, cost, ds.n - target)
+        p += 1
+        if pairs.shape[0] == 0:
+            break
+        ctx.merge_compact(ds, pairs)
+    return ds, p

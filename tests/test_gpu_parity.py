@@ -4,13 +4,11 @@ import pytest
 import torch
 
 import oracle as O
-from gpu_util import greedy_certificate, knn_agreement, sigma_of, small_scene
+from gpu_util import (ATTR_RTOL, COST_RTOL, greedy_certificate, knn_agreement, sigma_of,
+                      small_scene, stepwise)
 from paper_2603_16103_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-
-COST_RTOL = 2e-5     # |C_gpu - C_fp64| <= COST_RTOL * (1 + |C|), see design notes
-ATTR_RTOL = 1e-5     # merged attributes vs FP64
 
 
 @pytest.fixture
@@ -200,22 +198,6 @@ def test_prefilter(ngs, ctx):
         assert kept == cnt
         assert np.array_equal(ds.numpy()[0], scene.xyz[keep])
         assert np.array_equal(ds.numpy()[4], scene.sh[keep])
-
-
-def stepwise(ngs, ctx, scene, target, max_passes=64):
-    """Algorithm 1 through the per-step C-ABI calls."""
-    ds = dev(ngs, scene)
-    ctx.prefilter(ds)
-    p = 0
-    while ds.n > target and ds.n > 1 and p < max_passes:
-        g, nbr, lo, hi = ctx.build_graph(ds)
-        cost = ctx.edge_costs(ds, g, p)
-        pairs = ctx.select_pairs(g, cost, ds.n - target)
-        p += 1
-        if pairs.shape[0] == 0:
-            break
-        ctx.merge_compact(ds, pairs)
-    return ds, p
 
 
 @pytest.mark.parametrize("n,ratio,kind", [(20000, 0.5, "unit"), (9001, 0.1, "patch"),
