@@ -433,8 +433,6 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident inputs, CUDA events around each step
-    B.ngs_profile_reset(ctx.handle)
-    B.ngs_profile_enable(ctx.handle, True)
     clocks = ClockSampler(local)
     clocks.start()
     replicas.barrier()
@@ -454,9 +452,24 @@ def main():
         launches += stats["gpu_launches"]
     torch.cuda.synchronize()
     replicas.barrier()
-    clk = clocks.stop()
+    # ---- per-kernel durations: the same steps again with CUDA events around
+    # every launch on the ctx stream (those events add about 5 % to a step, so
+    # the headline steps above run without them)
+    B.ngs_profile_reset(ctx.handle)
+    B.ngs_profile_enable(ctx.handle, True)
+    prof_ms = 0.0
+    for _ in range(args.steps):
+        restore()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ctx.simplify(work, target)
+        ev1.record(stream)
+        ev1.synchronize()
+        prof_ms += ev0.elapsed_time(ev1)
     B.ngs_profile_enable(ctx.handle, False)
     prof = B.ngs_profile(ctx.handle)
+    clk = clocks.stop()
     total_ms = replicas.max_over_ranks(total_ms)
     ms_per_step = total_ms / args.steps
     value = replicas.whole_job_rate(n0 * args.steps, total_ms / 1e3)
@@ -544,6 +557,8 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "roofline": roof, "roofline_by_kernel": roofs, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
+            "kernel_timing": {"steps": args.steps, "ms_per_step_with_events": prof_ms / args.steps,
+                              "note": "per-kernel CUDA events in a second run of the timed steps"},
         }
         out.update(forms)
         print(json.dumps(out), flush=True)
