@@ -46,12 +46,16 @@ extern "C" {
 #define NGS_ERR_STATE       (-6) /* call order violated (e.g. no graph built)   */
 
 #define NGS_MAX_K   32   /* largest supported kNN size k                       */
+/* most rows of one call (all scenes of a batch together); n * k_eff may not
+ * exceed 2^30 either (int32 list-slot indices), so k = 16 reaches it exactly */
+#define NGS_MAX_N   ((int64_t)1 << 26)
 #define NGS_MAX_S   128  /* largest supported Monte Carlo sample count S       */
 
 typedef struct ngs_ctx ngs_ctx;
 
 /* A splat set in caller-owned device memory (see the layout above).
- * n = live rows, cap = allocated rows (cap >= n), sh_dim = F (1..64). */
+ * n = live rows (at most NGS_MAX_N), cap = allocated rows (cap >= n),
+ * sh_dim = F (1..64). */
 typedef struct {
     float  *xyz;
     float  *log_scale;

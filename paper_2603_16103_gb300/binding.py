@@ -25,6 +25,10 @@ NGS_ERR_TIMEOUT = -4
 NGS_ERR_BUDGET = -5
 NGS_ERR_STATE = -6
 NGS_STATS_MAX_PASSES = 64
+NGS_MAX_K = 32
+NGS_MAX_N = 1 << 26
+NGS_MAX_S = 128
+NGS_MAX_SCENES = 4096
 
 
 class NgsError(RuntimeError):

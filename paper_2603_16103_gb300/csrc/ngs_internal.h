@@ -9,9 +9,8 @@
 
 #include "ngs.h"
 
-// rows of one call (all scenes of a batch together); n * k_eff must also stay
-// at or below NGS_MAX_SLOTS, so that slot indices v * k_eff + j fit int32
-#define NGS_MAX_N ((int64_t)1 << 26)
+// NGS_MAX_N (ngs.h) bounds the rows of one call; n * k_eff must also stay at
+// or below NGS_MAX_SLOTS, so that slot indices v * k_eff + j fit int32
 #define NGS_MAX_SLOTS ((int64_t)1 << 30)
 #define NGS_LEAF 32                     // kNN tree leaf = one warp of points
 

@@ -11,17 +11,20 @@ def d2_fp64(xyz, i, js):
     return np.sum((x[js] - x[i]) ** 2, axis=1)
 
 
-def knn_agreement(xyz, got, ref, rel=1e-6):
+def knn_agreement(xyz, got, ref, rel=1e-6, rows=None):
     """Neighbour lists must be identical except where FP64 squared distances
     are within `rel` of each other (near ties may reorder or swap the last
-    member).  Returns the number of rows that differ (all explained)."""
+    member).  Row r of `got` and `ref` is the list of point rows[r] (of point
+    r when rows is None).  Returns the number of rows that differ (all
+    explained)."""
     differ = 0
-    for i in np.nonzero(np.any(got != ref, axis=1))[0]:
+    for r in np.nonzero(np.any(got != ref, axis=1))[0]:
         differ += 1
-        dg = d2_fp64(xyz, i, got[i])
-        dr = d2_fp64(xyz, i, ref[i])
-        assert len(set(got[i].tolist())) == got.shape[1], f"row {i}: duplicate neighbours"
-        assert i not in set(got[i].tolist()), f"row {i}: self in list"
+        i = r if rows is None else int(rows[r])
+        dg = d2_fp64(xyz, i, got[r])
+        dr = d2_fp64(xyz, i, ref[r])
+        assert len(set(got[r].tolist())) == got.shape[1], f"row {i}: duplicate neighbours"
+        assert i not in set(got[r].tolist()), f"row {i}: self in list"
         scale = max(dr.max(), 1e-300)
         assert np.all(np.abs(np.sort(dg) - np.sort(dr)) <= rel * scale), \
             f"row {i}: neighbour distances differ beyond near-ties"
@@ -63,6 +66,26 @@ def greedy_certificate(n, lo, hi, cost64, pairs, rel=1e-6):
         if not (best <= c + rel * max(abs(c), 1.0)):
             bad += 1
     return bad
+
+
+def check_merge_rows(cur, sub, got, ref):
+    """Merged rows `got` (GPU) against `ref` (FP64 oracle) for the pairs `sub`
+    of rows of `cur`: centre relative to the pair's span, covariance relative
+    to its Frobenius norm, SH relative to |f_i| + |f_j|, opacity on alpha."""
+    i, j = sub[:, 0], sub[:, 1]
+    xyz, ls, rot, logit, sh = (a.astype(np.float64) for a in got)
+    rxyz, rls, rrot, rlogit, rsh = ref
+    span = np.linalg.norm(cur.xyz[i].astype(np.float64) - cur.xyz[j], axis=1) + \
+        np.exp(cur.log_scale[i].astype(np.float64)).max(1)
+    eps32 = np.finfo(np.float32).eps
+    assert np.all(np.linalg.norm(xyz - rxyz, axis=1) <=
+                  ATTR_RTOL * span + 4 * eps32 * np.linalg.norm(rxyz, axis=1))
+    S, RS = sigma_of(ls, rot), sigma_of(rls, rrot)
+    assert np.all(np.linalg.norm(S - RS, axis=(1, 2)) <= ATTR_RTOL * np.linalg.norm(RS, axis=(1, 2)))
+    fs = np.abs(cur.sh[i].astype(np.float64)) + np.abs(cur.sh[j])
+    assert np.all(np.abs(sh - rsh) <= ATTR_RTOL * fs + 1e-7)
+    a, ra = 1 / (1 + np.exp(-logit)), 1 / (1 + np.exp(-rlogit))
+    assert np.all(np.abs(a - ra) <= ATTR_RTOL * ra)
 
 
 def small_scene(n, seed=0, kind="unit"):

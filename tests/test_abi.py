@@ -71,6 +71,26 @@ def test_struct_layouts_match_header():
     assert sizes == [ctypes.sizeof(getattr(binding, n)) for n in names]
 
 
+def test_binding_constants_match_header():
+    """Status codes and limits of the binding equal the header's macros (gcc)."""
+    import subprocess
+    import tempfile
+    from paper_2603_16103_gb300 import binding
+    names = ["NGS_OK", "NGS_ERR_INVALID_ARG", "NGS_ERR_OOM", "NGS_ERR_CUDA", "NGS_ERR_TIMEOUT",
+             "NGS_ERR_BUDGET", "NGS_ERR_STATE", "NGS_MAX_K", "NGS_MAX_N", "NGS_MAX_S",
+             "NGS_MAX_SCENES", "NGS_STATS_MAX_PASSES"]
+    src = ('#include <stdio.h>\n#include "ngs.h"\nint main(){'
+           + "".join(f'printf("%lld\\n", (long long)({n}));' for n in names) + "}\n")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "k.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "k")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True,
+                                               check=True).stdout.split()]
+    assert vals == [getattr(binding, n) for n in names]
+
+
 def test_default_tuning_host_only():
     from paper_2603_16103_gb300 import binding
     t = binding.ngs_default_tuning()

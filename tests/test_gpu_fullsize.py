@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_util import ATTR_RTOL, COST_RTOL, knn_agreement, sigma_of, stepwise
+from gpu_util import COST_RTOL, check_merge_rows, knn_agreement, stepwise
 from paper_2603_16103_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -101,12 +101,7 @@ def test_6m_sampled_neighbour_lists(run6m):
     cur = run6m["cur"]
     rows = np.random.default_rng(61).choice(cur.n, 300, replace=False)
     ref = O.knn(cur.xyz, 16, queries=rows)
-    got = run6m["nbr"][rows]
-    # knn_agreement indexes rows of the full scene
-    full_got = np.zeros((cur.n, 16), np.int32)
-    full_ref = np.zeros((cur.n, 16), np.int32)
-    full_got[rows], full_ref[rows] = got, ref
-    assert knn_agreement(cur.xyz, full_got, full_ref) <= 1
+    assert knn_agreement(cur.xyz, run6m["nbr"][rows], ref, rows=rows) <= 1
 
 
 def test_6m_edges_are_the_union_of_the_lists(run6m):
@@ -152,23 +147,6 @@ def _merged_rows(cur, pairs_all, out, sub):
     shift = np.cumsum(removed)[:-1]
     idx = sub[:, 0] - shift[sub[:, 0]]
     return tuple(a[idx] for a in out)
-
-
-def check_merge_rows(cur, sub, got, ref):
-    i, j = sub[:, 0], sub[:, 1]
-    xyz, ls, rot, logit, sh = (a.astype(np.float64) for a in got)
-    rxyz, rls, rrot, rlogit, rsh = ref
-    span = np.linalg.norm(cur.xyz[i].astype(np.float64) - cur.xyz[j], axis=1) + \
-        np.exp(cur.log_scale[i].astype(np.float64)).max(1)
-    eps32 = np.finfo(np.float32).eps
-    assert np.all(np.linalg.norm(xyz - rxyz, axis=1) <=
-                  ATTR_RTOL * span + 4 * eps32 * np.linalg.norm(rxyz, axis=1))
-    S, RS = sigma_of(ls, rot), sigma_of(rls, rrot)
-    assert np.all(np.linalg.norm(S - RS, axis=(1, 2)) <= ATTR_RTOL * np.linalg.norm(RS, axis=(1, 2)))
-    fs = np.abs(cur.sh[i].astype(np.float64)) + np.abs(cur.sh[j])
-    assert np.all(np.abs(sh - rsh) <= ATTR_RTOL * fs + 1e-7)
-    a, ra = 1 / (1 + np.exp(-logit)), 1 / (1 + np.exp(-rlogit))
-    assert np.all(np.abs(a - ra) <= ATTR_RTOL * ra)
 
 
 @pytest.mark.parametrize("ratio", [0.1, 0.01])
