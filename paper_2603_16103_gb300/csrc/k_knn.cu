@@ -261,10 +261,42 @@ __device__ __forceinline__ void sort_desc(uint64_t (&a)[N]) {
             }
 }
 
-// Insert each lane's queued keys into its list, in warp-wide rounds.  A lane
-// whose list is still empty (all k_eff = KMAX slots unused) takes its queue
-// by one sorting network instead of one insertion per key: the result is the
-// same list (the queued keys, largest first, padded with the empty marker).
+// Merge up to 8 queued keys (queue rows b0 .. b0+7 of this lane) into a full
+// list of KMAX keys by a network: the chunk sorted ascending against the list
+// (descending) keeps the elementwise smaller keys, which are the KMAX
+// smallest of both as a bitonic sequence; a bitonic merge puts them back in
+// descending order.  Same list as inserting the keys one by one.
+template <int KMAX>
+__device__ __forceinline__ void merge_chunk8(uint64_t (*queue)[32], int lane, int b0, int qlen,
+                                             TopK<KMAX> &tk) {
+    uint64_t a[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) a[i] = b0 + i < qlen ? queue[b0 + i][lane] : ~0ull;
+    sort_desc<8>(a);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint64_t y = a[7 - i];
+        if (y < tk.key[i]) tk.key[i] = y;
+    }
+#pragma unroll
+    for (int j = KMAX / 2; j > 0; j >>= 1)
+#pragma unroll
+        for (int i = 0; i < KMAX; i++)
+            if ((i & j) == 0) {
+                const uint64_t x = tk.key[i], y = tk.key[i + j];
+                const bool gt = x > y;
+                tk.key[i] = gt ? x : y;
+                tk.key[i + j] = gt ? y : x;
+            }
+}
+
+// Insert each lane's queued keys into its list.  A lane whose list is still
+// empty (all k_eff = KMAX slots unused) takes its queue by one sorting network
+// instead of one insertion per key: the result is the same list (the queued
+// keys, largest first, padded with the empty marker).  Otherwise the queue is
+// taken in warp-wide chunks of 8 rows: a chunk in which some lane holds 4 or
+// more keys goes through the merge network (full-width lists only), a smaller
+// one by single insertions.
 template <int KMAX>
 __device__ __forceinline__ void flush_queue(uint64_t (*queue)[32], int lane, int &qlen,
                                             TopK<KMAX> &tk, int keff) {
@@ -279,10 +311,26 @@ __device__ __forceinline__ void flush_queue(uint64_t (*queue)[32], int lane, int
         qlen = 0;
     }
     const int rounds = __reduce_max_sync(FULL_MASK, qlen);
-    for (int r = 0; r < rounds; r++) {
-        if (r < qlen) {
-            uint64_t x = queue[r][lane];
-            if (x < tk.kth()) tk.insert(x);
+    if (KMAX == 16 && keff == KMAX) {  // keff is the same for every lane
+        for (int b0 = 0; b0 < rounds; b0 += 8) {
+            const int cnt = min(8, rounds - b0);
+            if (cnt >= 4) {
+                merge_chunk8<KMAX>(queue, lane, b0, qlen, tk);
+            } else {
+                for (int r = b0; r < b0 + cnt; r++) {
+                    if (r < qlen) {
+                        uint64_t x = queue[r][lane];
+                        if (x < tk.kth()) tk.insert(x);
+                    }
+                }
+            }
+        }
+    } else {
+        for (int r = 0; r < rounds; r++) {
+            if (r < qlen) {
+                uint64_t x = queue[r][lane];
+                if (x < tk.kth()) tk.insert(x);
+            }
         }
     }
     qlen = 0;
