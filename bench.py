@@ -57,6 +57,9 @@ ALGO = {
     "slot_fill": ("hbm", lambda n, e, p: n * 16 * 4 + e * 16, "GB/s"),
     # round 0 of the matching: each vertex's 16 slot ids and costs read, its choice written
     "match_scan": ("hbm", lambda n, e, p: n * (16 * 8 + 8), "GB/s"),
+    # proposal form of the matching: each vertex's 16 slot ids and costs read,
+    # its 8-byte offer written, its partner and pair cost written
+    "suitor": ("hbm", lambda n, e, p: n * (16 * 8 + 8 + 8), "GB/s"),
 }
 
 # DRAM traffic per launch from ncu captures, in bytes per splat of the pass

@@ -133,7 +133,8 @@ typedef struct {
     int64_t n_filtered;     /* splats after the pre-filter                   */
     int64_t n_output;       /* splats returned                               */
     int32_t passes;         /* passes run                                    */
-    int32_t matching_rounds;/* locally-dominant rounds, summed over passes   */
+    int32_t matching_rounds;/* matching rounds summed over passes (the      *
+                             * proposal form counts one per pass)          */
     int64_t pass_n[NGS_STATS_MAX_PASSES];     /* N at the start of pass p   */
     int64_t pass_edges[NGS_STATS_MAX_PASSES]; /* |E| of pass p              */
     int64_t pass_pairs[NGS_STATS_MAX_PASSES]; /* merged pairs of pass p     */
@@ -304,10 +305,14 @@ typedef struct {
                                     per point (at most 8^9 cells), default 4 */
     int32_t cost_blocks_per_sm;  /* edge-cost grid: 256-thread blocks per SM (1..64),
                                     default 8 */
-    int32_t match_graph;         /* 1: the matching rounds after the first run as one
-                                    CUDA graph (a conditional WHILE node, no host round
-                                    trip per batch of rounds); 0: batches of rounds
-                                    launched and checked from the host.  Default 1 */
+    int32_t match_method;        /* pair selection, same pairs for each:
+                                    2: proposals (one kernel; the round form is run
+                                       instead if a thread exceeds its step limit);
+                                    1: locally-dominant rounds, those after the first
+                                       as one CUDA graph (a conditional WHILE node, no
+                                       host round trip per batch of rounds);
+                                    0: the rounds in batches launched and checked
+                                       from the host.  Default 2 */
 } ngs_tuning;
 
 void ngs_default_tuning(ngs_tuning *tuning);

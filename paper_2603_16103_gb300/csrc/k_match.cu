@@ -8,9 +8,11 @@
 //   * mutual pointers are matched (such an edge is the minimum of all edges
 //     touching either endpoint, so greedy would take it too);
 //   * a vertex re-scans only when its target was matched elsewhere.
-// Under a strict total order this reaches exactly the greedy matching.  The
-// cap keeps the P smallest matched edges, which are the greedy's first P
-// picks, found by a radix select on (cost bits, lo canonical id).
+// Under a strict total order this reaches exactly the greedy matching.  A
+// second form reaches the same matching by proposals (Manne and
+// Halappanavar's Suitor scheme) in one kernel; see k_suitor.  The cap keeps
+// the P smallest matched edges, which are the greedy's first P picks, found
+// by a radix select on (cost bits, lo canonical id).
 #include "ngs_device.cuh"
 #include "ngs_internal.h"
 
@@ -226,6 +228,152 @@ __global__ void k_write_pairs(int64_t n, const int32_t *__restrict__ partner,
     }
 }
 
+// ---------------------------------------------------------------- proposals
+// offer[v] = the best offer v holds: (cost order bits << 32) | the proposer's
+// canonical id.  For a fixed v this orders its edges exactly as (cost, lo,
+// hi), since lo and hi differ only in the other endpoint.  pos_of_cid maps a
+// canonical id back to its row.
+__global__ void k_suitor_init(int64_t n, const int32_t *__restrict__ cid, unsigned long long *offer,
+                              int32_t *pos_of_cid) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        offer[v] = ~0ull;
+        if (cid) pos_of_cid[cid[v]] = (int32_t)v;
+    }
+}
+
+// Each thread starts at one vertex u and proposes along u's best edge among
+// those that would improve the other endpoint's offer (ordered by cost, then
+// the other endpoint's canonical id, i.e. by (cost, lo, hi) for a fixed u).
+// The proposal is an atomicMin on that endpoint's offer; if it wins, the
+// previous holder (if any) has lost its partner and this thread continues
+// with it; if another offer got there first, u looks again.  Offers only
+// decrease, so the process ends; with a strict total order on the edges the
+// mutual offers at the end are the greedy matching, whatever the order in
+// which the threads run.  Offers are read through L2 (coherent with the
+// atomics).  A thread that takes more than max_steps proposals sets status
+// and stops; the caller then uses the round form instead.
+template <int K>
+__global__ void k_suitor(int64_t n, int kk, const int32_t *__restrict__ nbr,
+                         const float *__restrict__ cost_slot, const int32_t *__restrict__ rev_ptr,
+                         const int32_t *__restrict__ rev, const int32_t *__restrict__ cid,
+                         const int32_t *__restrict__ pos_of_cid, unsigned long long *offer,
+                         int32_t *status, int max_steps) {
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v0 < n;
+         v0 += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = (int32_t)v0;
+        for (int step = 0; u >= 0; step++) {
+            if (step >= max_steps) {
+                atomicOr(status, 1);
+                break;
+            }
+            const unsigned long long cu = cid_of(cid, u);
+            int32_t best = -1;
+            uint32_t bk = 0xffffffffu;
+            // an edge to v at cost c is a candidate if u's offer would beat v's
+            auto consider = [&](int32_t v, float c, unsigned long long held) {
+                const uint32_t k = cost_order_bits(c);
+                if ((((unsigned long long)k << 32) | cu) >= held) return;
+                if (best < 0 || k < bk || (k == bk && cid_of(cid, v) < cid_of(cid, best))) {
+                    best = v;
+                    bk = k;
+                }
+            };
+            const int64_t base = (int64_t)u * kk;
+            if (K > 0) {
+                constexpr int KK = K > 0 ? K : 4;
+                int32_t vs[KK];
+                float cs[KK];
+                unsigned long long hs[KK];
+                const int4 *nb4 = (const int4 *)(nbr + base);
+                const float4 *cs4 = (const float4 *)(cost_slot + base);
+#pragma unroll
+                for (int t4 = 0; t4 < K / 4; t4++) {
+                    const int4 v4 = __ldg(nb4 + t4);
+                    const float4 c4 = __ldg(cs4 + t4);
+                    vs[4 * t4] = v4.x; vs[4 * t4 + 1] = v4.y; vs[4 * t4 + 2] = v4.z; vs[4 * t4 + 3] = v4.w;
+                    cs[4 * t4] = c4.x; cs[4 * t4 + 1] = c4.y; cs[4 * t4 + 2] = c4.z; cs[4 * t4 + 3] = c4.w;
+                }
+#pragma unroll
+                for (int t = 0; t < KK; t++) hs[t] = __ldcg(offer + vs[t]);
+#pragma unroll
+                for (int t = 0; t < KK; t++) consider(vs[t], cs[t], hs[t]);
+            } else {
+                for (int t = 0; t < kk; t++) {
+                    const int32_t v = nbr[base + t];
+                    consider(v, cost_slot[base + t], __ldcg(offer + v));
+                }
+            }
+            const int32_t r1 = rev_ptr[u + 1];
+            for (int32_t r = rev_ptr[u]; r < r1; r += 4) {
+                int32_t ss[4], vv[4];
+                float cc[4];
+                unsigned long long hh[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) ss[q] = r + q < r1 ? __ldg(rev + r + q) : -1;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    vv[q] = ss[q] >= 0 ? ss[q] / kk : 0;
+                    cc[q] = ss[q] >= 0 ? __ldg(cost_slot + ss[q]) : 0.f;
+                    hh[q] = ss[q] >= 0 ? __ldcg(offer + vv[q]) : 0ull;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (ss[q] >= 0) consider(vv[q], cc[q], hh[q]);
+            }
+            if (best < 0) break;  // no edge left that u could win: u stays single
+            const unsigned long long mine = ((unsigned long long)bk << 32) | cu;
+            const unsigned long long prev = atomicMin(offer + best, mine);
+            if (prev > mine) {
+                // u holds best's offer now; the previous holder proposes again
+                u = prev == ~0ull ? -1
+                                  : (cid ? pos_of_cid[(uint32_t)prev] : (int32_t)(uint32_t)prev);
+            }
+            // else a better offer arrived first: u looks again
+        }
+    }
+}
+
+// Mutual offers are the pairs: mate[], the pair's cost bits in candkey[]
+// (as the round form leaves them), and the number of pairs.
+__global__ void k_suitor_mates(int64_t n, const unsigned long long *__restrict__ offer,
+                               const int32_t *__restrict__ cid, const int32_t *__restrict__ pos_of_cid,
+                               int32_t *mate, uint32_t *candkey, int32_t *pairs) {
+    int found = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long w = offer[v];
+        int32_t m = -1;
+        if (w != ~0ull) {
+            const int32_t u = cid ? pos_of_cid[(uint32_t)w] : (int32_t)(uint32_t)w;
+            const uint32_t cv = cid_of(cid, (int32_t)v);
+            if ((uint32_t)offer[u] == cv) {
+                m = u;
+                if (cv < (uint32_t)w) found++;
+            }
+        }
+        mate[v] = m;
+        candkey[v] = m >= 0 ? (uint32_t)(w >> 32) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(FULL_MASK, found, o);
+    if ((threadIdx.x & 31) == 0 && found) atomicAdd(pairs, found);
+}
+
+using SuitorKernel = void (*)(int64_t, int, const int32_t *, const float *, const int32_t *,
+                              const int32_t *, const int32_t *, const int32_t *,
+                              unsigned long long *, int32_t *, int);
+
+SuitorKernel suitor_kernel(int k) {
+    switch (k) {
+    case 4: return k_suitor<4>;
+    case 8: return k_suitor<8>;
+    case 16: return k_suitor<16>;
+    case 32: return k_suitor<32>;
+    default: return k_suitor<0>;
+    }
+}
+
 // Device-side control of the captured rounds.  State (int32): [0] worklist A
 // size, [1] worklist B size, [2] pairs of round A, [3] pairs of round B,
 // [4] rounds done, [5] pairs in all, [6] round limit reached, [7] pairs of
@@ -359,6 +507,33 @@ static bool match_rounds_graph(ngs_ctx *c, const GraphDev &g, int32_t *mate, int
     return true;
 }
 
+// The proposal form: returns false (and no result) if a thread exceeded its
+// step limit.  pos_of_cid: n ints of scratch.
+static bool match_suitor(ngs_ctx *c, const GraphDev &g, int32_t *mate, int32_t *pos_of_cid,
+                         uint32_t *candkey, int64_t *matched) {
+    const int64_t n = g.n;
+    unsigned long long *offer = ws<unsigned long long>(c, c->b_offer, n);
+    int32_t *stt = ws<int32_t>(c, c->b_mstate, 16);
+    NGS_CHECK_CUDA(cudaMemsetAsync(stt, 0, 2 * sizeof(int32_t), c->st));
+    const unsigned grid = grid_stride_blocks(c, n, 256, 8);
+    launch(c, "suitor_init", dim3(grid), dim3(256), 0, k_suitor_init, n, g.cid, offer, pos_of_cid);
+    // one thread per starting vertex, in small blocks: the proposal chains
+    // differ in length (about 1.7 proposals and 0.35 lost bids per vertex,
+    // chains of at most 8 on the 6M-splat scene)
+    launch(c, "suitor", dim3(blocks_for(n, 64)), dim3(64), 0, suitor_kernel(g.k_eff), n, g.k_eff, g.nbr,
+           (const float *)g.cost_slot, (const int32_t *)g.rev_ptr, (const int32_t *)g.rev, g.cid,
+           (const int32_t *)pos_of_cid, offer, stt, 1 << 16);
+    launch(c, "suitor_mates", dim3(grid), dim3(256), 0, k_suitor_mates, n,
+           (const unsigned long long *)offer, g.cid, (const int32_t *)pos_of_cid, mate, candkey,
+           stt + 1);
+    int32_t *hs = (int32_t *)(c->h_pin + 32);
+    get_small(c, hs, stt, 2 * sizeof(int32_t));
+    sync_stream(c);
+    if (hs[0]) return false;
+    *matched = hs[1];
+    return true;
+}
+
 int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
     const int64_t n = g.n;
     c->rounds = 0;
@@ -366,6 +541,15 @@ int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
     int32_t *mate = ws<int32_t>(c, c->b_mate, n);
     int32_t *cand = ws<int32_t>(c, c->b_cand, n);
     uint32_t *candkey = ws<uint32_t>(c, c->b_candkey, n);
+    if (g.n_edges > 0 && c->tune.match_method == 2) {
+        // cand serves as the proposal form's id map
+        int64_t matched = 0;
+        if (match_suitor(c, g, mate, cand, candkey, &matched)) {
+            c->rounds = 1;
+            return matched;
+        }
+        // a thread hit its step limit: the round form from the start
+    }
     const int max_rounds = 4096;
     int32_t *counts = ws<int32_t>(c, c->b_counts, 2 * max_rounds);
     int32_t *wl_counts = counts + max_rounds;  // worklist size feeding round r+1
@@ -375,7 +559,7 @@ int64_t match_rounds(ngs_ctx *c, const GraphDev &g) {
     launch(c, "match_init", dim3(grid), dim3(256), 0, k_match_init, n, mate, cand);
     int64_t matched = 0;
     int r = 0;
-    if (g.n_edges > 0 && c->tune.match_graph) {
+    if (g.n_edges > 0 && c->tune.match_method >= 1) {  // rounds in a CUDA graph
         int32_t *stt = ws<int32_t>(c, c->b_mstate, 16);
         NGS_CHECK_CUDA(cudaMemsetAsync(stt, 0, 16 * sizeof(int32_t), c->st));
         // round 0 over every vertex, then the captured loop

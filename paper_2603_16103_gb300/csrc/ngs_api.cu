@@ -239,7 +239,7 @@ static void release_all(ngs_ctx *c) {
                       &c->b_cand, &c->b_candkey, &c->b_counts, &c->b_sel, &c->b_role, &c->b_keep,
                       &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
                       &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2,
-                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc, &c->b_fp64list, &c->b_mstate, &c->b_order0};
+                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc, &c->b_fp64list, &c->b_mstate, &c->b_offer, &c->b_order0};
     for (DevBuf *b : bufs) ws_free(c, *b);
     for (int k = 0; k < 5; k++) {
         ws_free(c, c->b_sA[k]);
@@ -653,7 +653,7 @@ extern "C" void ngs_default_tuning(ngs_tuning *t) {
     t->knn_block_min = d.knn_block_min;
     t->cells_per_point = d.cells_per_point;
     t->cost_blocks_per_sm = d.cost_blocks_per_sm;
-    t->match_graph = d.match_graph;
+    t->match_method = d.match_method;
 }
 
 extern "C" int ngs_get_tuning(ngs_ctx *c, ngs_tuning *t) {
@@ -661,7 +661,7 @@ extern "C" int ngs_get_tuning(ngs_ctx *c, ngs_tuning *t) {
     t->knn_block_min = c->tune.knn_block_min;
     t->cells_per_point = c->tune.cells_per_point;
     t->cost_blocks_per_sm = c->tune.cost_blocks_per_sm;
-    t->match_graph = c->tune.match_graph;
+    t->match_method = c->tune.match_method;
     return NGS_OK;
 }
 
@@ -670,14 +670,14 @@ extern "C" int ngs_set_tuning(ngs_ctx *c, const ngs_tuning *t) {
     const int cpp = t->cells_per_point;
     if (t->knn_block_min < 16 || t->knn_block_min > 1024 ||
         !(cpp == 1 || cpp == 2 || cpp == 4 || cpp == 8) || t->cost_blocks_per_sm < 1 ||
-        t->cost_blocks_per_sm > 64 || (t->match_graph != 0 && t->match_graph != 1)) {
+        t->cost_blocks_per_sm > 64 || t->match_method < 0 || t->match_method > 2) {
         ngs_set_error("ngs_set_tuning: field out of range");
         return NGS_ERR_INVALID_ARG;
     }
     c->tune.knn_block_min = t->knn_block_min;
     c->tune.cells_per_point = cpp;
     c->tune.cost_blocks_per_sm = t->cost_blocks_per_sm;
-    c->tune.match_graph = t->match_graph;
+    c->tune.match_method = t->match_method;
     return NGS_OK;
 }
 

@@ -94,7 +94,7 @@ struct Tuning {
     int knn_block_min = 64;      // points the kNN 3x3x3 block must hold
     int cells_per_point = 4;     // cell-table density (cells >= this x points)
     int cost_blocks_per_sm = 8;  // edge-cost grid, 256-thread blocks per SM
-    int match_graph = 1;         // matching rounds after the first as one CUDA graph
+    int match_method = 2;        // 2 proposals, 1 rounds in a CUDA graph, 0 host-driven rounds
 };
 
 struct ngs_ctx {
@@ -124,6 +124,7 @@ struct ngs_ctx {
     DevBuf b_sC[5];              // third splat array set (several scenes at once)
     DevBuf b_fp64list;           // edges whose cost is evaluated in FP64
     DevBuf b_mstate;             // device-side state of the captured matching rounds
+    DevBuf b_offer;              // best offer per vertex (proposal form of the matching)
     DevBuf b_eng[32];            // per-scene tables and scratch of the multi-scene engine
 
     // pinned host scratch
