@@ -281,23 +281,23 @@ __global__ void k_suitor(int64_t n, int kk, const int32_t *__restrict__ nbr,
             };
             const int64_t base = (int64_t)u * kk;
             if (K > 0) {
-                constexpr int KK = K > 0 ? K : 4;
-                int32_t vs[KK];
-                float cs[KK];
-                unsigned long long hs[KK];
+                // four slots at a time: ids and costs as 16-byte vectors, then
+                // their offers; few live registers, so many warps hide the
+                // latency of the offer loads
                 const int4 *nb4 = (const int4 *)(nbr + base);
                 const float4 *cs4 = (const float4 *)(cost_slot + base);
-#pragma unroll
+#pragma unroll 1
                 for (int t4 = 0; t4 < K / 4; t4++) {
                     const int4 v4 = __ldg(nb4 + t4);
                     const float4 c4 = __ldg(cs4 + t4);
-                    vs[4 * t4] = v4.x; vs[4 * t4 + 1] = v4.y; vs[4 * t4 + 2] = v4.z; vs[4 * t4 + 3] = v4.w;
-                    cs[4 * t4] = c4.x; cs[4 * t4 + 1] = c4.y; cs[4 * t4 + 2] = c4.z; cs[4 * t4 + 3] = c4.w;
+                    const int32_t vs[4] = {v4.x, v4.y, v4.z, v4.w};
+                    const float cs[4] = {c4.x, c4.y, c4.z, c4.w};
+                    unsigned long long hs[4];
+#pragma unroll
+                    for (int t = 0; t < 4; t++) hs[t] = __ldcg(offer + vs[t]);
+#pragma unroll
+                    for (int t = 0; t < 4; t++) consider(vs[t], cs[t], hs[t]);
                 }
-#pragma unroll
-                for (int t = 0; t < KK; t++) hs[t] = __ldcg(offer + vs[t]);
-#pragma unroll
-                for (int t = 0; t < KK; t++) consider(vs[t], cs[t], hs[t]);
             } else {
                 for (int t = 0; t < kk; t++) {
                     const int32_t v = nbr[base + t];
