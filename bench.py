@@ -518,7 +518,7 @@ def main():
         host = host_src.clone()
         host = B.DeviceSplats(*(a.pin_memory() for a in host.tensors()))
         e2e_t = 0.0
-        reps = max(1, min(args.steps, 3))
+        reps = max(1, min(args.steps, 5))
         for it in range(reps + 1):
             for a, b in zip(host.tensors(), host_src.tensors()):
                 a.copy_(b)
