@@ -232,17 +232,11 @@ __device__ __forceinline__ void cov6(const float *R, const float *s, float *S6) 
             S6[idx++] = R[3 * a] * s2[0] * R[3 * b] + R[3 * a + 1] * s2[1] * R[3 * b + 1] +
                         R[3 * a + 2] * s2[2] * R[3 * b + 2];
 }
-struct Rec {
-    const float4 *p;
-    __device__ __forceinline__ float4 g(int k) const { return __ldg(p + k); }
-};
-
-__device__ __forceinline__ void load_R(const Rec &r, float *R, float *invs) {
-    const float4 a = r.g(1), b = r.g(2), c = r.g(3);
-    R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w;
-    R[4] = b.x; R[5] = b.y; R[6] = b.z; R[7] = b.w;
-    R[8] = c.x;
-    invs[0] = c.y; invs[1] = c.z; invs[2] = c.w;
+// 32 bytes through the read-only path in one load (p 32-byte aligned)
+__device__ __forceinline__ void ldg_v8(const float *p, float *r) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+        : "l"(p));
 }
 
 template <int MODE>
@@ -321,11 +315,24 @@ __global__ void __launch_bounds__(256, 4)
         if (!valid) continue;
         const int32_t sl = er.x;
         const int64_t i = er.y, j = er.z;
-        const Rec Ri{(const float4 *)(rec + i * REC)}, Rj{(const float4 *)(rec + j * REC)};
-        const float4 i0 = Ri.g(0), j0 = Rj.g(0);
+        float ri[16], rj[16];
+        ldg_v8(rec + i * REC, ri);
+        ldg_v8(rec + i * REC + 8, ri + 8);
+        ldg_v8(rec + j * REC, rj);
+        ldg_v8(rec + j * REC + 8, rj + 8);
+        const float4 i0 = make_float4(ri[0], ri[1], ri[2], ri[3]);
+        const float4 j0 = make_float4(rj[0], rj[1], rj[2], rj[3]);
         float Rm[9], invs_i[3], Rn[9], invs_j[3];
-        load_R(Ri, Rm, invs_i);
-        load_R(Rj, Rn, invs_j);
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            Rm[k] = ri[R_R + k];
+            Rn[k] = rj[R_R + k];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            invs_i[a] = ri[R_INVS + a];
+            invs_j[a] = rj[R_INVS + a];
+        }
         float si[3], sj[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -487,6 +494,8 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
     float *zs = ws<float>(c, c->b_rng, 4 * S);
     put_small(c, zs, h.data(), sizeof(float) * 4 * (size_t)S);
     float *rec = ws<float>(c, c->b_rec, s.n * REC);
+    // the edge-cost kernel reads each 64-byte record as two 32-byte loads
+    if ((uintptr_t)rec & 31) NGS_FAIL(NGS_ERR_CUDA, "edge_costs: record buffer not 32-byte aligned");
     launch(c, "cost_prep", dim3(grid_stride_blocks(c, s.n, 256, 8)), dim3(256), 0, k_prep, s.xyz,
            s.ls, s.rot, s.logit, s.n, rec);
     unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c, c->b_status, 64);
