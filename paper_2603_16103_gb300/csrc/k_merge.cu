@@ -361,7 +361,17 @@ __device__ __forceinline__ void move_chunk(const Rows &in, int64_t a, const WRow
 
 // merge rows i and j of `in` into row o of `out`; returns 1 if an eigenvalue
 // was raised to the floor
-__device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out, int64_t o, int F,
+// 32 bytes in one load (read-only path) or one store; p 32-byte aligned
+__device__ __forceinline__ void ldg_v8m(const float *p, float *r) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+        : "l"(p));
+}
+__device__ __forceinline__ void stg_v8m(float *p, const float *r) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "l"(p), "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]));
+}
+__device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out, int64_t o, int F, int sh8,
                           double eig_floor, int policy) {
     // every input field through the read-only path, so no load waits behind
     // an output store
@@ -383,8 +393,18 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
         mj[a] = __ldg(in.xyz + 3 * j + a);
         out.xyz[3 * o + a] = pi * mi[a] + pj * mj[a];
     }
-    // appearance
-    if ((F & 3) == 0) {
+    // appearance: 32-byte chunks when F % 8 == 0 and both arrays are 32-byte
+    // aligned (sh8), else 16-byte chunks, else scalars
+    if (sh8) {
+        for (int t = 0; t < F / 8; t++) {
+            float a[8], b[8], r[8];
+            ldg_v8m(in.sh + i * F + 8 * t, a);
+            ldg_v8m(in.sh + j * F + 8 * t, b);
+#pragma unroll
+            for (int q = 0; q < 8; q++) r[q] = pi * a[q] + pj * b[q];
+            stg_v8m(out.sh + o * F + 8 * t, r);
+        }
+    } else if ((F & 3) == 0) {
         const float4 *fi = (const float4 *)(in.sh + i * F), *fj = (const float4 *)(in.sh + j * F);
         float4 *fo = (float4 *)(out.sh + o * F);
         // read-only loads: the compiler may issue them ahead of the stores
@@ -490,14 +510,14 @@ __global__ void k_list_merges(int64_t n, const int32_t *__restrict__ mflag,
         if (mflag[v]) list[mpos[v]] = (int32_t)v;
 }
 
-__global__ void k_merge(Rows in, WRows out, const int32_t *__restrict__ list, int64_t npairs, int F,
+__global__ void k_merge(Rows in, WRows out, const int32_t *__restrict__ list, int64_t npairs, int F, int sh8,
                         const int32_t *__restrict__ role, const int32_t *__restrict__ pos,
                         double eig_floor, int policy, unsigned long long *floor_hits) {
     int hits = 0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npairs;
          t += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = list[t];
-        hits += merge_pair(in, i, role[i], out, pos[i], F, eig_floor, policy);
+        hits += merge_pair(in, i, role[i], out, pos[i], F, sh8, eig_floor, policy);
     }
     if (hits) atomicAdd(floor_hits, (unsigned long long)hits);
 }
@@ -637,7 +657,9 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
     NGS_CHECK_CUDA(cudaMemsetAsync(hits, 0, 8, c->st));
     if (npairs > 0)
         launch(c, "merge", dim3(grid_stride_blocks(c, npairs, 128, 16)), dim3(128), 0, k_merge, ri,
-               wo, (const int32_t *)list, npairs, in.F, role, (const int32_t *)pos,
+               wo, (const int32_t *)list, npairs, in.F,
+               (in.F % 8 == 0 && ((uintptr_t)ri.sh & 31) == 0 && ((uintptr_t)wo.sh & 31) == 0) ? 1 : 0,
+               role, (const int32_t *)pos,
                c->prm.eig_floor, c->prm.fp64_policy, hits);
     get_small(c, c->h_pin + 2, hits, 8);
     if (cid) {
