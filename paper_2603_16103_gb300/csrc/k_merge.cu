@@ -359,8 +359,6 @@ __device__ __forceinline__ void move_chunk(const Rows &in, int64_t a, const WRow
     }
 }
 
-// merge rows i and j of `in` into row o of `out`; returns 1 if an eigenvalue
-// was raised to the floor
 // 32 bytes in one load (read-only path) or one store; p 32-byte aligned
 __device__ __forceinline__ void ldg_v8m(const float *p, float *r) {
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -371,6 +369,8 @@ __device__ __forceinline__ void stg_v8m(float *p, const float *r) {
     asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
                  :: "l"(p), "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]));
 }
+// merge rows i and j of `in` into row o of `out`; returns 1 if an eigenvalue
+// was raised to the floor
 __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out, int64_t o, int F, int sh8,
                           double eig_floor, int policy) {
     // every input field through the read-only path, so no load waits behind
