@@ -66,10 +66,10 @@ ALGO = {
 # (the profiles/ summaries give the commands and the raw counters).
 NCU_TRAFFIC_PER_SPLAT = {
     "knn_k16": 42.44,        # 42.43 MB over 999,792 queries (knn_grid_patches1m.md)
-    "edge_cost": 480.6,      # 480.52 MB over 999,792 splats (edge_cost_patches1m.md)
+    "edge_cost": 480.5,      # 480.37 MB over 999,792 splats (edge_cost_patches1m.md)
     "slot_classify": 104.8,  # 104.76 MB over 999,792 splats (slot_classify_patches1m.md)
     "slot_fill": 250.6,      # 250.57 MB over 999,792 splats (slot_classify_patches1m.md)
-    "merge": 331.2,          # 331.16 MB, pass of 999,792 splats (merge_patches1m.md)
+    "merge": 335.6,          # 335.52 MB, pass of 999,792 splats (merge_patches1m.md)
     "match_scan": 154.8,     # 154.81 MB over 999,792 splats, round 0 (match_scan_patches1m.md)
     "suitor": 163.6,         # 163.52 MB over 999,792 splats (suitor_patches1m.md)
 }
