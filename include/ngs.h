@@ -191,8 +191,9 @@ int ngs_edge_costs(ngs_ctx *ctx, const ngs_splats *splats, const ngs_graph *grap
 /* Disjoint pair selection (Sec. 3.4, Algorithm 1 GreedyDisjointPairs): the
  * greedy matching of `graph` under the strict order (cost, edge id) -- cost
  * ascending, NaN ranked as +inf, -0 as +0 -- keeping its max_pairs smallest
- * members.  Computed as a locally-dominant matching, which yields exactly
- * that set.  pairs_out (device, caller-owned, 2*max_pairs int32) receives
+ * members.  Computed by proposals (or, per ngs_tuning.match_method, by
+ * locally-dominant rounds); under a strict order both yield exactly that
+ * set.  pairs_out (device, caller-owned, 2*max_pairs int32) receives
  * (lo, hi) rows sorted by lo; *n_pairs (host) the count.  Synchronises.
  * Errors: INVALID_ARG, STATE, CUDA, TIMEOUT. */
 int ngs_select_pairs(ngs_ctx *ctx, const ngs_graph *graph, const float *cost,
