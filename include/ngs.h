@@ -314,6 +314,9 @@ typedef struct {
                                        host round trip per batch of rounds);
                                     0: the rounds in batches launched and checked
                                        from the host.  Default 2 */
+    int32_t match_max_steps;     /* proposals a thread may make before the pass
+                                    falls back to the round form (1..2^30), default
+                                    65536 */
 } ngs_tuning;
 
 void ngs_default_tuning(ngs_tuning *tuning);

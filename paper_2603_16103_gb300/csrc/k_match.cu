@@ -522,7 +522,7 @@ static bool match_suitor(ngs_ctx *c, const GraphDev &g, int32_t *mate, int32_t *
     // chains of at most 8 on the 6M-splat scene)
     launch(c, "suitor", dim3(blocks_for(n, 64)), dim3(64), 0, suitor_kernel(g.k_eff), n, g.k_eff, g.nbr,
            (const float *)g.cost_slot, (const int32_t *)g.rev_ptr, (const int32_t *)g.rev, g.cid,
-           (const int32_t *)pos_of_cid, offer, stt, 1 << 16);
+           (const int32_t *)pos_of_cid, offer, stt, c->tune.match_max_steps);
     launch(c, "suitor_mates", dim3(grid), dim3(256), 0, k_suitor_mates, n,
            (const unsigned long long *)offer, g.cid, (const int32_t *)pos_of_cid, mate, candkey,
            stt + 1);

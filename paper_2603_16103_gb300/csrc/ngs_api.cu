@@ -654,6 +654,7 @@ extern "C" void ngs_default_tuning(ngs_tuning *t) {
     t->cells_per_point = d.cells_per_point;
     t->cost_blocks_per_sm = d.cost_blocks_per_sm;
     t->match_method = d.match_method;
+    t->match_max_steps = d.match_max_steps;
 }
 
 extern "C" int ngs_get_tuning(ngs_ctx *c, ngs_tuning *t) {
@@ -662,6 +663,7 @@ extern "C" int ngs_get_tuning(ngs_ctx *c, ngs_tuning *t) {
     t->cells_per_point = c->tune.cells_per_point;
     t->cost_blocks_per_sm = c->tune.cost_blocks_per_sm;
     t->match_method = c->tune.match_method;
+    t->match_max_steps = c->tune.match_max_steps;
     return NGS_OK;
 }
 
@@ -670,7 +672,8 @@ extern "C" int ngs_set_tuning(ngs_ctx *c, const ngs_tuning *t) {
     const int cpp = t->cells_per_point;
     if (t->knn_block_min < 16 || t->knn_block_min > 1024 ||
         !(cpp == 1 || cpp == 2 || cpp == 4 || cpp == 8) || t->cost_blocks_per_sm < 1 ||
-        t->cost_blocks_per_sm > 64 || t->match_method < 0 || t->match_method > 2) {
+        t->cost_blocks_per_sm > 64 || t->match_method < 0 || t->match_method > 2 ||
+        t->match_max_steps < 1 || t->match_max_steps > (1 << 30)) {
         ngs_set_error("ngs_set_tuning: field out of range");
         return NGS_ERR_INVALID_ARG;
     }
@@ -678,6 +681,7 @@ extern "C" int ngs_set_tuning(ngs_ctx *c, const ngs_tuning *t) {
     c->tune.cells_per_point = cpp;
     c->tune.cost_blocks_per_sm = t->cost_blocks_per_sm;
     c->tune.match_method = t->match_method;
+    c->tune.match_max_steps = t->match_max_steps;
     return NGS_OK;
 }
 

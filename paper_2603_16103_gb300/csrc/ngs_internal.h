@@ -95,6 +95,7 @@ struct Tuning {
     int cells_per_point = 4;     // cell-table density (cells >= this x points)
     int cost_blocks_per_sm = 8;  // edge-cost grid, 256-thread blocks per SM
     int match_method = 2;        // 2 proposals, 1 rounds in a CUDA graph, 0 host-driven rounds
+    int match_max_steps = 1 << 16;  // proposal steps per thread before the round form takes over
 };
 
 struct ngs_ctx {

@@ -33,7 +33,8 @@ def test_autotune_picks_a_candidate_and_keeps_results(ngs):
 
 @pytest.mark.parametrize("tuning", [dict(knn_block_min=16, cells_per_point=1, cost_blocks_per_sm=1),
                                     dict(knn_block_min=1024, cells_per_point=8, cost_blocks_per_sm=64),
-                                    dict(match_method=0), dict(match_method=1)])
+                                    dict(match_method=0), dict(match_method=1),
+                                    dict(match_max_steps=1)])   # proposals fall back to rounds
 def test_extreme_tunings_give_identical_results(ngs, tuning):
     scene = small_scene(12000, seed=72)
     target = O.target_count(scene.n, 0.1)
