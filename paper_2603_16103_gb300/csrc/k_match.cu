@@ -253,8 +253,10 @@ __global__ void k_suitor_init(int64_t n, const int32_t *__restrict__ cid, unsign
 // which the threads run.  Offers are read through L2 (coherent with the
 // atomics).  A thread that takes more than max_steps proposals sets status
 // and stops; the caller then uses the round form instead.
+// 32 registers (full occupancy in 64-thread blocks): more warps hide the
+// latency of the offer loads
 template <int K>
-__global__ void k_suitor(int64_t n, int kk, const int32_t *__restrict__ nbr,
+__global__ void __launch_bounds__(64, 32) k_suitor(int64_t n, int kk, const int32_t *__restrict__ nbr,
                          const float *__restrict__ cost_slot, const int32_t *__restrict__ rev_ptr,
                          const int32_t *__restrict__ rev, const int32_t *__restrict__ cid,
                          const int32_t *__restrict__ pos_of_cid, unsigned long long *offer,
