@@ -71,7 +71,7 @@ NCU_TRAFFIC_PER_SPLAT = {
     "slot_fill": 250.6,      # 250.57 MB over 999,792 splats (slot_classify_patches1m.md)
     "merge": 335.6,          # 335.52 MB, pass of 999,792 splats (merge_patches1m.md)
     "match_scan": 154.8,     # 154.81 MB over 999,792 splats, round 0 (match_scan_patches1m.md)
-    "suitor": 163.6,         # 163.52 MB over 999,792 splats (suitor_patches1m.md)
+    "suitor": 170.9,         # 170.88 MB over 999,792 splats (suitor_patches1m.md)
 }
 
 
