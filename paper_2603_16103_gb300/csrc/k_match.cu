@@ -252,15 +252,15 @@ __global__ void k_suitor_init(int64_t n, const int32_t *__restrict__ cid, unsign
 // mutual offers at the end are the greedy matching, whatever the order in
 // which the threads run.  Offers are read through L2 (coherent with the
 // atomics).  A thread that takes more than max_steps proposals sets status
-// and stops; the caller then uses the round form instead.
-// 32 registers (full occupancy in 64-thread blocks): more warps hide the
-// latency of the offer loads
+// and stops; the caller then uses the round form instead.  Launched in
+// 64-thread blocks at 32 registers (full occupancy): more warps hide the
+// latency of the offer loads.
 template <int K>
-__global__ void __launch_bounds__(64, 32) k_suitor(int64_t n, int kk, const int32_t *__restrict__ nbr,
-                         const float *__restrict__ cost_slot, const int32_t *__restrict__ rev_ptr,
-                         const int32_t *__restrict__ rev, const int32_t *__restrict__ cid,
-                         const int32_t *__restrict__ pos_of_cid, unsigned long long *offer,
-                         int32_t *status, int max_steps) {
+__global__ void __launch_bounds__(64, 32)
+    k_suitor(int64_t n, int kk, const int32_t *__restrict__ nbr, const float *__restrict__ cost_slot,
+             const int32_t *__restrict__ rev_ptr, const int32_t *__restrict__ rev,
+             const int32_t *__restrict__ cid, const int32_t *__restrict__ pos_of_cid,
+             unsigned long long *offer, int32_t *status, int max_steps) {
     for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v0 < n;
          v0 += (int64_t)gridDim.x * blockDim.x) {
         int32_t u = (int32_t)v0;
