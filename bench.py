@@ -62,16 +62,17 @@ ALGO = {
     "suitor": ("hbm", lambda n, e, p: n * (16 * 8 + 8 + 8), "GB/s"),
 }
 
-# DRAM traffic per launch from ncu captures, in bytes per splat of the pass
-# (the profiles/ summaries give the commands and the raw counters).
+# DRAM traffic per launch from ncu captures on the first pass of the
+# 1,000,000-splat patch scene (999,792 splats after the pre-filter), in bytes
+# per splat of the pass.
 NCU_TRAFFIC_PER_SPLAT = {
-    "knn_k16": 42.44,        # 42.43 MB over 999,792 queries (knn_grid_patches1m.md)
-    "edge_cost": 480.5,      # 480.37 MB over 999,792 splats (edge_cost_patches1m.md)
-    "slot_classify": 104.8,  # 104.76 MB over 999,792 splats (slot_classify_patches1m.md)
-    "slot_fill": 250.6,      # 250.57 MB over 999,792 splats (slot_classify_patches1m.md)
-    "merge": 335.6,          # 335.52 MB, pass of 999,792 splats (merge_patches1m.md)
-    "match_scan": 154.8,     # 154.81 MB over 999,792 splats, round 0 (match_scan_patches1m.md)
-    "suitor": 170.9,         # 170.88 MB over 999,792 splats (suitor_patches1m.md)
+    "knn_k16": 42.44,        # 42.43 MB
+    "edge_cost": 480.5,      # 480.37 MB
+    "slot_classify": 104.8,  # 104.76 MB
+    "slot_fill": 250.6,      # 250.57 MB
+    "merge": 335.6,          # 335.52 MB
+    "match_scan": 154.8,     # 154.81 MB, round 0
+    "suitor": 170.9,         # 170.88 MB
 }
 
 
@@ -86,7 +87,8 @@ def parse():
     ap.add_argument("--fp64-policy", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--cpu-one-thread", type=int, default=1_000_000,
+                    help="splats of the one-thread oracle timing (0: skip it)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched, serving and cost-variant measurements")
     ap.add_argument("--form-steps", type=int, default=3)
@@ -160,14 +162,38 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+REF_BUDGET_S = 150.0   # the reference arm's whole run (warm-up + timed steps)
+
+
+def workload_config(name, n0, target, ratio):
+    return f"{name}: {n0} splats -> {target} ({ratio:g})"
+
+
 def reference_arm(args, ws, rank):
-    """FP64 CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    """The FP64 CPU oracle, as it stands, on the host cores (rank 0 only).
+    Each step simplifies the largest seeded random subset of the workload
+    that keeps the whole run (warm-up and timed steps) near REF_BUDGET_S;
+    a short run (few steps) gets the whole workload."""
     if rank != 0:
         return
+    import numpy as np
+
     import oracle as O
     from paper_2603_16103_gb300 import synth
-    sample = synth.patches_cube(args.cpu_sample, seed=2, frac_degenerate=0.05,
-                                frac_duplicate=0.01)
+    full = synth.workload(args.workload)
+    rng = np.random.default_rng(7)
+    probe = full.subset(np.sort(rng.choice(full.n, min(full.n, 100_000), replace=False)))
+    t = time.perf_counter()
+    O.simplify(probe, O.target_count(probe.n, args.ratio))
+    rate = probe.n / (time.perf_counter() - t)
+    per_step = REF_BUDGET_S / max(1, args.warmup + args.steps)
+    n = int(0.8 * rate * per_step) // 10_000 * 10_000
+    if n >= full.n:
+        sample, same = full, True
+    else:
+        n = max(n, 100_000)
+        sample = full.subset(np.sort(rng.choice(full.n, n, replace=False)))
+        same = False
     target = O.target_count(sample.n, args.ratio)
     times = []
     for it in range(args.warmup + args.steps):
@@ -178,33 +204,58 @@ def reference_arm(args, ws, rank):
             times.append(dt)
     tot = sum(times)
     value = sample.n * len(times) / tot
-    desc = (f"oracle (FP64 C, OpenMP) on a {sample.n}-splat scene of the same recipe "
-            f"(64 patches, 5% degenerate, 1% duplicates) -> {args.ratio:g}")
+    if same:
+        wl = workload_config(args.workload, full.n, target, args.ratio)
+        desc = f"oracle (FP64 C, OpenMP) on the whole workload, {wl}"
+    else:
+        wl = (f"{args.workload} random subset ({sample.n} of {full.n} splats, seed 7) "
+              f"-> {target} ({args.ratio:g})")
+        desc = (f"oracle (FP64 C, OpenMP) on a seeded random subset of {sample.n} of the "
+                f"{full.n} splats, sized so that {args.warmup}+{args.steps} steps take about "
+                f"{REF_BUDGET_S:.0f} s")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"patches6m sample ({sample.n} splats) -> {args.ratio:g}",
-                   "sample_splats": sample.n},
+        "config": {"workload": wl, "sample_splats": sample.n, "same_config": same},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(),
                          "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def cpu_baseline(args):
+def cpu_baseline(args, scene):
+    """The oracle on all host cores over the whole workload, plus one thread
+    on a 1,000,000-splat random subset of it (the whole workload on one
+    thread would take several minutes)."""
+    import numpy as np
+
     import oracle as O
-    from paper_2603_16103_gb300 import synth
-    sample = synth.patches_cube(args.cpu_sample, seed=2, frac_degenerate=0.05,
-                                frac_duplicate=0.01)
-    target = O.target_count(sample.n, args.ratio)
+    cores = O.num_threads()
+    target = O.target_count(scene.n, args.ratio)
     t = time.perf_counter()
-    O.simplify(sample, target)
+    O.simplify(scene, target)
     dt = time.perf_counter() - t
-    return {"value": sample.n / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"one oracle simplify of a {sample.n}-splat scene of the same recipe "
-                      f"-> {args.ratio:g} ({dt:.1f} s)"}
+    out = {"value": scene.n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"one oracle simplify of the whole workload, "
+                     f"{workload_config(args.workload, scene.n, target, args.ratio)} "
+                     f"({dt:.1f} s on {cores} threads)"}
+    if args.cpu_one_thread > 0:
+        rng = np.random.default_rng(7)
+        n1 = min(scene.n, args.cpu_one_thread)
+        sub = scene.subset(np.sort(rng.choice(scene.n, n1, replace=False)))
+        O.set_num_threads(1)
+        try:
+            t = time.perf_counter()
+            O.simplify(sub, O.target_count(sub.n, args.ratio))
+            d1 = time.perf_counter() - t
+        finally:
+            O.set_num_threads(cores)
+        out["one_thread"] = {"value": sub.n / d1, "unit": UNIT, "cores": 1,
+                             "sample": f"seeded random subset of {sub.n} of the {scene.n} "
+                                       f"splats -> {args.ratio:g} ({d1:.1f} s)"}
+    return out
 
 
 def _timed(torch, stream, fn):
@@ -544,7 +595,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(args)
+        cpu = cpu_baseline(args, scene)
 
     if rank == 0:
         out = {
@@ -552,7 +603,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {n0} splats -> {target} ({args.ratio:g})",
+            "config": {"workload": workload_config(args.workload, n0, target, args.ratio),
                        "splats": n0, "target": target, "k": 16, "mc_samples": 1,
                        "fp64_policy": ctx.params.fp64_policy, "tuning": tuning,
                        "passes": stats["passes"], "pass_n": stats["pass_n"],

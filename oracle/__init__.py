@@ -50,6 +50,8 @@ def lib():
         if _lib is None:
             L = ctypes.CDLL(build())
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             L.orc_prefilter.restype = _i64
             L.orc_prefilter.argtypes = [_i64, _ptr, _dbl, _ptr]
             L.orc_knn_brute.restype = ctypes.c_int
@@ -118,6 +120,12 @@ def _splat_arrays(s):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(t: int) -> int:
+    """Threads of the oracle's parallel loops from now on (timing only; the
+    results do not depend on it).  Returns the count in effect."""
+    return int(lib().orc_set_num_threads(int(t)))
 
 
 def k_effective(n: int, k: int) -> int:

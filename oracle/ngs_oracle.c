@@ -9,7 +9,7 @@
  * merging), App. A (Monte Carlo estimator Eq. mc_kl_estimator and the closed
  * Gaussian I-divergence), App. B Algorithm 1 (the driver loop).
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent:
  *   - quaternion order (w,x,y,z), normalised before use;
  *   - median = lower median sorted[(n-1)/2];
  *   - ties: kNN by (d^2, index), greedy by (cost, lo, hi), NaN cost last;
@@ -45,6 +45,15 @@ int orc_num_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* Threads of the later parallel loops started from the calling thread (t > 0);
+   returns the count in effect.  Timing only: results do not depend on it. */
+int orc_set_num_threads(int t) {
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#endif
+    return orc_num_threads();
 }
 
 /* softplus(x) = log(1 + e^x), written to avoid overflow. */

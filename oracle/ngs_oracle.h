@@ -23,6 +23,7 @@ extern "C" {
 #endif
 
 int orc_num_threads(void);
+int orc_set_num_threads(int t);
 
 /* Algorithm 1, opacity pre-filter: tau' = min(tau, lower median alpha); keep
  * alpha >= tau'.  keep[i] is set to 0/1; returns the kept count. */

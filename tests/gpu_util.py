@@ -94,7 +94,7 @@ def small_scene(n, seed=0, kind="unit"):
     return synth.patches_cube(n, seed=seed, frac_degenerate=0.05, frac_duplicate=0.01)
 
 
-COST_RTOL = 2e-5     # |C_gpu - C_fp64| <= COST_RTOL * (1 + |C|), see design notes
+COST_RTOL = 2e-5     # |C_gpu - C_fp64| <= COST_RTOL * (1 + |C|)
 ATTR_RTOL = 1e-5     # merged attributes vs FP64
 
 
