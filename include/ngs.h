@@ -290,6 +290,10 @@ int64_t ngs_workspace_bytes(ngs_ctx *ctx);
  * next call grows it again).  Invalidates the graph of ngs_build_graph.
  * Synchronises the ctx stream.  Errors: CUDA. */
 int ngs_release_workspace(ngs_ctx *ctx);
+/* Bytes in use and reserved in the library's private memory pool on `device`
+ * (the pool every ctx's workspace comes from; both 0 before its first use).
+ * Errors: INVALID_ARG, CUDA. */
+int ngs_pool_usage(int device, int64_t *used_bytes, int64_t *reserved_bytes);
 /* Move the ctx to another CUDA stream (NULL = legacy default stream) after
  * the work queued on its current stream has finished.  Errors: CUDA. */
 int ngs_set_stream(ngs_ctx *ctx, void *stream);

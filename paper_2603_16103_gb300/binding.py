@@ -151,6 +151,8 @@ _SIGS = {
     "ngs_knn_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
     "ngs_workspace_bytes": (ctypes.c_int64, [_P]),
     "ngs_release_workspace": (ctypes.c_int, [_P]),
+    "ngs_pool_usage": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64)]),
     "ngs_set_stream": (ctypes.c_int, [_P, _P]),
     "ngs_default_tuning": (None, [ctypes.POINTER(ngs_tuning)]),
     "ngs_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ngs_tuning)]),

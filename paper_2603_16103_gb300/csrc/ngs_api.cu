@@ -63,6 +63,8 @@ static cudaMemPool_t pool_of(int dev) {
 
 void *ws_get(ngs_ctx *c, DevBuf &b, size_t bytes) {
     if (bytes <= b.bytes) return b.p;
+    if (c->ws_fixed)
+        NGS_FAIL(NGS_ERR_STATE, "fixed workspace: %zu bytes needed, %zu bound", bytes, b.bytes);
     if (b.p) {
         NGS_CHECK_CUDA(cudaFreeAsync(b.p, c->st));  // after the queued work that used it
         c->ws_bytes -= (int64_t)b.bytes;
@@ -81,6 +83,30 @@ void *ws_get(ngs_ctx *c, DevBuf &b, size_t bytes) {
     b.bytes = want;
     c->ws_bytes += (int64_t)want;
     return p;
+}
+
+extern "C" int ngs_pool_usage(int device, int64_t *used_bytes, int64_t *reserved_bytes) {
+    if (device < 0 || device >= 64 || !used_bytes || !reserved_bytes) {
+        ngs_set_error("ngs_pool_usage: bad device index or NULL output");
+        return NGS_ERR_INVALID_ARG;
+    }
+    cudaMemPool_t p;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        p = g_pool[device];
+    }
+    *used_bytes = *reserved_bytes = 0;
+    if (!p) return NGS_OK;
+    uint64_t u = 0, r = 0;
+    cudaError_t e = cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &u);
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &r);
+    if (e != cudaSuccess) {
+        ngs_set_error("ngs_pool_usage: %s", cudaGetErrorString(e));
+        return NGS_ERR_CUDA;
+    }
+    *used_bytes = (int64_t)u;
+    *reserved_bytes = (int64_t)r;
+    return NGS_OK;
 }
 
 static void ws_free(ngs_ctx *c, DevBuf &b) {

@@ -16,6 +16,10 @@
 // by the caller.  The array's device address is looked up with
 // cudaGetSymbolAddress on the first call on each device (with that device
 // current); that first call should therefore come before any stream capture.
+// The address is looked up again when the device's context has changed since
+// (after cudaDeviceReset the array is loaded anew, at another address).
+#include <cuda.h>
+
 #include <mutex>
 
 #include "ngs_internal.h"
@@ -46,6 +50,26 @@ __device__ __align__(256) unsigned char g_knn_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_dev[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// The current driver context, fetched through the runtime's driver entry
+// point (no link-time dependency on libcuda); nullptr if unavailable.
+CUcontext current_context() {
+    using CtxGetCurrent = CUresult (*)(CUcontext *);
+    static CtxGetCurrent fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return (CtxGetCurrent)f;
+    }();
+    CUcontext cx = nullptr;
+    if (fn && fn(&cx) != CUDA_SUCCESS) cx = nullptr;
+    return cx;
+}
 
 void bind(DevBuf &b, unsigned char *&cur, size_t bytes) {
     b.p = cur;
@@ -77,10 +101,18 @@ extern "C" int ngs_knn_noalloc(const float *xyz, int64_t n, int32_t k, int32_t *
         ngs_set_error("ngs_knn_noalloc: no usable current device (%s)", cudaGetErrorString(e));
         return NGS_ERR_CUDA;
     }
+    // the table level must fit the fixed cell-table slice
+    if (knn_table_level(n, Tuning{}.cells_per_point) > kTableLevel) {
+        ngs_set_error("ngs_knn_noalloc: cell table for n=%lld exceeds the fixed slice",
+                      (long long)n);
+        return NGS_ERR_INVALID_ARG;
+    }
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_dev[dev]) {
+        // set-up once per device (and again if the device's context changed)
+        const CUcontext cx = current_context();
+        if (!g_scratch_dev[dev] || cx != g_scratch_ctx[dev]) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_knn_scratch);
             if (e != cudaSuccess || !p) {
@@ -89,10 +121,12 @@ extern "C" int ngs_knn_noalloc(const float *xyz, int64_t n, int32_t k, int32_t *
                 return NGS_ERR_CUDA;
             }
             g_scratch_dev[dev] = p;
+            g_scratch_ctx[dev] = current_context();
         }
         base = g_scratch_dev[dev];
     }
     ngs_ctx c;  // stack context: no workspace ever grows beyond the bound slices
+    c.ws_fixed = true;  // a slice too small fails the call instead of allocating
     ngs_default_params(&c.prm);
     c.prm.k = k;
     c.st = (cudaStream_t)stream;
