@@ -607,6 +607,10 @@ def main():
                        "splats": n0, "target": target, "k": 16, "mc_samples": 1,
                        "fp64_policy": ctx.params.fp64_policy, "tuning": tuning,
                        "passes": stats["passes"], "pass_n": stats["pass_n"],
+                       "pass_edges": stats["pass_edges"],
+                       "cost_tol": ctx.params.cost_tol,
+                       "fp64_cost_edges": stats["fp64_cost_edges"],
+                       "near_tie_slots": stats["near_tie_slots"],
                        "l2": "inputs (1.42 GB) larger than L2, restored from a pristine "
                              "device copy before every step",
                        "parallelism": f"replicas x{ws}"},

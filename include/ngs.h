@@ -92,6 +92,14 @@ typedef struct {
  *               ill-conditioned merged covariances
  *   prefilter   1: ngs_simplify first applies the opacity pre-filter
  *   eig_floor   lower bound on merged covariance eigenvalues (default 1e-30)
+ *   cost_tol    accuracy contract of the edge costs (default 3e-5; 0 turns
+ *               it off): an FP32 cost is kept only when twice its running
+ *               rounding-error estimate is within cost_tol max(|C|, 1), else
+ *               the edge is evaluated in FP64; then any two adjacent edges
+ *               whose costs lie within cost_tol (max(|C_e|,1) + max(|C_f|,1))
+ *               of each other are both recomputed in FP64 (rounded once to
+ *               FP32), so every decision of the greedy rule (Sec. 3.4)
+ *               follows the FP64 costs up to one FP32 rounding
  */
 typedef struct {
     int32_t  k;
@@ -105,6 +113,7 @@ typedef struct {
     int32_t  fp64_policy;
     int32_t  prefilter;
     double   eig_floor;
+    double   cost_tol;
 } ngs_params;
 
 /* The merge graph of one pass (Sec. 3.1, Algorithm 1 KNN and
@@ -138,9 +147,12 @@ typedef struct {
     int64_t pass_n[NGS_STATS_MAX_PASSES];     /* N at the start of pass p   */
     int64_t pass_edges[NGS_STATS_MAX_PASSES]; /* |E| of pass p              */
     int64_t pass_pairs[NGS_STATS_MAX_PASSES]; /* merged pairs of pass p     */
-    int64_t fp64_cost_edges;/* edges whose cost took the FP64 path           */
+    int64_t fp64_cost_edges;/* edges sent to FP64 by their error estimate or
+                             * by a near-degenerate merged covariance       */
     int64_t eig_floor_hits; /* merged eigenvalues raised to eig_floor        */
     int64_t gpu_launches;   /* kernels the library launched for this call    */
+    int64_t near_tie_slots; /* list slots recomputed in FP64 as near ties
+                             * (a mutual edge may count twice)             */
 } ngs_stats;
 
 /* ---- lifecycle ---- */

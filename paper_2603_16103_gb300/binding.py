@@ -50,7 +50,7 @@ class ngs_params(ctypes.Structure):
                 ("lambda_geo", ctypes.c_float), ("lambda_app", ctypes.c_float),
                 ("seed", ctypes.c_uint64), ("max_passes", ctypes.c_int32),
                 ("fp64_policy", ctypes.c_int32), ("prefilter", ctypes.c_int32),
-                ("eig_floor", ctypes.c_double)]
+                ("eig_floor", ctypes.c_double), ("cost_tol", ctypes.c_double)]
 
 
 class ngs_graph(ctypes.Structure):
@@ -67,7 +67,7 @@ class ngs_stats(ctypes.Structure):
                 ("pass_edges", ctypes.c_int64 * NGS_STATS_MAX_PASSES),
                 ("pass_pairs", ctypes.c_int64 * NGS_STATS_MAX_PASSES),
                 ("fp64_cost_edges", ctypes.c_int64), ("eig_floor_hits", ctypes.c_int64),
-                ("gpu_launches", ctypes.c_int64)]
+                ("gpu_launches", ctypes.c_int64), ("near_tie_slots", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         p = self.passes
@@ -77,7 +77,8 @@ class ngs_stats(ctypes.Structure):
                 "pass_n": list(self.pass_n[:p]), "pass_edges": list(self.pass_edges[:p]),
                 "pass_pairs": list(self.pass_pairs[:p]),
                 "fp64_cost_edges": self.fp64_cost_edges,
-                "eig_floor_hits": self.eig_floor_hits, "gpu_launches": self.gpu_launches}
+                "eig_floor_hits": self.eig_floor_hits, "gpu_launches": self.gpu_launches,
+                "near_tie_slots": self.near_tie_slots}
 
 
 class ngs_tuning(ctypes.Structure):

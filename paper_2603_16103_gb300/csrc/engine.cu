@@ -648,7 +648,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     };
 
     int pass = 0;
-    int64_t fp64_total = 0;
+    int64_t fp64_total = 0, tie_total = 0;
     while (pass < c->prm.max_passes) {
         extract(false);
         if (A.n <= 0) break;
@@ -762,6 +762,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
             apply_cap(c, g, sidA, thr, capped ? 1 : 0, partner);
         }
         fp64_total += (int64_t)c->h_pin[1];
+        tie_total += (int64_t)c->h_pin[5];
         if (st && pass < NGS_STATS_MAX_PASSES) {
             st->pass_n[pass] = nA;
             st->pass_edges[pass] = g.n_edges;
@@ -804,6 +805,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         st->n_output = tot;
         st->passes = pass;
         st->fp64_cost_edges = fp64_total;
+        st->near_tie_slots = tie_total;
         st->eig_floor_hits = c->floor_hits;
         st->gpu_launches = c->launches - launches0;
     }

@@ -19,6 +19,18 @@
 // (the Sec. 4 ablation), evaluated in FP32 with no FP64 path.
 // A merged covariance whose FP32 Cholesky pivots fall below 1e-2 of the
 // matching diagonal entries (near-degenerate) is redone entirely in FP64.
+//
+// Accuracy contract (cost_tol = tau_c > 0): the FP32 kernel carries a
+// first-order running estimate E of its own rounding error (each Mahalanobis
+// term, log-determinant, log-sum-exp and sum, weighted by how much it enters
+// the result) and sends an edge to the FP64 path when 2 E exceeds
+// tau_c max(|C|, 1); every cost it keeps is then within tau_c max(|C|, 1) of
+// the FP64 value.  After the costs, each vertex compares the costs of its
+// adjacent edges: two whose costs lie within tau_c (max(|C_e|,1) +
+// max(|C_f|,1)) of each other are both recomputed in FP64 (D_geo and D_app)
+// and stored rounded to FP32.  Every comparison the greedy rule of Sec. 3.4
+// makes is between adjacent edges, so the pair set then follows the FP64
+// costs except where two FP64 costs round to the same FP32 value.
 #include "ngs_device.cuh"
 #include "ngs_internal.h"
 
@@ -78,6 +90,18 @@ __device__ __forceinline__ float lse2(float a, float b) {
     float m = fmaxf(a, b);
     return m + log1pf(__expf(-fabsf(a - b)));
 }
+// the same value, and wa = the weight of a in it (exp(a - lse))
+__device__ __forceinline__ float lse2w(float a, float b, float &wa) {
+    const float m = fmaxf(a, b);
+    const float e = __expf(-fabsf(a - b));
+    const float ws = __fdividef(e, 1.0f + e);  // weight of the smaller argument
+    wa = a >= b ? 1.0f - ws : ws;
+    return m + log1pf(e);
+}
+__device__ __forceinline__ float absmax3(const float *v) {
+    return fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fabsf(v[2]));
+}
+constexpr float U32 = 5.9604645e-8f;  // unit roundoff of FP32, 2^-24
 
 // |diag(inv_s) R^T v|^2
 __device__ __forceinline__ float maha_splat(const float *R, const float *invs, const float *v) {
@@ -217,6 +241,24 @@ __device__ __noinline__ double dgeo_fp64(const float *xyz, const float *ls, cons
     return acc / S;
 }
 
+// D_app = sum over the F coefficients of (f_i - f_j)^2 in FP64
+__device__ double dapp_fp64(const float *sh, int F, int64_t i, int64_t j) {
+    double a = 0;
+    for (int t = 0; t < F; t++) {
+        const double d = (double)sh[i * F + t] - (double)sh[j * F + t];
+        a += d * d;
+    }
+    return a;
+}
+
+// the whole cost in FP64, rounded once to FP32 (i = lower canonical id)
+__device__ float cost_fp64(const float *xyz, const float *ls, const float *rot, const float *logit,
+                           const float *sh, int F, int64_t i, int64_t j, int S,
+                           const float *zs, const float *us, int mode, float lg, float la) {
+    const double dg = dgeo_fp64(xyz, ls, rot, logit, i, j, S, zs, us, mode);
+    return (float)((double)lg * dg + (double)la * dapp_fp64(sh, F, i, j));
+}
+
 // ---------------------------------------------------------------- edge kernel
 // Record layout in float4 groups: G0 = (mu, log w), G1..G3 = R (row-major)
 // then inv_s in G3.yzw.
@@ -248,7 +290,7 @@ __global__ void __launch_bounds__(256, 4)
                 const float *__restrict__ ls, const float *__restrict__ rot,
                 const float *__restrict__ logit, float *__restrict__ cost_slot,
                 float *__restrict__ cost_out, unsigned long long *fp64_count,
-                int2 *__restrict__ fp64_list) {
+                int32_t *__restrict__ fp64_list, float tol) {
     const int lane = threadIdx.x & 31;
     const int F4 = F >> 2;
     const float4 *sh4 = (const float4 *)sh;
@@ -398,12 +440,25 @@ __global__ void __launch_bounds__(256, 4)
                              fmaxf(fmaxf(invs_j[0], invs_j[1]), invs_j[2]);
             flag = flag || ri < 1e-3f || rj < 1e-3f;
         }
-        float dgeo;
+        float dgeo, eg = 0.f;  // eg: running error estimate of dgeo (times S)
+        bool tie = false;      // mode 1: u_s within FP32 reach of pi
         if (!flag) {
             // a_c = log sqrt(det Sm / det Sigma_c) as a product of O(1) ratios
             const float ai = logf((L[0] * invs_i[0]) * (L[2] * invs_i[1]) * (L[5] * invs_i[2]));
             const float aj = logf((L[0] * invs_j[0]) * (L[2] * invs_j[1]) * (L[5] * invs_j[2]));
             const float ci = lpi + ai, cj = lpj + aj;
+            // error scales of the estimate: log-determinant (Cholesky pivot
+            // ratios Sm_kk / L_kk^2), the c terms, log w, the inverse scales
+            const float r1 = Sm[3] * il[1] * il[1], r2 = Sm[5] * il[2] * il[2];
+            const float rmax = fmaxf(1.f, fmaxf(r1, r2));
+            const float e_a = U32 * (12.f + 4.f * (r1 + r2));
+            const float e_ci = e_a + U32 * (fabsf(lpi) + fabsf(ai));
+            const float e_cj = e_a + U32 * (fabsf(lpj) + fabsf(aj));
+            const float e_ld = 2.f * U32 * (fabsf(i0.w) + fabsf(j0.w));
+            const float dm = absmax3(d);
+            const float imx_i = fmaxf(fmaxf(invs_i[0], invs_i[1]), invs_i[2]);
+            const float imx_j = fmaxf(fmaxf(invs_j[0], invs_j[1]), invs_j[2]);
+            const float ilmx = fmaxf(fmaxf(il[0], il[1]), il[2]);
             float acc = 0.f;
             for (int s = 0; s < S; s++) {
                 const float z[3] = {zs[3 * s], zs[3 * s + 1], zs[3 * s + 2]};
@@ -415,19 +470,54 @@ __global__ void __launch_bounds__(256, 4)
                 float v1[3] = {d[0] + yi[0], d[1] + yi[1], d[2] + yi[2]};
                 float v2[3] = {pj * d[0] + yi[0], pj * d[1] + yi[1], pj * d[2] + yi[2]};
                 const float qj = maha_splat(Rn, invs_j, v1);
-                const float gi = lse2(ci - 0.5f * zz, cj - 0.5f * qj) +
-                                 (MODE == 2 ? 1.5f : 0.5f * maha_chol(L, il, v2));
+                const float qmi = MODE == 2 ? 0.f : maha_chol(L, il, v2);
+                const float A1 = ci - 0.5f * zz, B1 = cj - 0.5f * qj;
+                float wa1;
+                const float l1 = lse2w(A1, B1, wa1);
+                const float gi = l1 + (MODE == 2 ? 1.5f : 0.5f * qmi);
                 // x = x_j
                 float w1[3] = {yj[0] - d[0], yj[1] - d[1], yj[2] - d[2]};
                 float w2[3] = {yj[0] - pi * d[0], yj[1] - pi * d[1], yj[2] - pi * d[2]};
                 const float qi = maha_splat(Rm, invs_i, w1);
-                const float gj = lse2(ci - 0.5f * qi, cj - 0.5f * zz) +
-                                 (MODE == 2 ? 1.5f : 0.5f * maha_chol(L, il, w2));
+                const float qmj = MODE == 2 ? 0.f : maha_chol(L, il, w2);
+                const float A2 = ci - 0.5f * qi, B2 = cj - 0.5f * zz;
+                float wa2;
+                const float l2 = lse2w(A2, B2, wa2);
+                const float gj = l2 + (MODE == 2 ? 1.5f : 0.5f * qmj);
                 acc += MODE != 1 ? (pi * gi + pj * gj) : (us[s] < pi ? gi : gj);
+                if (tol > 0.f) {
+                    // first-order rounding error of each Mahalanobis term:
+                    // offsets of size |d| + |y| through 1/s (or 1/L), and q itself
+                    const float vi = dm + absmax3(yi), vj = dm + absmax3(yj);
+                    const float e_qj = 8.f * U32 * sqrtf(qj) * vi * imx_j + 2.f * U32 * qj;
+                    const float e_qi = 8.f * U32 * sqrtf(qi) * vj * imx_i + 2.f * U32 * qi;
+                    const float e_qmi = MODE == 2 ? 0.f : 8.f * U32 * sqrtf(qmi) * vi * ilmx + 4.f * U32 * rmax * qmi;
+                    const float e_qmj = MODE == 2 ? 0.f : 8.f * U32 * sqrtf(qmj) * vj * ilmx + 4.f * U32 * rmax * qmj;
+                    // ... entering each log-sum-exp by its weight
+                    const float wb1 = 1.f - wa1, wb2 = 1.f - wa2;
+                    const float e_gi = wa1 * e_ci + wb1 * (e_cj + 0.5f * e_qj) + 0.5f * e_qmi +
+                                       U32 * (wa1 * fabsf(A1) + wb1 * fabsf(B1) + fabsf(l1) + qmi);
+                    const float e_gj = wa2 * (e_ci + 0.5f * e_qi) + wb2 * e_cj + 0.5f * e_qmj +
+                                       U32 * (wa2 * fabsf(A2) + wb2 * fabsf(B2) + fabsf(l2) + qmj);
+                    if (MODE != 1) {
+                        eg += pi * e_gi + pj * e_gj + ppd * e_ld * (fabsf(gi) + fabsf(gj) + 2.f) +
+                              U32 * (pi * fabsf(gi) + pj * fabsf(gj));
+                    } else {
+                        eg += us[s] < pi ? e_gi + U32 * fabsf(gi) : e_gj + U32 * fabsf(gj);
+                        tie = tie || fabsf(us[s] - pi) <= 1e-5f;
+                    }
+                }
             }
             dgeo = acc / (float)S;
         } else {
             dgeo = 0.f;  // evaluated in FP64 by k_edge_cost64 from the list below
+        }
+        const float c = lg * dgeo + la * dapp;
+        if (tol > 0.f && !flag) {
+            // keep the FP32 cost only when twice its error estimate is within
+            // tol max(|C|, 1); D_app: F/4 + 4 roundings per lane sum, 16 in all
+            const float E = lg * (eg / (float)S) + la * 16.f * U32 * dapp + U32 * fabsf(c);
+            flag = tie || !(2.f * E <= tol * fmaxf(fabsf(c), 1.f));
         }
         // flagged edges go to the FP64 list (one atomic per warp)
         const unsigned am = __activemask();
@@ -437,35 +527,144 @@ __global__ void __launch_bounds__(256, 4)
             unsigned long long at = 0;
             if (lane == first) at = atomicAdd(fp64_count, (unsigned long long)__popc(fm));
             at = __shfl_sync(am, at, first);
-            if (flag) fp64_list[at + __popc(fm & ((1u << lane) - 1u))] = make_int2((int)e, __float_as_int(dapp));
+            if (flag) fp64_list[at + __popc(fm & ((1u << lane) - 1u))] = (int32_t)e;
         }
         if (flag) continue;
-        const float c = lg * dgeo + la * dapp;
         cost_slot[sl] = c;
         if (er.w >= 0) cost_slot[er.w] = c;
         if (cost_out) cost_out[e] = c;
     }
 }
 
-// FP64 evaluation of the flagged edges: D_geo in FP64, D_app as computed in
-// FP32 by the main kernel.
-__global__ void k_edge_cost64(const int2 *__restrict__ list, const unsigned long long *__restrict__ count,
+// FP64 evaluation of the flagged edges: D_geo and D_app in FP64, the cost
+// rounded once to FP32.
+__global__ void k_edge_cost64(const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
                               const int4 *__restrict__ erec, const float *__restrict__ zs,
                               const float *__restrict__ us, int S, int mode, float lg, float la,
                               const float *__restrict__ xyz, const float *__restrict__ ls,
                               const float *__restrict__ rot, const float *__restrict__ logit,
+                              const float *__restrict__ sh, int F,
                               float *__restrict__ cost_slot, float *__restrict__ cost_out) {
     const int64_t cnt = (int64_t)*count;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int2 it = list[t];
-        const int64_t e = it.x;
+        const int64_t e = list[t];
         const int4 er = erec[e];
-        const float dgeo = (float)dgeo_fp64(xyz, ls, rot, logit, er.y, er.z, S, zs, us, mode);
-        const float c = lg * dgeo + la * __int_as_float(it.y);
+        const float c = cost_fp64(xyz, ls, rot, logit, sh, F, er.y, er.z, S, zs, us, mode, lg, la);
         cost_slot[er.x] = c;
         if (er.w >= 0) cost_slot[er.w] = c;
         if (cost_out) cost_out[e] = c;
+    }
+}
+
+// ---------------------------------------------------------------- near ties
+// Two adjacent edges whose costs are within the accuracy contract of each
+// other (see the file header) are both recomputed in FP64.
+__device__ __forceinline__ bool near_tie(float a, float b, float tol) {
+    return fabsf(a - b) <= tol * (fmaxf(fabsf(a), 1.f) + fmaxf(fabsf(b), 1.f));
+}
+
+// mark slot s; a slot marked for the first time goes to the refine list
+__device__ __forceinline__ void mark_slot(uint32_t *bits, int32_t s, int32_t *list,
+                                          unsigned long long *cnt) {
+    const uint32_t bit = 1u << (s & 31);
+    const uint32_t old = atomicOr(bits + (s >> 5), bit);
+    if (!(old & bit)) list[atomicAdd(cnt, 1ull)] = s;
+}
+
+// One thread per vertex v: the costs of its K slots (16-byte loads when K is
+// a multiple of 4; K = 0 for any width up to NGS_MAX_K) and of its in-slots
+// (non-mutual edges of other vertices that point at v) are compared pairwise.
+template <int K>
+__global__ void k_near_ties(int64_t n, int kk, const float *__restrict__ cost_slot,
+                            const int32_t *__restrict__ rev_ptr, const int32_t *__restrict__ rev,
+                            float tol, uint32_t *bits, int32_t *list, unsigned long long *cnt) {
+    constexpr int KM = K > 0 ? K : NGS_MAX_K;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t base = v * kk;
+        float c[KM];
+        if (K > 0) {
+            const float4 *c4 = (const float4 *)(cost_slot + base);
+#pragma unroll
+            for (int t = 0; t < KM / 4; t++) {
+                const float4 x = __ldg(c4 + t);
+                c[4 * t] = x.x; c[4 * t + 1] = x.y; c[4 * t + 2] = x.z; c[4 * t + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < KM; t++) c[t] = t < kk ? cost_slot[base + t] : NAN;
+        }
+        uint32_t own = 0;  // own slots to mark
+#pragma unroll
+        for (int a = 0; a < KM; a++)
+#pragma unroll
+            for (int b = a + 1; b < KM; b++)
+                if (near_tie(c[a], c[b], tol)) own |= (1u << a) | (1u << b);
+        const int32_t r0 = rev_ptr[v], r1 = rev_ptr[v + 1];
+        for (int32_t r = r0; r < r1; r++) {
+            const int32_t sr = __ldg(rev + r);
+            const float cr = __ldg(cost_slot + sr);
+            bool hit = false;
+#pragma unroll
+            for (int a = 0; a < KM; a++)
+                if (near_tie(c[a], cr, tol)) {
+                    own |= 1u << a;
+                    hit = true;
+                }
+            for (int32_t r2 = r + 1; r2 < r1; r2++) {
+                const int32_t s2 = __ldg(rev + r2);
+                if (near_tie(cr, __ldg(cost_slot + s2), tol)) {
+                    hit = true;
+                    mark_slot(bits, s2, list, cnt);
+                }
+            }
+            if (hit) mark_slot(bits, sr, list, cnt);
+        }
+        while (own) {
+            const int a = __ffs(own) - 1;
+            own &= own - 1;
+            mark_slot(bits, (int32_t)(base + a), list, cnt);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t cid_at(const int32_t *cid, int64_t v) {
+    return cid ? (uint32_t)cid[v] : (uint32_t)v;
+}
+
+// FP64 cost of the edge of each listed slot, into both slots of a mutual
+// edge and, for the C-ABI view, into its lexicographic position.
+__global__ void k_refine_costs(const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
+                               int kk, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cid,
+                               const float *__restrict__ zs, const float *__restrict__ us, int S,
+                               int mode, float lg, float la, const float *__restrict__ xyz,
+                               const float *__restrict__ ls, const float *__restrict__ rot,
+                               const float *__restrict__ logit, const float *__restrict__ sh, int F,
+                               float *cost_slot, const int32_t *__restrict__ elo,
+                               const int32_t *__restrict__ ehi, int64_t m, float *cost_out) {
+    const int64_t cnt = (int64_t)*count;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = list[t];
+        const int64_t a = s / kk, b = nbr[s];
+        const uint32_t ca = cid_at(cid, a), cb = cid_at(cid, b);
+        const int64_t lo = ca < cb ? a : b, hi = ca < cb ? b : a;
+        const float c = cost_fp64(xyz, ls, rot, logit, sh, F, lo, hi, S, zs, us, mode, lg, la);
+        cost_slot[s] = c;
+        for (int q = 0; q < kk; q++)  // the mirror slot of a mutual edge
+            if (nbr[b * kk + q] == (int32_t)a) cost_slot[b * kk + q] = c;
+        if (cost_out) {
+            // lexicographic position of (lo, hi) in canonical ids
+            const uint64_t key = ((uint64_t)(ca < cb ? ca : cb) << 32) | (ca < cb ? cb : ca);
+            int64_t x = 0, y = m;
+            while (x < y) {
+                const int64_t mid = (x + y) >> 1;
+                const uint64_t km = ((uint64_t)(uint32_t)elo[mid] << 32) | (uint32_t)ehi[mid];
+                if (km < key) x = mid + 1; else y = mid;
+            }
+            if (x < m) cost_out[x] = c;
+        }
     }
 }
 
@@ -486,41 +685,60 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
                 float *cost_out) {
     const int64_t m = g.n_edges;
     const int S = c->prm.mc_samples;
-    c->h_pin[1] = 0;  // FP64-path edge count of this call (filled below)
+    c->h_pin[1] = 0;  // edges sent to FP64 by their error estimate (filled below)
+    c->h_pin[5] = 0;  // slots recomputed in FP64 as near ties
     if (m <= 0) return;
     // the host buffer may go out of scope on return (put_small stages it)
     std::vector<float> h(4 * (size_t)S);
     host_mc_draws(c->prm.seed, pass, S, h.data(), h.data() + 3 * S);
     float *zs = ws<float>(c, c->b_rng, 4 * S);
     put_small(c, zs, h.data(), sizeof(float) * 4 * (size_t)S);
+    const float *us = zs + 3 * S;
     float *rec = ws<float>(c, c->b_rec, s.n * REC);
     // the edge-cost kernel reads each 64-byte record as two 32-byte loads
     if ((uintptr_t)rec & 31) NGS_FAIL(NGS_ERR_CUDA, "edge_costs: record buffer not 32-byte aligned");
     launch(c, "cost_prep", dim3(grid_stride_blocks(c, s.n, 256, 8)), dim3(256), 0, k_prep, s.xyz,
            s.ls, s.rot, s.logit, s.n, rec);
+    // [0] edges on the FP64 list, [1] slots on the near-tie list
     unsigned long long *cnt = (unsigned long long *)ws<uint8_t>(c, c->b_status, 64);
-    int2 *list = ws<int2>(c, c->b_fp64list, m);
-    NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, c->st));
+    int32_t *list = ws<int32_t>(c, c->b_fp64list, m);
+    NGS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 16, c->st));
     const int mode = c->prm.cost_mode;
+    const float tol = (float)c->prm.cost_tol;
+    const float lg = c->prm.lambda_geo, la = c->prm.lambda_app;
+    const int4 *er = lex ? g.erec_lex : g.erec;
+    float *cout = lex ? cost_out : nullptr;
     auto kern = mode == 1 ? k_edge_cost<1> : mode == 2 ? k_edge_cost<2> : mode == 3 ? k_edge_cost<3>
                                                                                     : k_edge_cost<0>;
     launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, c->tune.cost_blocks_per_sm)), dim3(256), 0,
-           kern,
-           (const int4 *)(lex ? g.erec_lex : g.erec), m, (const float *)rec, (const float *)s.sh,
-           s.F, (const float *)zs,
-           (const float *)(zs + 3 * S), S, c->prm.lambda_geo,
-           c->prm.lambda_app, c->prm.fp64_policy, (const float *)s.xyz, (const float *)s.ls,
-           (const float *)s.rot, (const float *)s.logit, g.cost_slot, lex ? cost_out : nullptr,
-           cnt, list);
-    // the flagged edges (few: near-degenerate merged covariances) in FP64; the
-    // grid covers the worst case, threads past the device count exit at once
+           kern, er, m, (const float *)rec, (const float *)s.sh, s.F, (const float *)zs, us, S, lg,
+           la, c->prm.fp64_policy, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
+           (const float *)s.logit, g.cost_slot, cout, cnt, list, tol);
+    // the flagged edges (few) in FP64; the grid covers the worst case, threads
+    // past the device count exit at once
     launch(c, "edge_cost64", dim3(grid_stride_blocks(c, m, 128, 2)), dim3(128), 0, k_edge_cost64,
-           (const int2 *)list, (const unsigned long long *)cnt,
-           (const int4 *)(lex ? g.erec_lex : g.erec), (const float *)zs,
-           (const float *)(zs + 3 * S), S, c->prm.cost_mode, c->prm.lambda_geo,
-           c->prm.lambda_app, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
-           (const float *)s.logit, g.cost_slot, lex ? cost_out : nullptr);
+           (const int32_t *)list, (const unsigned long long *)cnt, er, (const float *)zs, us, S, mode,
+           lg, la, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
+           (const float *)s.logit, (const float *)s.sh, s.F, g.cost_slot, cout);
+    if (tol > 0.f) {
+        const int64_t ns = g.n * g.k_eff;
+        uint32_t *bits = ws<uint32_t>(c, c->b_tiebits, (ns + 31) / 32);
+        NGS_CHECK_CUDA(cudaMemsetAsync(bits, 0, 4 * ((ns + 31) / 32), c->st));
+        int32_t *tl = ws<int32_t>(c, c->b_tielist, ns);
+        const dim3 gr(grid_stride_blocks(c, g.n, 128, 16)), bl(128);
+        auto nt = g.k_eff == 4 ? k_near_ties<4> : g.k_eff == 8 ? k_near_ties<8>
+                : g.k_eff == 16 ? k_near_ties<16> : g.k_eff == 32 ? k_near_ties<32> : k_near_ties<0>;
+        launch(c, "near_ties", gr, bl, 0, nt, g.n, g.k_eff, (const float *)g.cost_slot,
+               (const int32_t *)g.rev_ptr, (const int32_t *)g.rev, tol, bits, tl, cnt + 1);
+        launch(c, "refine_costs", dim3(grid_stride_blocks(c, ns, 128, 4)), dim3(128), 0,
+               k_refine_costs, (const int32_t *)tl, (const unsigned long long *)(cnt + 1), g.k_eff,
+               g.nbr, g.cid, (const float *)zs, us, S, mode, lg, la, (const float *)s.xyz,
+               (const float *)s.ls, (const float *)s.rot, (const float *)s.logit,
+               (const float *)s.sh, s.F, g.cost_slot, lex ? (const int32_t *)g.elo : nullptr,
+               lex ? (const int32_t *)g.ehi : nullptr, m, cout);
+    }
     get_small(c, c->h_pin + 1, cnt, 8);
+    get_small(c, c->h_pin + 5, cnt + 1, 8);
 }
 
 void costs_to_slots(ngs_ctx *c, GraphDev &g, const float *cost_lex) {

@@ -213,6 +213,7 @@ extern "C" void ngs_default_params(ngs_params *p) {
     p->fp64_policy = 0;
     p->prefilter = 1;
     p->eig_floor = 1e-30;
+    p->cost_tol = 3e-5;
 }
 
 static int check_params(const ngs_params *p) {
@@ -223,6 +224,7 @@ static int check_params(const ngs_params *p) {
     if (p->max_passes < 0 || p->max_passes > NGS_STATS_MAX_PASSES) return 0;
     if (p->fp64_policy < 0 || p->fp64_policy > 2) return 0;
     if (!(p->eig_floor > 0.0)) return 0;
+    if (!(p->cost_tol >= 0.0 && p->cost_tol < 1.0)) return 0;
     return 1;
 }
 
@@ -265,7 +267,8 @@ static void release_all(ngs_ctx *c) {
                       &c->b_cand, &c->b_candkey, &c->b_counts, &c->b_sel, &c->b_role, &c->b_keep,
                       &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
                       &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2,
-                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc, &c->b_fp64list, &c->b_mstate, &c->b_offer, &c->b_order0};
+                      &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc, &c->b_fp64list, &c->b_mstate, &c->b_offer, &c->b_order0,
+                      &c->b_tiebits, &c->b_tielist};
     for (DevBuf *b : bufs) ws_free(c, *b);
     for (int k = 0; k < 5; k++) {
         ws_free(c, c->b_sA[k]);
@@ -554,6 +557,7 @@ extern "C" int ngs_batch_simplify(ngs_ctx *c, ngs_splats *scenes, const int64_t 
         acc.passes = acc.passes > x.passes ? acc.passes : x.passes;
         acc.matching_rounds += x.matching_rounds;
         acc.fp64_cost_edges += x.fp64_cost_edges;
+        acc.near_tie_slots += x.near_tie_slots;
         acc.eig_floor_hits += x.eig_floor_hits;
     };
     for (int s = 0; s < nscenes; s++) {

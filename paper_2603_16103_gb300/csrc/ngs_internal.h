@@ -124,6 +124,7 @@ struct ngs_ctx {
     DevBuf b_host_dev[5];        // device staging for ngs_simplify_host
     DevBuf b_sC[5];              // third splat array set (several scenes at once)
     DevBuf b_fp64list;           // edges whose cost is evaluated in FP64
+    DevBuf b_tiebits, b_tielist; // near-tie slot marks and the slots to recompute in FP64
     DevBuf b_mstate;             // device-side state of the captured matching rounds
     DevBuf b_offer;              // best offer per vertex (proposal form of the matching)
     DevBuf b_eng[32];            // per-scene tables and scratch of the multi-scene engine
@@ -150,6 +151,7 @@ struct ngs_ctx {
 
     // per-call counters
     int64_t fp64_edges = 0;
+    int64_t tie_slots = 0;
     int64_t floor_hits = 0;
     int32_t rounds = 0;
 };

@@ -94,8 +94,16 @@ def small_scene(n, seed=0, kind="unit"):
     return synth.patches_cube(n, seed=seed, frac_degenerate=0.05, frac_duplicate=0.01)
 
 
-COST_RTOL = 2e-5     # |C_gpu - C_fp64| <= COST_RTOL * (1 + |C|)
+COST_TOL = 3e-5      # |C_gpu - C_fp64| <= COST_TOL * max(|C|, 1) for every edge
 ATTR_RTOL = 1e-5     # merged attributes vs FP64
+
+
+def cost_excess(cost, ref, tol=None):
+    """Largest |C_gpu - C_fp64| / max(|C_fp64|, 1) over all edges, divided by
+    the accuracy contract (<= 1 passes)."""
+    tol = COST_TOL if tol is None else tol
+    err = np.abs(np.asarray(cost, np.float64) - ref) / np.maximum(np.abs(ref), 1.0)
+    return float(err.max() / tol) if len(err) else 0.0
 
 
 def stepwise(ngs, ctx, scene, target, max_passes=64):
