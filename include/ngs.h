@@ -93,7 +93,7 @@ typedef struct {
  *   prefilter   1: ngs_simplify first applies the opacity pre-filter
  *   eig_floor   lower bound on merged covariance eigenvalues (default 1e-30)
  *   cost_tol    accuracy contract of the edge costs (default 3e-5; 0 turns
- *               it off): an FP32 cost is kept only when twice its running
+ *               it off; at most 1e-4): an FP32 cost is kept only when twice its running
  *               rounding-error estimate is within cost_tol max(|C|, 1), else
  *               the edge is evaluated in FP64; then any two adjacent edges
  *               whose costs lie within cost_tol (max(|C_e|,1) + max(|C_f|,1))

@@ -98,6 +98,8 @@ __device__ __forceinline__ float lse2w(float a, float b, float &wa) {
     wa = a >= b ? 1.0f - ws : ws;
     return m + log1pf(e);
 }
+// square root of q >= 0 for the error estimate (approximate; 0 at 0)
+__device__ __forceinline__ float sqrt_nn(float q) { return q * rsqrtf(fmaxf(q, 1e-30f)); }
 __device__ __forceinline__ float absmax3(const float *v) {
     return fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fabsf(v[2]));
 }
@@ -182,9 +184,12 @@ __device__ __noinline__ double dgeo_fp64(const float *xyz, const float *ls, cons
         }
         return r;
     }
-    double ld = gi.lw - gj.lw;
-    double lpi = -softplus_d(-ld), lpj = -softplus_d(ld);
-    double pi = exp(lpi), pj = exp(lpj);
+    // pi = sigmoid(ld) and its complement share t = e^{-|ld|}
+    const double ld = gi.lw - gj.lw;
+    const double t = exp(-fabs(ld)), l1t = log1p(t);
+    const double lpi = -(fmax(-ld, 0.0) + l1t), lpj = -(fmax(ld, 0.0) + l1t);
+    const double big = 1.0 / (1.0 + t), small = t * big;
+    const double pi = ld >= 0 ? big : small, pj = ld >= 0 ? small : big;
     double d[3] = {gi.mu[0] - gj.mu[0], gi.mu[1] - gj.mu[1], gi.mu[2] - gj.mu[2]};
     double Sm[6];
     int idx = 0;
@@ -200,7 +205,7 @@ __device__ __noinline__ double dgeo_fp64(const float *xyz, const float *ls, cons
     double t22 = Sm[5] - l20 * l20 - l21 * l21;
     if (!(t22 > 0)) return INFINITY;
     double l22 = sqrt(t22);
-    double half_ldm = log(l00) + log(l11) + log(l22);
+    double half_ldm = 0.5 * log(Sm[0] * t11 * t22);  // log(l00 l11 l22)
     double ai = half_ldm - gi.sum_ls, aj = half_ldm - gj.sum_ls;
     double acc = 0;
     for (int s = 0; s < S; s++) {
@@ -282,7 +287,7 @@ __device__ __forceinline__ void ldg_v8(const float *p, float *r) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
     k_edge_cost(const int4 *__restrict__ erec, int64_t m, const float *__restrict__ rec,
                 const float *__restrict__ sh, int F,
                 const float *__restrict__ zs, const float *__restrict__ us, int S,
@@ -451,54 +456,66 @@ __global__ void __launch_bounds__(256, 4)
             // ratios Sm_kk / L_kk^2), the c terms, log w, the inverse scales
             const float r1 = Sm[3] * il[1] * il[1], r2 = Sm[5] * il[2] * il[2];
             const float rmax = fmaxf(1.f, fmaxf(r1, r2));
-            const float e_a = U32 * (12.f + 4.f * (r1 + r2));
-            const float e_ci = e_a + U32 * (fabsf(lpi) + fabsf(ai));
-            const float e_cj = e_a + U32 * (fabsf(lpj) + fabsf(aj));
+            // (one bound for both c terms)
+            const float e_c = U32 * (12.f + 4.f * (r1 + r2) + fabsf(lpi) + fabsf(ai) +
+                                     fabsf(lpj) + fabsf(aj));
             const float e_ld = 2.f * U32 * (fabsf(i0.w) + fabsf(j0.w));
             const float dm = absmax3(d);
             const float imx_i = fmaxf(fmaxf(invs_i[0], invs_i[1]), invs_i[2]);
             const float imx_j = fmaxf(fmaxf(invs_j[0], invs_j[1]), invs_j[2]);
             const float ilmx = fmaxf(fmaxf(il[0], il[1]), il[2]);
             float acc = 0.f;
+            const bool est = tol > 0.f;
             for (int s = 0; s < S; s++) {
                 const float z[3] = {zs[3 * s], zs[3 * s + 1], zs[3 * s + 2]};
                 const float zz = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
-                float yi[3], yj[3];
-                sym_sqrt_apply(Rm, si, z, yi);
-                sym_sqrt_apply(Rn, sj, z, yj);
-                // x = x_i
-                float v1[3] = {d[0] + yi[0], d[1] + yi[1], d[2] + yi[2]};
-                float v2[3] = {pj * d[0] + yi[0], pj * d[1] + yi[1], pj * d[2] + yi[2]};
-                const float qj = maha_splat(Rn, invs_j, v1);
-                const float qmi = MODE == 2 ? 0.f : maha_chol(L, il, v2);
-                const float A1 = ci - 0.5f * zz, B1 = cj - 0.5f * qj;
-                float wa1;
-                const float l1 = lse2w(A1, B1, wa1);
-                const float gi = l1 + (MODE == 2 ? 1.5f : 0.5f * qmi);
+                // x = x_i.  Error terms are formed as soon as their inputs
+                // exist (first-order rounding of each Mahalanobis term:
+                // offsets of size |d| + |y| through 1/s or 1/L, and q itself;
+                // each entering its log-sum-exp by its weight)
+                float gi, e_gi = 0.f;
+                {
+                    float yi[3];
+                    sym_sqrt_apply(Rm, si, z, yi);
+                    const float vi = dm + absmax3(yi);
+                    float v1[3] = {d[0] + yi[0], d[1] + yi[1], d[2] + yi[2]};
+                    float v2[3] = {pj * d[0] + yi[0], pj * d[1] + yi[1], pj * d[2] + yi[2]};
+                    const float qj = maha_splat(Rn, invs_j, v1);
+                    const float qmi = MODE == 2 ? 0.f : maha_chol(L, il, v2);
+                    const float A1 = ci - 0.5f * zz, B1 = cj - 0.5f * qj;
+                    float wa1;
+                    const float l1 = lse2w(A1, B1, wa1);
+                    gi = l1 + (MODE == 2 ? 1.5f : 0.5f * qmi);
+                    if (est) {
+                        const float e_qj = 8.f * U32 * sqrt_nn(qj) * vi * imx_j + 2.f * U32 * qj;
+                        const float e_qm = MODE == 2 ? 0.f : 8.f * U32 * sqrt_nn(qmi) * vi * ilmx + 4.f * U32 * rmax * qmi;
+                        // rounding of the log-sum-exp inputs, weighted, is within
+                        // |l| + 1 (l = lse >= the larger input), its output within |l|
+                        e_gi = e_c + (1.f - wa1) * 0.5f * e_qj + 0.5f * e_qm + U32 * (2.f * fabsf(l1) + 1.f + qmi);
+                    }
+                }
                 // x = x_j
-                float w1[3] = {yj[0] - d[0], yj[1] - d[1], yj[2] - d[2]};
-                float w2[3] = {yj[0] - pi * d[0], yj[1] - pi * d[1], yj[2] - pi * d[2]};
-                const float qi = maha_splat(Rm, invs_i, w1);
-                const float qmj = MODE == 2 ? 0.f : maha_chol(L, il, w2);
-                const float A2 = ci - 0.5f * qi, B2 = cj - 0.5f * zz;
-                float wa2;
-                const float l2 = lse2w(A2, B2, wa2);
-                const float gj = l2 + (MODE == 2 ? 1.5f : 0.5f * qmj);
+                float gj, e_gj = 0.f;
+                {
+                    float yj[3];
+                    sym_sqrt_apply(Rn, sj, z, yj);
+                    const float vj = dm + absmax3(yj);
+                    float w1[3] = {yj[0] - d[0], yj[1] - d[1], yj[2] - d[2]};
+                    float w2[3] = {yj[0] - pi * d[0], yj[1] - pi * d[1], yj[2] - pi * d[2]};
+                    const float qi = maha_splat(Rm, invs_i, w1);
+                    const float qmj = MODE == 2 ? 0.f : maha_chol(L, il, w2);
+                    const float A2 = ci - 0.5f * qi, B2 = cj - 0.5f * zz;
+                    float wa2;
+                    const float l2 = lse2w(A2, B2, wa2);
+                    gj = l2 + (MODE == 2 ? 1.5f : 0.5f * qmj);
+                    if (est) {
+                        const float e_qi = 8.f * U32 * sqrt_nn(qi) * vj * imx_i + 2.f * U32 * qi;
+                        const float e_qm = MODE == 2 ? 0.f : 8.f * U32 * sqrt_nn(qmj) * vj * ilmx + 4.f * U32 * rmax * qmj;
+                        e_gj = e_c + wa2 * 0.5f * e_qi + 0.5f * e_qm + U32 * (2.f * fabsf(l2) + 1.f + qmj);
+                    }
+                }
                 acc += MODE != 1 ? (pi * gi + pj * gj) : (us[s] < pi ? gi : gj);
-                if (tol > 0.f) {
-                    // first-order rounding error of each Mahalanobis term:
-                    // offsets of size |d| + |y| through 1/s (or 1/L), and q itself
-                    const float vi = dm + absmax3(yi), vj = dm + absmax3(yj);
-                    const float e_qj = 8.f * U32 * sqrtf(qj) * vi * imx_j + 2.f * U32 * qj;
-                    const float e_qi = 8.f * U32 * sqrtf(qi) * vj * imx_i + 2.f * U32 * qi;
-                    const float e_qmi = MODE == 2 ? 0.f : 8.f * U32 * sqrtf(qmi) * vi * ilmx + 4.f * U32 * rmax * qmi;
-                    const float e_qmj = MODE == 2 ? 0.f : 8.f * U32 * sqrtf(qmj) * vj * ilmx + 4.f * U32 * rmax * qmj;
-                    // ... entering each log-sum-exp by its weight
-                    const float wb1 = 1.f - wa1, wb2 = 1.f - wa2;
-                    const float e_gi = wa1 * e_ci + wb1 * (e_cj + 0.5f * e_qj) + 0.5f * e_qmi +
-                                       U32 * (wa1 * fabsf(A1) + wb1 * fabsf(B1) + fabsf(l1) + qmi);
-                    const float e_gj = wa2 * (e_ci + 0.5f * e_qi) + wb2 * e_cj + 0.5f * e_qmj +
-                                       U32 * (wa2 * fabsf(A2) + wb2 * fabsf(B2) + fabsf(l2) + qmj);
+                if (est) {
                     if (MODE != 1) {
                         eg += pi * e_gi + pj * e_gj + ppd * e_ld * (fabsf(gi) + fabsf(gj) + 2.f) +
                               U32 * (pi * fabsf(gi) + pj * fabsf(gj));
@@ -572,54 +589,161 @@ __device__ __forceinline__ void mark_slot(uint32_t *bits, int32_t s, int32_t *li
     if (!(old & bit)) list[atomicAdd(cnt, 1ull)] = s;
 }
 
-// One thread per vertex v: the costs of its K slots (16-byte loads when K is
-// a multiple of 4; K = 0 for any width up to NGS_MAX_K) and of its in-slots
-// (non-mutual edges of other vertices that point at v) are compared pairwise.
+// Ascending sort of N register keys by a bitonic network (static indices).
+template <int N>
+__device__ __forceinline__ void sort_asc_u32(uint32_t (&a)[N]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint32_t x = a[i], y = a[l];
+                    const bool up = (i & k) == 0;
+                    a[i] = up ? min(x, y) : max(x, y);
+                    a[l] = up ? max(x, y) : min(x, y);
+                }
+            }
+}
+
+// Exact pairwise marks of one vertex (any slot width, any number of in-slots).
+template <int KM>
+__device__ __forceinline__ void near_ties_pairwise(const float (&c)[KM], int64_t base, int32_t r0,
+                                                   int32_t r1, const float *__restrict__ cost_slot,
+                                                   const int32_t *__restrict__ rev, float tol,
+                                                   uint32_t *bits, int32_t *list,
+                                                   unsigned long long *cnt) {
+    uint32_t own = 0;  // own slots to mark
+#pragma unroll
+    for (int a = 0; a < KM; a++)
+#pragma unroll
+        for (int b = a + 1; b < KM; b++)
+            if (near_tie(c[a], c[b], tol)) own |= (1u << a) | (1u << b);
+    for (int32_t r = r0; r < r1; r++) {
+        const int32_t sr = __ldg(rev + r);
+        const float cr = __ldg(cost_slot + sr);
+        bool hit = false;
+#pragma unroll
+        for (int a = 0; a < KM; a++)
+            if (near_tie(c[a], cr, tol)) {
+                own |= 1u << a;
+                hit = true;
+            }
+        for (int32_t r2 = r + 1; r2 < r1; r2++) {
+            const int32_t s2 = __ldg(rev + r2);
+            if (near_tie(cr, __ldg(cost_slot + s2), tol)) {
+                hit = true;
+                mark_slot(bits, s2, list, cnt);
+            }
+        }
+        if (hit) mark_slot(bits, sr, list, cnt);
+    }
+    while (own) {
+        const int a = __ffs(own) - 1;
+        own &= own - 1;
+        mark_slot(bits, (int32_t)(base + a), list, cnt);
+    }
+}
+
+// decoded value of a packed sort key (low bits hold a slot index)
 template <int K>
-__global__ void k_near_ties(int64_t n, int kk, const float *__restrict__ cost_slot,
-                            const int32_t *__restrict__ rev_ptr, const int32_t *__restrict__ rev,
-                            float tol, uint32_t *bits, int32_t *list, unsigned long long *cnt) {
+__device__ __forceinline__ float key_value(uint32_t k) {
+    return order_bits_float(k & ~(uint32_t)(K - 1));
+}
+
+// One thread per vertex v: the costs of its K slots and of its in-slots
+// (non-mutual edges of other vertices that point at v) are compared.
+// For K in {4, 8, 16, 32} the K own costs are sorted (slot index packed into
+// the low log2(K) bits of the orderable key, which moves a value by under K
+// ulp) and only sorted neighbours are compared, with the threshold widened
+// by 1e-3 of itself and by 2K ulp.  Sorted neighbours suffice: if two costs
+// a < c are in near tie, every cost b between them is within the same
+// distance of a and of c, and with tol <= 1e-4 all of m_a, m_b, m_c =
+// max(|.|, 1) lie within 3 tol (< 1e-3) of each other, so each consecutive pair of the
+// chain passes the widened test (marking a superset).  An in-slot cost is
+// placed into the sorted own costs (binary search over shared memory) and
+// compared with its two neighbours there, by the same chain argument; in-slot
+// pairs are compared directly.  Other K: every pair is compared.
+template <int K>
+__global__ void __launch_bounds__(128)
+    k_near_ties(int64_t n, int kk, const float *__restrict__ cost_slot,
+                const int32_t *__restrict__ rev_ptr, const int32_t *__restrict__ rev,
+                float tol, uint32_t *bits, int32_t *list, unsigned long long *cnt) {
     constexpr int KM = K > 0 ? K : NGS_MAX_K;
+    constexpr int KS = K > 0 ? K : 1;
+    constexpr uint32_t IMASK = K > 0 ? (uint32_t)K - 1u : 0u;
+    __shared__ uint32_t skey[KS][128];  // sorted own keys, one column per thread
+    const float tw = tol * 1.001f;
+    const float ulps = 2.f * KM * 1.2e-7f;
+    auto close = [&](float x, float y) {  // widened near-tie test
+        const float mx = fmaxf(fabsf(x), 1.f), my = fmaxf(fabsf(y), 1.f);
+        return fabsf(x - y) <= tw * (mx + my) + ulps * fmaxf(mx, my);
+    };
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t base = v * kk;
-        float c[KM];
-        if (K > 0) {
-            const float4 *c4 = (const float4 *)(cost_slot + base);
-#pragma unroll
-            for (int t = 0; t < KM / 4; t++) {
-                const float4 x = __ldg(c4 + t);
-                c[4 * t] = x.x; c[4 * t + 1] = x.y; c[4 * t + 2] = x.z; c[4 * t + 3] = x.w;
-            }
-        } else {
+        const int32_t r0 = rev_ptr[v], r1 = rev_ptr[v + 1];
+        if (K == 0) {
+            float c[KM];
 #pragma unroll
             for (int t = 0; t < KM; t++) c[t] = t < kk ? cost_slot[base + t] : NAN;
+            near_ties_pairwise<KM>(c, base, r0, r1, cost_slot, rev, tol, bits, list, cnt);
+            continue;
         }
-        uint32_t own = 0;  // own slots to mark
+        uint32_t key[KS];
+        {
+            const float4 *c4 = (const float4 *)(cost_slot + base);
 #pragma unroll
-        for (int a = 0; a < KM; a++)
-#pragma unroll
-            for (int b = a + 1; b < KM; b++)
-                if (near_tie(c[a], c[b], tol)) own |= (1u << a) | (1u << b);
-        const int32_t r0 = rev_ptr[v], r1 = rev_ptr[v + 1];
-        for (int32_t r = r0; r < r1; r++) {
-            const int32_t sr = __ldg(rev + r);
-            const float cr = __ldg(cost_slot + sr);
-            bool hit = false;
-#pragma unroll
-            for (int a = 0; a < KM; a++)
-                if (near_tie(c[a], cr, tol)) {
-                    own |= 1u << a;
-                    hit = true;
-                }
-            for (int32_t r2 = r + 1; r2 < r1; r2++) {
-                const int32_t s2 = __ldg(rev + r2);
-                if (near_tie(cr, __ldg(cost_slot + s2), tol)) {
-                    hit = true;
-                    mark_slot(bits, s2, list, cnt);
-                }
+            for (int t = 0; t < KS / 4; t++) {
+                const float4 x = __ldg(c4 + t);
+                key[4 * t] = (cost_order_bits(x.x) & ~IMASK) | (uint32_t)(4 * t);
+                key[4 * t + 1] = (cost_order_bits(x.y) & ~IMASK) | (uint32_t)(4 * t + 1);
+                key[4 * t + 2] = (cost_order_bits(x.z) & ~IMASK) | (uint32_t)(4 * t + 2);
+                key[4 * t + 3] = (cost_order_bits(x.w) & ~IMASK) | (uint32_t)(4 * t + 3);
             }
-            if (hit) mark_slot(bits, sr, list, cnt);
+        }
+        sort_asc_u32<KS>(key);
+        uint32_t own = 0;  // own slots to mark
+        float prev = key_value<KS>(key[0]);
+#pragma unroll
+        for (int a = 0; a + 1 < KS; a++) {
+            const float cur = key_value<KS>(key[a + 1]);
+            if (close(prev, cur)) own |= (1u << (key[a] & IMASK)) | (1u << (key[a + 1] & IMASK));
+            prev = cur;
+        }
+        if (r1 > r0) {
+#pragma unroll
+            for (int a = 0; a < KS; a++) skey[a][threadIdx.x] = key[a];
+            for (int32_t r = r0; r < r1; r++) {
+                const int32_t sr = __ldg(rev + r);
+                const float cr = __ldg(cost_slot + sr);
+                const uint32_t kr = cost_order_bits(cr);
+                // first sorted own key above kr, then its two neighbours
+                int lo = 0, hi = KS;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (skey[mid][threadIdx.x] <= kr) lo = mid + 1; else hi = mid;
+                }
+                bool hit = false;
+                if (lo > 0) {
+                    const uint32_t kb = skey[lo - 1][threadIdx.x];
+                    if (close(key_value<KS>(kb), cr)) { own |= 1u << (kb & IMASK); hit = true; }
+                }
+                if (lo < KS) {
+                    const uint32_t ka = skey[lo][threadIdx.x];
+                    if (close(key_value<KS>(ka), cr)) { own |= 1u << (ka & IMASK); hit = true; }
+                }
+                for (int32_t r2 = r + 1; r2 < r1; r2++) {
+                    const int32_t s2 = __ldg(rev + r2);
+                    if (near_tie(cr, __ldg(cost_slot + s2), tol)) {
+                        hit = true;
+                        mark_slot(bits, s2, list, cnt);
+                    }
+                }
+                if (hit) mark_slot(bits, sr, list, cnt);
+            }
         }
         while (own) {
             const int a = __ffs(own) - 1;
