@@ -374,6 +374,38 @@ def cost_variants_form(B, torch, pristine, target, tuning, args):
     return res
 
 
+def precision_form(B, torch, pristine, target, tuning, args):
+    """The eigen finish of the merge in float-float (fp64_policy 0, default)
+    and in FP64 (3) on the headline scene: whole-loop step time and the merge
+    kernel's time per step (CUDA events around its launches)."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for policy in (0, 3):
+        ctx = B.Context(fp64_policy=policy)
+        ctx.set_tuning(**tuning)
+        work = pristine.clone()
+        times = []
+        for it in range(1 + args.form_steps):
+            for a, b in zip(work.tensors(), pristine.tensors()):
+                a.copy_(b)
+            work.n = pristine.n
+            if it == 1:
+                B.ngs_profile_reset(ctx.handle)
+                B.ngs_profile_enable(ctx.handle, True)
+            ms, st = _timed(torch, stream, lambda: ctx.simplify(work, target))
+            if it:
+                times.append(ms)
+        B.ngs_profile_enable(ctx.handle, False)
+        merge_ms = sum(p[2] for p in B.ngs_profile(ctx.handle) if p[0] == "merge") / args.form_steps
+        res[f"policy_{policy}"] = {"step_ms_with_events": statistics.median(times),
+                                   "merge_ms_per_step": merge_ms,
+                                   "eigen_finish": "float-float" if policy == 0 else "fp64"}
+        del work
+        ctx.close()
+    torch.cuda.empty_cache()
+    return res
+
+
 def serving_form(B, torch, synth, args):
     """Poisson stream (20 jobs/s, 200 jobs, sizes log-uniform on [20k, 6M],
     ratios from {0.5, 0.1, 0.01}) replayed through the serving loop (4 slots,
@@ -592,6 +624,7 @@ def main():
         forms["batched"] = batched_form(B, torch, synth, args)
         forms["serving"] = serving_form(B, torch, synth, args)
         forms["cost_variants"] = cost_variants_form(B, torch, pristine, target, tuning, args)
+        forms["precision"] = precision_form(B, torch, pristine, target, tuning, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -89,7 +89,8 @@ typedef struct {
  *               near-degenerate merged covariances (default);
  *               1: additionally FP64 cost terms for edges with a
  *               near-degenerate endpoint; 2: the float-float finish only for
- *               ill-conditioned merged covariances
+ *               ill-conditioned merged covariances; 3: as 0 with the
+ *               eigendecomposition finished in FP64 instead of float-float
  *   prefilter   1: ngs_simplify first applies the opacity pre-filter
  *   eig_floor   lower bound on merged covariance eigenvalues (default 1e-30)
  *   cost_tol    accuracy contract of the edge costs (default 3e-5; 0 turns

@@ -14,7 +14,7 @@
 // The eigendecomposition starts with an FP32 cyclic Jacobi and is finished
 // in float-float arithmetic (Sigma_m assembled in float-float, one Jacobi
 // sweep warm-started from the re-orthonormalised FP32 eigenvectors; see
-// finish_ff).  Canonical form: eigenvalues descending,
+// finish_ff), or in FP64 under fp64_policy 3 (finish_fp64).  Canonical form: eigenvalues descending,
 // each eigenvector's largest-magnitude component positive, det V = +1,
 // quaternion with w >= 0.
 #include "ngs_device.cuh"
@@ -252,6 +252,65 @@ __device__ __forceinline__ void finish_ff(const float *Ri, const float *Rj, cons
     lam[2] = B[5];
 }
 
+// FP64 finish of the eigendecomposition (fp64_policy 3): Sigma_m assembled
+// in FP64 from the inputs (rotation from the quaternion, s^2 = e^{2 log s},
+// pi from the weights, the centre difference), rotated into the FP32
+// eigenvectors V and diagonalised by FP64 Jacobi sweeps; eigenvalues and
+// eigenvectors are handed to the canonical form as float-float and FP32.
+__device__ __forceinline__ void finish_fp64(const float *qi, const float *qj, const float *lsi,
+                                            const float *lsj, float li, float lj, const float *mi,
+                                            const float *mj, float *V, ff *lam) {
+    double Ri[9], Rj[9], s2i[3], s2j[3], Si[9], Sj[9], S[9];
+    quat_to_rot<double>(qi, Ri);
+    quat_to_rot<double>(qj, Rj);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        s2i[a] = exp(2.0 * (double)lsi[a]);
+        s2j[a] = exp(2.0 * (double)lsj[a]);
+    }
+    rot_cov<double>(Ri, s2i, Si);
+    rot_cov<double>(Rj, s2j, Sj);
+    const double lwi = -softplus_d(-(double)li) + ((double)lsi[0] + (double)lsi[1] + (double)lsi[2]);
+    const double lwj = -softplus_d(-(double)lj) + ((double)lsj[0] + (double)lsj[1] + (double)lsj[2]);
+    const double ld = lwi - lwj, t = exp(-fabs(ld));
+    const double big = 1.0 / (1.0 + t), small = t * big;
+    const double pi = ld >= 0 ? big : small, pj = ld >= 0 ? small : big;
+    double d[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) d[a] = (double)mi[a] - (double)mj[a];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+            S[3 * a + b] = pi * Si[3 * a + b] + pj * Sj[3 * a + b] + pi * pj * d[a] * d[b];
+    // A = Q^T S Q with Q = V (FP32 eigenvectors), then Jacobi in FP64
+    double Q[9], T[9], A[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) Q[k] = V[k];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+            T[3 * a + b] = S[3 * a] * Q[b] + S[3 * a + 1] * Q[3 + b] + S[3 * a + 2] * Q[6 + b];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+            A[3 * a + b] = Q[a] * T[b] + Q[3 + a] * T[3 + b] + Q[6 + a] * T[6 + b];
+    for (int sw = 0; sw < 8; sw++) {
+        if (offdiag2(A) <= 1e-30 * diag2(A)) break;
+        jacobi_sweep<double>(A, Q);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const double l = A[4 * k];
+        const float h = (float)l;
+        lam[k] = {h, (float)(l - (double)h)};
+    }
+#pragma unroll
+    for (int k = 0; k < 9; k++) V[k] = (float)Q[k];
+}
+
 // canonical eigen form + quaternion (w >= 0)
 __device__ void canonical_quat(ff *lam, float *V, float *q_out) {
     // sort descending (3-element network), permuting columns
@@ -370,7 +429,8 @@ __device__ __forceinline__ void stg_v8m(float *p, const float *r) {
                  :: "l"(p), "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]));
 }
 // merge rows i and j of `in` into row o of `out`; returns 1 if an eigenvalue
-// was raised to the floor
+// was raised to the floor.  F64: the FP64 eigen finish (fp64_policy 3).
+template <bool F64>
 __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out, int64_t o, int F, int sh8,
                           double eig_floor, int policy) {
     // every input field through the read-only path, so no load waits behind
@@ -451,7 +511,9 @@ __device__ int merge_pair(const Rows &in, int64_t i, int64_t j, const WRows &out
     }
     ff lam[3];
     const float lmin = fminf(fminf(A[0], A[4]), A[8]), lmax = fmaxf(fmaxf(A[0], A[4]), A[8]);
-    if (policy != 2 || !(lmin > 1e-4f * lmax)) {
+    if (F64) {
+        finish_fp64(qi, qj, lsi, lsj, li, lj, mi, mj, V, lam);
+    } else if (policy != 2 || !(lmin > 1e-4f * lmax)) {
         finish_ff(Ri, Rj, s2i, s2j, pi, pj, mi, mj, V, lam);
     } else {
         lam[0] = {A[0], 0.f};
@@ -510,6 +572,7 @@ __global__ void k_list_merges(int64_t n, const int32_t *__restrict__ mflag,
         if (mflag[v]) list[mpos[v]] = (int32_t)v;
 }
 
+template <bool F64>
 __global__ void k_merge(Rows in, WRows out, const int32_t *__restrict__ list, int64_t npairs, int F, int sh8,
                         const int32_t *__restrict__ role, const int32_t *__restrict__ pos,
                         double eig_floor, int policy, unsigned long long *floor_hits) {
@@ -517,7 +580,7 @@ __global__ void k_merge(Rows in, WRows out, const int32_t *__restrict__ list, in
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npairs;
          t += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = list[t];
-        hits += merge_pair(in, i, role[i], out, pos[i], F, sh8, eig_floor, policy);
+        hits += merge_pair<F64>(in, i, role[i], out, pos[i], F, sh8, eig_floor, policy);
     }
     if (hits) atomicAdd(floor_hits, (unsigned long long)hits);
 }
@@ -656,7 +719,8 @@ int64_t merge_compact(ngs_ctx *c, const SplatView &in, const int32_t *role, Spla
     unsigned long long *hits = (unsigned long long *)ws<uint8_t>(c, c->b_status, 64) + 1;
     NGS_CHECK_CUDA(cudaMemsetAsync(hits, 0, 8, c->st));
     if (npairs > 0)
-        launch(c, "merge", dim3(grid_stride_blocks(c, npairs, 128, 16)), dim3(128), 0, k_merge, ri,
+        launch(c, "merge", dim3(grid_stride_blocks(c, npairs, 128, 16)), dim3(128), 0,
+               c->prm.fp64_policy == 3 ? k_merge<true> : k_merge<false>, ri,
                wo, (const int32_t *)list, npairs, in.F,
                (in.F % 8 == 0 && ((uintptr_t)ri.sh & 31) == 0 && ((uintptr_t)wo.sh & 31) == 0) ? 1 : 0,
                role, (const int32_t *)pos,

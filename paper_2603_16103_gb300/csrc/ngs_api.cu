@@ -222,7 +222,7 @@ static int check_params(const ngs_params *p) {
     if (p->cost_mode < 0 || p->cost_mode > 3) return 0;
     if (!(p->tau >= 0.0 && p->tau < 1.0)) return 0;
     if (p->max_passes < 0 || p->max_passes > NGS_STATS_MAX_PASSES) return 0;
-    if (p->fp64_policy < 0 || p->fp64_policy > 2) return 0;
+    if (p->fp64_policy < 0 || p->fp64_policy > 3) return 0;
     if (!(p->eig_floor > 0.0)) return 0;
     if (!(p->cost_tol >= 0.0 && p->cost_tol <= 1e-4)) return 0;
     return 1;

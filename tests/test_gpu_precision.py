@@ -1,7 +1,8 @@
 """Precision report: error of every output attribute against the FP64 oracle
 on the 200,000-splat scene with 5% near-degenerate splats and 1% duplicated
 centres, for each FP64 policy.  One pass in lockstep (the oracle runs on the
-GPU's own pass input); the report is printed as one JSON line per policy."""
+GPU's own pass input); the report is printed as one JSON line per policy
+(3: the eigendecomposition finished in FP64 instead of float-float)."""
 import json
 
 import numpy as np
@@ -48,7 +49,7 @@ def attr_errors(cur, pairs, got):
             for k, v in out.items()}
 
 
-@pytest.mark.parametrize("policy", [0, 1, 2])
+@pytest.mark.parametrize("policy", [0, 1, 2, 3])
 def test_precision_report(ngs, policy):
     scene = synth.workload("patches200k")
     c = ngs.Context(fp64_policy=policy)
@@ -60,7 +61,7 @@ def test_precision_report(ngs, policy):
         cost = c.edge_costs(ds, g, 0)
         z, u = O.mc_draws(0, 0, 1)
         rc = O.edge_costs(cur, lo.cpu().numpy(), hi.cpu().numpy(), z, u)
-        cerr = np.abs(cost.cpu().numpy().astype(np.float64) - rc) / (1 + np.abs(rc))
+        cerr = np.abs(cost.cpu().numpy().astype(np.float64) - rc) / np.maximum(np.abs(rc), 1)
         pairs = c.select_pairs(g, cost, cur.n // 2)
         rlo, rhi = O.greedy(cur.n, lo.cpu().numpy(), hi.cpu().numpy(),
                             cost.cpu().numpy().astype(np.float64), cur.n // 2)
@@ -69,7 +70,7 @@ def test_precision_report(ngs, policy):
         p = pairs.cpu().numpy()
         c.merge_compact(ds, pairs)
         rep = attr_errors(cur, p, ds.numpy())
-        rep["edge_cost_rel"] = {"max": float(cerr.max()), "mean": float(cerr.mean()),
+        rep["edge_cost_rel_max1"] = {"max": float(cerr.max()), "mean": float(cerr.mean()),
                                 "p99.9": float(np.quantile(cerr, 0.999))}
         w = int(np.argmax(cerr))
         lw, hw = int(lo[w]), int(hi[w])
@@ -88,5 +89,6 @@ def test_precision_report(ngs, policy):
         # the extended-precision eigen finish keeps small eigenvalues accurate
         # (sorted log-scales); policy 2 skips it for well-conditioned merges
         assert rep["log_scale_abs"]["max"] <= (1e-5 if policy != 2 else 1e-4)
+        assert cerr.max() <= c.params.cost_tol
     finally:
         c.close()
