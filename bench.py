@@ -44,6 +44,7 @@ SPLAT_BYTES = 4 * (3 + 3 + 4 + 1 + 48)   # 236 B per splat, SH degree 3
 # smallest block it scans: 64 candidates per query x 9 ops (3 sub, 3 mul,
 # 2 add, 1 compare).
 KNN_OPS_PER_QUERY = 64 * 9
+KNN_HBM_BYTES_PER_QUERY = 12 + 64
 ALGO = {
     "knn_k16": ("alu", lambda n, e, p: n * KNN_OPS_PER_QUERY, "Gop/s"),
     # each splat's 64-byte record and 192-byte SH row read once, per edge its
@@ -582,8 +583,17 @@ def main():
         traffic = None
         if name in NCU_TRAFFIC_PER_SPLAT:
             traffic = NCU_TRAFFIC_PER_SPLAT[name] * sum(x[0] for x in per_step) / launches_per_step
+        extra = {}
+        if name == "knn_k16":
+            # the same launches against HBM on the scope table's bytes per query
+            # (12 B centre read + 64 B neighbour ids written)
+            gbs = sum(x[0] for x in per_step) * KNN_HBM_BYTES_PER_QUERY / launches_per_step \
+                / avg_launch_s / 1e9
+            extra = {"hbm_view": {"bytes_per_query": KNN_HBM_BYTES_PER_QUERY, "achieved": gbs,
+                                  "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                  "frac": gbs / pk["hbm_gbs"]}}
         return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic,
+                "frac": achieved / peak, "traffic": traffic, **extra,
                 "peak_source": (f"{src} hbm_gbs" if bound == "hbm" else
                                 f"{sms} SMs x 128 FP32 lanes x {src} sm_max_mhz"),
                 "share": ms / kern_total, "ms_per_launch": avg_launch_s * 1e3}
