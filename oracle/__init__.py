@@ -78,7 +78,10 @@ def lib():
             L.orc_simplify.argtypes = [_i64, _ptr, _ptr, _ptr, _ptr, _ptr, ctypes.c_int, _i64,
                                        ctypes.c_int, _dbl, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, _dbl, _dbl, _u64, _dbl, ctypes.c_int,
-                                       ctypes.c_int, _ptr, _ptr, _ptr, _ptr]
+                                       ctypes.c_int, ctypes.c_int, _ptr, _ptr, _ptr, _ptr, _ptr]
+            L.orc_refresh_lists.restype = _i64
+            L.orc_refresh_lists.argtypes = [_i64, ctypes.c_int, _ptr, _i64, _ptr, _ptr, _i64,
+                                            _ptr, ctypes.c_int, _ptr, _ptr]
             L.orc_quat_to_R.restype = None
             L.orc_quat_to_R.argtypes = [_ptr, _ptr]
             L.orc_eig3.restype = ctypes.c_int
@@ -227,7 +230,7 @@ def merge_compact(splats, pair_lo, pair_hi, eig_floor: float = 1e-30):
 def simplify(splats, target: int, k: int = 16, tau: float = 0.005, prefilter: bool = True,
              S: int = 1, mode: int = 0, lambda_geo: float = 1.0, lambda_app: float = 1.0,
              seed: int = 0, eig_floor: float = 1e-30, max_passes: int = 64,
-             use_grid: bool = True):
+             use_grid: bool = True, refresh_period: int = 1):
     arrs = [a.copy() for a in _splat_arrays(splats)]
     xyz, ls, rot, logit, sh = arrs
     n0, F = sh.shape
@@ -235,14 +238,31 @@ def simplify(splats, target: int, k: int = 16, tau: float = 0.005, prefilter: bo
     pn = np.zeros(max_passes, dtype=np.int64)
     pe = np.zeros(max_passes, dtype=np.int64)
     pm = np.zeros(max_passes, dtype=np.int64)
+    prq = np.zeros(max_passes, dtype=np.int64)
     nn = lib().orc_simplify(n0, _p(xyz), _p(ls), _p(rot), _p(logit), _p(sh), F, target, k,
                             tau, int(prefilter), S, mode, lambda_geo, lambda_app, seed,
-                            eig_floor, max_passes, int(use_grid), _p(passes), _p(pn), _p(pe),
-                            _p(pm))
+                            eig_floor, max_passes, int(use_grid), int(refresh_period),
+                            _p(passes), _p(pn), _p(pe), _p(pm), _p(prq))
     p = int(passes[0])
     stats = {"passes": p, "n": pn[:p].tolist(), "edges": pe[:p].tolist(),
-             "pairs": pm[:p].tolist()}
+             "pairs": pm[:p].tolist(), "requeried": prq[:p].tolist()}
     return tuple(a[:nn].copy() for a in arrs), stats
+
+
+def refresh_lists(prev, pair_lo, pair_hi, xyz_new, k: int = 16):
+    """Sec. 3.4 local refresh: (lists of the new splats, re-query flags)."""
+    prev = np.ascontiguousarray(prev, dtype=np.int32)
+    n_old, k_old = prev.shape
+    plo = np.ascontiguousarray(pair_lo, dtype=np.int32)
+    phi = np.ascontiguousarray(pair_hi, dtype=np.int32)
+    xyz = _d(xyz_new).reshape(-1, 3)
+    n_new = xyz.shape[0]
+    ke = k_effective(n_new, k)
+    out = np.full((n_new, max(ke, 0)), -1, dtype=np.int32)
+    rq = np.zeros(n_new, dtype=np.uint8)
+    lib().orc_refresh_lists(n_old, k_old, _p(prev), plo.shape[0], _p(plo), _p(phi), n_new,
+                            _p(xyz), k, _p(out), _p(rq))
+    return out, rq.astype(bool)
 
 
 # ---- single-pair helpers (pins) ----

@@ -766,6 +766,73 @@ int64_t orc_merge_compact(int64_t n, const double *xyz, const double *log_scale,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 3.4, local neighbourhood refresh: the lists of the pass after a merge */
+/* from the lists before it, re-running kNN queries only around new splats.   */
+
+/* Row order after a merge (merged splat at the lower row, the higher row
+   removed, the others in order): new id of every old row, the removed row
+   taking its partner's. */
+static void merge_id_map(int64_t n_old, int64_t np, const int32_t *plo, const int32_t *phi,
+                         int32_t *map_old) {
+    uint8_t *gone = (uint8_t *)calloc((size_t)(n_old > 0 ? n_old : 1), 1);
+    for (int64_t t = 0; t < np; t++) gone[phi[t]] = 1;
+    int32_t r = 0;
+    for (int64_t o = 0; o < n_old; o++) map_old[o] = gone[o] ? -1 : r++;
+    for (int64_t t = 0; t < np; t++) map_old[phi[t]] = map_old[plo[t]];
+    free(gone);
+}
+
+int64_t orc_refresh_lists(int64_t n_old, int k_old, const int32_t *prev, int64_t np,
+                          const int32_t *plo, const int32_t *phi, int64_t n_new,
+                          const double *xyz, int k, int32_t *nbr, uint8_t *requery) {
+    int ke = k_effective(n_new, k);
+    if (ke <= 0) return 0;
+    int32_t *map_old = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_old > 0 ? n_old : 1));
+    int32_t *src = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_new);
+    merge_id_map(n_old, np, plo, phi, map_old);
+    for (int64_t r = 0; r < n_new; r++) src[r] = -1;
+    uint8_t *merged = (uint8_t *)calloc((size_t)n_old, 1);
+    for (int64_t t = 0; t < np; t++) merged[plo[t]] = merged[phi[t]] = 1;
+    for (int64_t o = 0; o < n_old; o++)
+        if (!merged[o]) src[map_old[o]] = (int32_t)o;   /* kept rows; new splats stay -1 */
+    int64_t nq = 0;
+    cand_t *list = (cand_t *)malloc(sizeof(cand_t) * (size_t)(k_old > 0 ? k_old : 1));
+    for (int64_t r = 0; r < n_new; r++) {
+        int rq = src[r] < 0 || k_old != ke;
+        int cnt = 0;
+        for (int t = 0; !rq && t < k_old; t++) {
+            int32_t m = map_old[prev[(int64_t)src[r] * k_old + t]];
+            if (m == r) { rq = 1; break; }
+            for (int a = 0; a < cnt; a++)
+                if (list[a].j == m) { rq = 1; break; }
+            if (rq) break;
+            cand_t c = {dist2(xyz + 3 * r, xyz + 3 * (int64_t)m), m};
+            topk_insert(list, &cnt, ke, c);
+        }
+        requery[r] = (uint8_t)rq;
+        if (rq) { nq++; continue; }
+        for (int a = 0; a < ke; a++) nbr[r * ke + a] = list[a].j;   /* sorted by (d^2, id) */
+    }
+    if (nq > 0) {
+        int64_t *q = (int64_t *)malloc(sizeof(int64_t) * (size_t)nq);
+        int32_t *out = (int32_t *)malloc(sizeof(int32_t) * (size_t)nq * ke);
+        int64_t t = 0;
+        for (int64_t r = 0; r < n_new; r++)
+            if (requery[r]) q[t++] = r;
+        orc_knn_brute_queries(n_new, xyz, k, nq, q, out);
+        for (t = 0; t < nq; t++)
+            memcpy(nbr + q[t] * ke, out + t * ke, sizeof(int32_t) * ke);
+        free(q);
+        free(out);
+    }
+    free(list);
+    free(merged);
+    free(src);
+    free(map_old);
+    return nq;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Algorithm 1 end to end.                                                    */
 
 static void select_rows(int64_t n, const uint8_t *keep, double *a, int w) {
@@ -780,8 +847,9 @@ static void select_rows(int64_t n, const uint8_t *keep, double *a, int w) {
 int64_t orc_simplify(int64_t n0, double *xyz, double *log_scale, double *rot, double *logit,
                      double *sh, int F, int64_t target, int k, double tau, int prefilter,
                      int S, int mode, double lambda_geo, double lambda_app, uint64_t seed,
-                     double eig_floor, int max_passes, int use_grid,
-                     int32_t *passes, int64_t *pass_n, int64_t *pass_e, int64_t *pass_m) {
+                     double eig_floor, int max_passes, int use_grid, int refresh_period,
+                     int32_t *passes, int64_t *pass_n, int64_t *pass_e, int64_t *pass_m,
+                     int64_t *pass_rq) {
     int64_t n = n0;
     if (passes) *passes = 0;
     if (n <= 0) return 0;
@@ -809,9 +877,23 @@ int64_t orc_simplify(int64_t n0, double *xyz, double *log_scale, double *rot, do
     int32_t *phi = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n0 / 2 + 1));
     float *z = (float *)malloc(sizeof(float) * 3 * (S > 0 ? S : 1));
     float *u = (float *)malloc(sizeof(float) * (S > 0 ? S : 1));
+    int32_t *prev = (int32_t *)malloc(sizeof(int32_t) * (size_t)n0 * (k > 0 ? k : 1));
+    uint8_t *rqf = (uint8_t *)malloc((size_t)(n0 > 0 ? n0 : 1));
+    int64_t n_prev = 0, mm_prev = 0;
+    int ke_prev = 0;
     int p = 0;
     while (n > target && n > 1 && p < max_passes) {
-        int ke = use_grid ? orc_knn_grid(n, xyz, k, nbr) : orc_knn_brute(n, xyz, k, nbr);
+        int ke;
+        int64_t rq = n;
+        if (refresh_period > 1 && p % refresh_period != 0) {
+            /* the previous pass's lists carried through its merge */
+            memcpy(prev, nbr, sizeof(int32_t) * (size_t)n_prev * ke_prev);
+            rq = orc_refresh_lists(n_prev, ke_prev, prev, mm_prev, plo, phi, n, xyz, k, nbr, rqf);
+            ke = k_effective(n, k);
+        } else {
+            ke = use_grid ? orc_knn_grid(n, xyz, k, nbr) : orc_knn_brute(n, xyz, k, nbr);
+        }
+        if (pass_rq) pass_rq[p] = rq;
         int64_t m = orc_union_edges(n, ke, nbr, elo, ehi);
         orc_mc_draws(seed, (uint32_t)p, S, z, u);
         orc_edge_costs(n, xyz, log_scale, rot, logit, sh, F, m, elo, ehi, S, z, u, mode,
@@ -823,6 +905,9 @@ int64_t orc_simplify(int64_t n0, double *xyz, double *log_scale, double *rot, do
         if (pass_m) pass_m[p] = mm;
         p++;
         if (mm == 0) break;
+        n_prev = n;
+        ke_prev = ke;
+        mm_prev = mm;
         int64_t nn = orc_merge_compact(n, xyz, log_scale, rot, logit, sh, F, mm, plo, phi,
                                        eig_floor, b_xyz, b_ls, b_rot, b_logit, b_sh);
         memcpy(xyz, b_xyz, sizeof(double) * 3 * nn);
@@ -835,5 +920,6 @@ int64_t orc_simplify(int64_t n0, double *xyz, double *log_scale, double *rot, do
     if (passes) *passes = p;
     free(b_xyz); free(b_ls); free(b_rot); free(b_logit); free(b_sh);
     free(nbr); free(elo); free(ehi); free(cost); free(plo); free(phi); free(z); free(u);
+    free(prev); free(rqf);
     return n;
 }

@@ -82,8 +82,20 @@ int64_t orc_merge_compact(int64_t n, const double *xyz, const double *log_scale,
 int64_t orc_simplify(int64_t n0, double *xyz, double *log_scale, double *rot, double *logit,
                      double *sh, int F, int64_t target, int k, double tau, int prefilter,
                      int S, int mode, double lambda_geo, double lambda_app, uint64_t seed,
-                     double eig_floor, int max_passes, int use_grid,
-                     int32_t *passes, int64_t *pass_n, int64_t *pass_e, int64_t *pass_m);
+                     double eig_floor, int max_passes, int use_grid, int refresh_period,
+                     int32_t *passes, int64_t *pass_n, int64_t *pass_e, int64_t *pass_m,
+                     int64_t *pass_rq);
+/* Sec. 3.4 local neighbourhood refresh: the kNN lists after a merge from the
+   lists before it.  prev: n_old x k_old lists; (plo[t], phi[t]) the merged
+   pairs (old ids, plo < phi); xyz: the n_new centres after the merge (merged
+   splat at the lower row, the higher row removed, others in order).  A new
+   row is re-queried (exact k_eff nearest, brute force) when it holds a merged
+   splat, when k_eff changed, or when its old list maps to an id repeated or
+   equal to itself; otherwise its list is the mapped old list sorted by
+   (d^2, id).  requery[r] records the decision; returns the re-queried count. */
+int64_t orc_refresh_lists(int64_t n_old, int k_old, const int32_t *prev, int64_t np,
+                          const int32_t *plo, const int32_t *phi, int64_t n_new,
+                          const double *xyz, int k, int32_t *nbr, uint8_t *requery);
 
 /* ---- single-pair helpers, exposed for the pins ---- */
 /* Unit quaternion (w,x,y,z) -> row-major rotation matrix (normalises q). */

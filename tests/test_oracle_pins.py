@@ -535,3 +535,77 @@ def test_simplify_counts_and_loop_rules():
     assert out4[0].shape[0] == 1 and st4["passes"] == 0
     out5, st5 = O.simplify(sc, 1, max_passes=64)
     assert out5[0].shape[0] == 1          # a graph exists until one splat is left
+
+
+# ---- Sec. 3.4 local neighbourhood refresh ----
+
+def test_refresh_lists_hand_derived():
+    g = json.load(open(os.path.join(GOLDEN, "refresh_line6.json")))
+    line = lambda x: np.stack([np.asarray(x, float), np.zeros(len(x)), np.zeros(len(x))], 1)
+    prev = O.knn(line(g["x_old"]), g["k"])
+    assert prev.tolist() == g["lists_old"]
+    pairs = np.asarray(g["pairs"])
+    nb, rq = O.refresh_lists(prev, pairs[:, 0], pairs[:, 1], line(g["x_new"]), g["k"])
+    assert nb.tolist() == g["lists_new"]
+    assert rq.tolist() == g["requery"]
+
+
+def test_refresh_lists_properties():
+    """On a merged random scene: re-queried rows are exactly the merged
+    splats and the rows whose mapped list collapses; kept rows hold the mapped
+    ids of their old list; re-queried rows hold the brute-force kNN."""
+    scene = synth.surfaces_unit_cube(3000, seed=8)
+    k = 8
+    prev = O.knn(scene.xyz, k)
+    lo, hi = O.union_edges(prev)
+    z, u = O.mc_draws(0, 0, 1)
+    plo, phi = O.greedy(scene.n, lo, hi, O.edge_costs(scene, lo, hi, z, u), scene.n // 4)
+    merged = O.merge_compact(scene, plo, phi)
+    nb, rq = O.refresh_lists(prev, plo, phi, merged[0], k)
+    n_new = merged[0].shape[0]
+    assert n_new == scene.n - len(plo)
+    # old -> new ids, written out independently of the oracle
+    gone = np.zeros(scene.n, bool)
+    gone[phi] = True
+    newid = np.cumsum(~gone) - 1
+    newid[phi] = newid[plo]
+    is_merged = np.zeros(scene.n, bool)
+    is_merged[plo] = is_merged[phi] = True
+    src = np.full(n_new, -1)
+    kept = np.nonzero(~is_merged)[0]
+    src[newid[kept]] = kept
+    brute = O.knn(merged[0], k)
+    for r in range(n_new):
+        if src[r] < 0:
+            assert rq[r]
+            continue
+        m = newid[prev[src[r]]]
+        collapses = len(set(m.tolist())) < k or r in set(m.tolist())
+        assert rq[r] == collapses
+        if collapses:
+            assert np.array_equal(nb[r], brute[r])
+        else:
+            assert sorted(nb[r].tolist()) == sorted(m.tolist())
+            d2 = np.sum((merged[0][nb[r]] - merged[0][r]) ** 2, 1)
+            assert np.all(np.diff(d2) >= 0)
+    assert np.array_equal(nb[rq], brute[rq])
+
+
+def test_simplify_refresh_period():
+    """Period 1 re-queries every row (the rebuild every pass of the paper's
+    runs); period 2 carries lists on odd passes and still reaches the target
+    exactly; a period longer than the run is the rebuild on pass 0 only."""
+    scene = synth.surfaces_unit_cube(4000, seed=9)
+    target = O.target_count(scene.n, 0.2)
+    out1, st1 = O.simplify(scene, target, refresh_period=1)
+    assert st1["requeried"] == st1["n"]
+    out2, st2 = O.simplify(scene, target, refresh_period=2)
+    assert out2[0].shape[0] == target
+    assert st2["passes"] >= 2
+    for p in range(st2["passes"]):
+        if p % 2 == 0:
+            assert st2["requeried"][p] == st2["n"][p]
+        else:
+            assert 0 < st2["requeried"][p] <= st2["n"][p]
+    out1b, st1b = O.simplify(scene, target)
+    assert st1b == st1 and all(np.array_equal(a, b) for a, b in zip(out1, out1b))
