@@ -407,6 +407,48 @@ def precision_form(B, torch, pristine, target, tuning, args):
     return res
 
 
+def refresh_form(B, torch, pristine, target, tuning, args):
+    """Local neighbourhood refresh (Sec. 3.4) on the headline scene: the
+    whole loop with the kNN graph rebuilt every pass (the paper's runs,
+    default) and carried through the merges on every second and on all but
+    every fourth pass; step time, kNN queries per step and kNN time."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for period in (1, 2, 4):
+        ctx = B.Context(refresh_period=period)
+        ctx.set_tuning(**tuning)
+        work = pristine.clone()
+        times = []
+        for it in range(1 + args.form_steps):
+            for a, b in zip(work.tensors(), pristine.tensors()):
+                a.copy_(b)
+            work.n = pristine.n
+            ms, st = _timed(torch, stream, lambda: ctx.simplify(work, target))
+            if it:
+                times.append(ms)
+        # kNN-stage time of one more step with per-launch events
+        for a, b in zip(work.tensors(), pristine.tensors()):
+            a.copy_(b)
+        work.n = pristine.n
+        B.ngs_profile_reset(ctx.handle)
+        B.ngs_profile_enable(ctx.handle, True)
+        ctx.simplify(work, target)
+        B.ngs_profile_enable(ctx.handle, False)
+        knn_ms = sum(p[2] for p in B.ngs_profile(ctx.handle)
+                     if p[0].startswith("knn_") or p[0].startswith("refresh") or
+                     p[0].startswith("qpos"))
+        res[f"period_{period}"] = {
+            "step_ms": statistics.median(times), "value": pristine.n / (statistics.median(times) / 1e3),
+            "unit": UNIT, "passes": st["passes"], "knn_queries": st["requeried_rows"],
+            "rows_over_passes": sum(st["pass_n"]),
+            "queried_fraction": st["requeried_rows"] / max(1, sum(st["pass_n"])),
+            "knn_stage_ms": knn_ms, "n_output": work.n}
+        del work
+        ctx.close()
+    torch.cuda.empty_cache()
+    return res
+
+
 def serving_form(B, torch, synth, args):
     """Poisson stream (20 jobs/s, 200 jobs, sizes log-uniform on [20k, 6M],
     ratios from {0.5, 0.1, 0.01}) replayed through the serving loop (4 slots,
@@ -635,6 +677,7 @@ def main():
         forms["serving"] = serving_form(B, torch, synth, args)
         forms["cost_variants"] = cost_variants_form(B, torch, pristine, target, tuning, args)
         forms["precision"] = precision_form(B, torch, pristine, target, tuning, args)
+        forms["refresh"] = refresh_form(B, torch, pristine, target, tuning, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -101,6 +101,13 @@ typedef struct {
  *               of each other are both recomputed in FP64 (rounded once to
  *               FP32), so every decision of the greedy rule (Sec. 3.4)
  *               follows the FP64 costs up to one FP32 rounding
+ *   refresh_period  local neighbourhood refresh (Sec. 3.4; default 1, the
+ *               rebuild every pass of the paper's runs): ngs_simplify rebuilds
+ *               the kNN graph on passes p with p % refresh_period == 0 and on
+ *               the others carries the previous lists through the merge,
+ *               querying again only new splats and rows whose carried list
+ *               collapsed (ngs_build_graph_refresh).  One scene only:
+ *               ngs_batch_simplify rebuilds every pass.  1..NGS_STATS_MAX_PASSES
  */
 typedef struct {
     int32_t  k;
@@ -115,6 +122,7 @@ typedef struct {
     int32_t  prefilter;
     double   eig_floor;
     double   cost_tol;
+    int32_t  refresh_period;
 } ngs_params;
 
 /* The merge graph of one pass (Sec. 3.1, Algorithm 1 KNN and
@@ -154,6 +162,8 @@ typedef struct {
     int64_t gpu_launches;   /* kernels the library launched for this call    */
     int64_t near_tie_slots; /* list slots recomputed in FP64 as near ties
                              * (a mutual edge may count twice)             */
+    int64_t requeried_rows; /* kNN queries over all passes (a rebuild queries
+                             * every row; a local refresh only some)       */
 } ngs_stats;
 
 /* ---- lifecycle ---- */
@@ -296,6 +306,29 @@ int ngs_profile_get(ngs_ctx *ctx, int i, const char **name, int64_t *launches, d
 int ngs_profile_reset(ngs_ctx *ctx);
 /* Total kernels launched by the ctx since creation (all calls). */
 int64_t ngs_launch_count(ngs_ctx *ctx);
+/* Local neighbourhood refresh (Sec. 3.4: re-run kNN queries around newly
+ * formed splats).  Builds the merge graph of the splats a merge produced from
+ * the lists before that merge, like ngs_build_graph but querying only some
+ * rows:
+ *   s         the splats after ngs_merge_compact(pairs): n = n_old - n_pairs,
+ *             merged splat at the lower row, the higher row removed, the
+ *             others in order
+ *   prev_nbr  device, n_old x k_old directed lists of the splats before the
+ *             merge (for example graph->nbr of the previous build; it is
+ *             copied first, so it may be that ctx-owned array); every entry
+ *             in [0, n_old), else INVALID_ARG
+ *   pairs     device, 2*n_pairs (lo, hi) rows as given to ngs_merge_compact
+ *   out, n_requeried (host, may be NULL)  as ngs_build_graph; the rows
+ *             queried anew
+ * A row is queried anew (exact k_eff nearest) when it holds a merged splat,
+ * when k_eff changed, or when its old list maps to a repeated id or to
+ * itself; otherwise its list is its old neighbours' new rows, sorted by
+ * (d^2, index).  Synchronises the ctx stream.
+ * Errors: INVALID_ARG (sizes, pairs, list entries), OOM, CUDA. */
+int ngs_build_graph_refresh(ngs_ctx *ctx, const ngs_splats *s, const int32_t *prev_nbr,
+                            int64_t n_old, int32_t k_old, const int32_t *pairs, int64_t n_pairs,
+                            ngs_graph *out, int64_t *n_requeried);
+
 /* Device workspace the ctx currently holds, in bytes (grows with the largest
  * input seen; released by ngs_destroy). */
 int64_t ngs_workspace_bytes(ngs_ctx *ctx);

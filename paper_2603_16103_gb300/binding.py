@@ -50,7 +50,8 @@ class ngs_params(ctypes.Structure):
                 ("lambda_geo", ctypes.c_float), ("lambda_app", ctypes.c_float),
                 ("seed", ctypes.c_uint64), ("max_passes", ctypes.c_int32),
                 ("fp64_policy", ctypes.c_int32), ("prefilter", ctypes.c_int32),
-                ("eig_floor", ctypes.c_double), ("cost_tol", ctypes.c_double)]
+                ("eig_floor", ctypes.c_double), ("cost_tol", ctypes.c_double),
+                ("refresh_period", ctypes.c_int32)]
 
 
 class ngs_graph(ctypes.Structure):
@@ -67,7 +68,8 @@ class ngs_stats(ctypes.Structure):
                 ("pass_edges", ctypes.c_int64 * NGS_STATS_MAX_PASSES),
                 ("pass_pairs", ctypes.c_int64 * NGS_STATS_MAX_PASSES),
                 ("fp64_cost_edges", ctypes.c_int64), ("eig_floor_hits", ctypes.c_int64),
-                ("gpu_launches", ctypes.c_int64), ("near_tie_slots", ctypes.c_int64)]
+                ("gpu_launches", ctypes.c_int64), ("near_tie_slots", ctypes.c_int64),
+                ("requeried_rows", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         p = self.passes
@@ -78,7 +80,7 @@ class ngs_stats(ctypes.Structure):
                 "pass_pairs": list(self.pass_pairs[:p]),
                 "fp64_cost_edges": self.fp64_cost_edges,
                 "eig_floor_hits": self.eig_floor_hits, "gpu_launches": self.gpu_launches,
-                "near_tie_slots": self.near_tie_slots}
+                "near_tie_slots": self.near_tie_slots, "requeried_rows": self.requeried_rows}
 
 
 class ngs_tuning(ctypes.Structure):
@@ -130,6 +132,10 @@ _SIGS = {
     "ngs_last_error": (ctypes.c_char_p, []),
     "ngs_prefilter": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats)]),
     "ngs_build_graph": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), ctypes.POINTER(ngs_graph)]),
+    "ngs_build_graph_refresh": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), _P, ctypes.c_int64,
+                                               ctypes.c_int32, _P, ctypes.c_int64,
+                                               ctypes.POINTER(ngs_graph),
+                                               ctypes.POINTER(ctypes.c_int64)]),
     "ngs_edge_costs": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), ctypes.POINTER(ngs_graph),
                                       ctypes.c_uint32, _P]),
     "ngs_select_pairs": (ctypes.c_int, [_P, ctypes.POINTER(ngs_graph), _P, ctypes.c_int64, _P,
@@ -244,6 +250,16 @@ def ngs_build_graph(ctx: int, s: ngs_splats) -> ngs_graph:
     g = ngs_graph()
     _check(load().ngs_build_graph(_P(ctx), ctypes.byref(s), ctypes.byref(g)))
     return g
+
+
+def ngs_build_graph_refresh(ctx: int, s: ngs_splats, prev_ptr: int, n_old: int, k_old: int,
+                            pairs_ptr: int, n_pairs: int):
+    g = ngs_graph()
+    nq = ctypes.c_int64(0)
+    _check(load().ngs_build_graph_refresh(_P(ctx), ctypes.byref(s), _P(prev_ptr), n_old, k_old,
+                                          _P(pairs_ptr), n_pairs, ctypes.byref(g),
+                                          ctypes.byref(nq)))
+    return g, nq.value
 
 
 def ngs_edge_costs(ctx: int, s: ngs_splats, g: ngs_graph, pass_index: int, cost_ptr: int):
@@ -400,6 +416,23 @@ class Context:
         lo = _wrap_i32(g.edge_lo, g.n_edges, dev).clone()
         hi = _wrap_i32(g.edge_hi, g.n_edges, dev).clone()
         return g, nbr, lo, hi
+
+    def build_graph_refresh(self, ds: DeviceSplats, prev_nbr, pairs):
+        """Local refresh (Sec. 3.4) after merging `pairs` (int32 [m, 2], old
+        rows) into splats whose lists were `prev_nbr` (int32 [n_old, k_old]).
+        Returns (graph struct, nbr, edge_lo, edge_hi, rows queried anew)."""
+        s = ds.struct()
+        prev = prev_nbr.contiguous()
+        pr = pairs.contiguous()
+        g, nq = ngs_build_graph_refresh(self.handle, s, prev.data_ptr(), prev.shape[0],
+                                        prev.shape[1] if prev.dim() == 2 else 0,
+                                        pr.data_ptr(), pr.shape[0])
+        dev = ds.xyz.device
+        nbr = _wrap_i32(g.nbr, g.n * g.k_eff, dev).view(g.n, g.k_eff).clone() if g.k_eff > 0 \
+            else torch.zeros((g.n, 0), dtype=torch.int32, device=dev)
+        lo = _wrap_i32(g.edge_lo, g.n_edges, dev).clone()
+        hi = _wrap_i32(g.edge_hi, g.n_edges, dev).clone()
+        return g, nbr, lo, hi, nq
 
     def edge_costs(self, ds: DeviceSplats, g: ngs_graph, pass_index: int = 0):
         cost = torch.empty(max(1, g.n_edges), dtype=torch.float32, device=ds.xyz.device)

@@ -648,7 +648,13 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     };
 
     int pass = 0;
-    int64_t fp64_total = 0, tie_total = 0;
+    int64_t fp64_total = 0, tie_total = 0, requeried_total = 0;
+    // local neighbourhood refresh (Sec. 3.4), one scene: on passes p with
+    // p % refresh_period != 0 the previous lists are carried through the merge
+    const int R = multi ? 1 : c->prm.refresh_period;
+    bool have_prev = false;
+    int64_t n_prev = 0;
+    int k_prev = 0;
     while (pass < c->prm.max_passes) {
         extract(false);
         if (A.n <= 0) break;
@@ -691,8 +697,20 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         int32_t *nbr = ws<int32_t>(c, c->b_nbr, nA * g.k_eff);
         std::vector<int64_t> scene_n(S);
         for (int s = 0; s < S; s++) scene_n[s] = out_done[s] ? 0 : n[s];
-        knn_search(c, KnnInput{pts, pk, pv, ssid, frames, scene_n.data(), S, nA, 0, cidA},
-                   g.k_eff, nbr);
+        if (R > 1 && have_prev && pass % R != 0) {
+            int32_t *qlist = ws<int32_t>(c, c->b_qlist, nA + 1);
+            const int64_t nq = refresh_rows(c, nA, g.k_eff, k_prev, n_prev, (const int32_t *)c->b_rsrc.p,
+                                            (const int32_t *)c->b_prevnbr.p, (const int32_t *)c->b_rmap.p,
+                                            A.xyz, cidA, pv, nbr, qlist);
+            knn_search(c, KnnInput{pts, pk, pv, ssid, frames, scene_n.data(), S, nA, 0, cidA, qlist, nq},
+                       g.k_eff, nbr);
+            requeried_total += nq;
+        } else {
+            knn_search(c, KnnInput{pts, pk, pv, ssid, frames, scene_n.data(), S, nA, 0, cidA},
+                       g.k_eff, nbr);
+            requeried_total += nA;
+        }
+        have_prev = false;
         build_edges(c, nbr, g);
         ensure_sh();
         edge_costs(c, A, g, (uint32_t)pass, false, nullptr);
@@ -777,6 +795,14 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
             partner_to_role(c, partner, cidA, nA, role);
             B.n = nA;
             const int64_t nn = merge_compact(c, A, role, B, cidA, cidB);
+            if (R > 1 && pass % R != 0) {
+                // the next pass carries these lists: keep them and the row maps
+                refresh_map(c, nA, role, ws<int32_t>(c, c->b_rmap, nA), ws<int32_t>(c, c->b_rsrc, nn));
+                std::swap(c->b_nbr, c->b_prevnbr);
+                have_prev = true;
+                n_prev = nA;
+                k_prev = g.k_eff;
+            }
             std::swap(A, B);
             std::swap(cidA, cidB);
             int64_t cur = 0;
@@ -806,6 +832,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         st->passes = pass;
         st->fp64_cost_edges = fp64_total;
         st->near_tie_slots = tie_total;
+        st->requeried_rows = requeried_total;
         st->eig_floor_hits = c->floor_hits;
         st->gpu_launches = c->launches - launches0;
     }

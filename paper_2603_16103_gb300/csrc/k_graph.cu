@@ -217,6 +217,127 @@ __global__ void k_lex_view(const uint32_t *__restrict__ klo, const uint32_t *__r
     }
 }
 
+// ---------------------------------------------------------------- local refresh
+// Sec. 3.4: "re-running KNN queries around newly formed splats".  The lists
+// of a pass are carried through its merge: a kept row keeps the new ids of
+// its old neighbours when they are still k_eff distinct splats other than
+// itself; new splats and rows whose list collapsed are queried again.
+
+__global__ void k_refresh_keep(int64_t n, const int32_t *__restrict__ role, int32_t *keep) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        keep[v] = role[v] != -2;
+}
+
+__global__ void k_refresh_map(int64_t n_old, const int32_t *__restrict__ role,
+                              const int32_t *__restrict__ pos, int32_t *map_old, int32_t *src_new) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_old;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = role[o];
+        if (r == -2) continue;
+        const int32_t p = pos[o];
+        map_old[o] = p;
+        src_new[p] = r == -1 ? (int32_t)o : -1;
+        if (r >= 0) map_old[r] = p;  // the removed partner names the merged splat
+    }
+}
+
+__device__ __forceinline__ float dist2_rn3(float dx, float dy, float dz) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// ascending bitonic network over N register keys
+template <int N>
+__device__ __forceinline__ void sort_asc_u64(uint64_t (&a)[N]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint64_t x = a[i], y = a[l];
+                    const bool up = (i & k) == 0;
+                    const bool sw = up ? (x > y) : (x < y);
+                    a[i] = sw ? y : x;
+                    a[l] = sw ? x : y;
+                }
+            }
+}
+
+// K = k_eff in {4, 8, 16, 32}; K = 0 for any width up to NGS_MAX_K
+// An old list entry outside [0, n_old) sets *err and the row is queried.
+template <int K>
+__global__ void k_refresh_rows(int64_t n, int keff, int k_old, int64_t n_old,
+                               const int32_t *__restrict__ src_new,
+                               const int32_t *__restrict__ prev, const int32_t *__restrict__ map_old,
+                               const float *__restrict__ xyz, const int32_t *__restrict__ cid,
+                               int32_t *nbr, int32_t *qflag, int32_t *err) {
+    constexpr int KM = K > 0 ? K : NGS_MAX_K;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = src_new[r];
+        bool rq = o < 0 || k_old != keff;
+        uint64_t key[KM];
+        if (!rq) {
+            const float x = xyz[3 * r], y = xyz[3 * r + 1], z = xyz[3 * r + 2];
+#pragma unroll
+            for (int t = 0; t < KM; t++) {
+                if (K == 0 && t >= keff) {
+                    key[t] = ~0ull;
+                    continue;
+                }
+                const int32_t po = prev[(int64_t)o * k_old + t];
+                if (po < 0 || po >= n_old) {
+                    atomicOr(err, 1);
+                    rq = true;
+                    key[t] = ~0ull;
+                    continue;
+                }
+                const int32_t m = map_old[po];
+                rq = rq || m == (int32_t)r;
+                const float d2 = dist2_rn3(__fsub_rn(x, xyz[3 * (int64_t)m]),
+                                           __fsub_rn(y, xyz[3 * (int64_t)m + 1]),
+                                           __fsub_rn(z, xyz[3 * (int64_t)m + 2]));
+                const uint32_t id = cid ? (uint32_t)cid[m] : (uint32_t)m;
+                key[t] = ((uint64_t)__float_as_uint(d2) << 32) | id;
+            }
+            sort_asc_u64<KM>(key);
+            // a repeated id gives equal keys, now side by side
+#pragma unroll
+            for (int t = 0; t + 1 < KM; t++)
+                if (K > 0 || t + 1 < keff) rq = rq || key[t] == key[t + 1];
+        }
+        qflag[r] = rq ? 1 : 0;
+        if (!rq) {
+#pragma unroll
+            for (int t = 0; t < KM; t++)
+                if (K > 0 || t < keff) nbr[r * keff + t] = (int32_t)(uint32_t)key[t];
+        }
+    }
+}
+
+__global__ void k_check_ids(const int32_t *__restrict__ a, int64_t m, int64_t n, int32_t *err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (a[i] < 0 || a[i] >= n) atomicOr(err, 1);
+}
+
+__global__ void k_qpos_flags(int64_t n, const uint32_t *__restrict__ order,
+                             const int32_t *__restrict__ qflag, int32_t *f) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        f[p] = qflag[order[p]];
+}
+
+__global__ void k_qpos_write(int64_t n, const int32_t *__restrict__ f,
+                             const int32_t *__restrict__ fpos, int32_t *qlist) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        if (f[p]) qlist[fpos[p]] = (int32_t)p;
+}
+
 }  // namespace
 
 void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
@@ -291,4 +412,66 @@ void build_lex_view(ngs_ctx *c, GraphDev &g) {
     launch(c, "lex_view", dim3(grid_stride_blocks(c, ne, 256, 8)), dim3(256), 0, k_lex_view,
            (const uint32_t *)t1, (const uint32_t *)ktmp, (const uint32_t *)idx,
            (const int4 *)g.erec, ne, g.elo, g.ehi, g.erec_lex);
+}
+
+void refresh_map(ngs_ctx *c, int64_t n_old, const int32_t *role, int32_t *map_old,
+                 int32_t *src_new) {
+    if (n_old <= 0) return;
+    // new rows: the exclusive scan of the surviving old rows
+    int32_t *keep = ws<int32_t>(c, c->b_qflag, n_old + 1);
+    int32_t *pos = ws<int32_t>(c, c->b_qlist, n_old + 1);
+    const unsigned grid = grid_stride_blocks(c, n_old, 256, 8);
+    launch(c, "refresh_keep", dim3(grid), dim3(256), 0, k_refresh_keep, n_old, role, keep);
+    scan_i32(c, keep, pos, n_old);
+    launch(c, "refresh_map", dim3(grid), dim3(256), 0, k_refresh_map, n_old, role,
+           (const int32_t *)pos, map_old, src_new);
+}
+
+int64_t refresh_rows(ngs_ctx *c, int64_t n, int k_eff, int k_old, int64_t n_old,
+                     const int32_t *src_new, const int32_t *prev, const int32_t *map_old,
+                     const float *xyz, const int32_t *cid, const uint32_t *order, int32_t *nbr,
+                     int32_t *qlist) {
+    if (n <= 0) return 0;
+    int32_t *qflag = ws<int32_t>(c, c->b_qflag, n + 1);
+    int32_t *err = (int32_t *)ws<uint8_t>(c, c->b_status, 64) + 12;
+    NGS_CHECK_CUDA(cudaMemsetAsync(err, 0, 4, c->st));
+    const dim3 gr(grid_stride_blocks(c, n, 128, 16)), bl(128);
+#define REFRESH_LAUNCH(KT)                                                                      \
+    launch(c, "refresh_rows", gr, bl, 0, k_refresh_rows<KT>, n, k_eff, k_old, n_old, src_new,   \
+           prev, map_old, xyz, cid, nbr, qflag, err)
+    switch (k_eff) {
+    case 4: REFRESH_LAUNCH(4); break;
+    case 8: REFRESH_LAUNCH(8); break;
+    case 16: REFRESH_LAUNCH(16); break;
+    case 32: REFRESH_LAUNCH(32); break;
+    default: REFRESH_LAUNCH(0); break;
+    }
+#undef REFRESH_LAUNCH
+    get_small(c, (int32_t *)(c->h_pin + 6) + 1, err, 4);
+    // sorted positions of the rows to query
+    int32_t *f = ws<int32_t>(c, c->b_keep, n + 1);
+    int32_t *fpos = ws<int32_t>(c, c->b_pos, n + 1);
+    const unsigned grid = grid_stride_blocks(c, n, 256, 8);
+    launch(c, "qpos_flags", dim3(grid), dim3(256), 0, k_qpos_flags, n, order,
+           (const int32_t *)qflag, f);
+    scan_i32(c, f, fpos, n);
+    launch(c, "qpos_write", dim3(grid), dim3(256), 0, k_qpos_write, n, (const int32_t *)f,
+           (const int32_t *)fpos, qlist);
+    get_small(c, c->h_pin + 6, fpos + n, 4);
+    sync_stream(c);
+    if (((int32_t *)(c->h_pin + 6))[1])
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "refresh: a previous list entry is outside [0, %lld)",
+                 (long long)n_old);
+    return *(int32_t *)(c->h_pin + 6);
+}
+
+bool ids_in_range(ngs_ctx *c, const int32_t *a, int64_t m, int64_t n) {
+    if (m <= 0) return true;
+    int32_t *err = (int32_t *)ws<uint8_t>(c, c->b_status, 64) + 13;
+    NGS_CHECK_CUDA(cudaMemsetAsync(err, 0, 4, c->st));
+    launch(c, "check_ids", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0, k_check_ids, a, m,
+           n, err);
+    get_small(c, (int32_t *)(c->h_pin + 7), err, 4);
+    sync_stream(c);
+    return *(int32_t *)(c->h_pin + 7) == 0;
 }

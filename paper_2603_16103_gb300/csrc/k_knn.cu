@@ -377,12 +377,15 @@ __global__ void __launch_bounds__(KNN_BLOCK, 3)
                const uint32_t *__restrict__ sidx, const int32_t *__restrict__ ssid, int64_t n,
                const int32_t *__restrict__ Tall, const int32_t *__restrict__ lts,
                const int64_t *__restrict__ toff, const float *__restrict__ frames, int keff,
-               int out_by_cid, int block_min, int32_t *__restrict__ nbr) {
+               int out_by_cid, int block_min, const int32_t *__restrict__ qlist, int64_t nq,
+               int32_t *__restrict__ nbr) {
     __shared__ uint64_t queue_all[KNN_BLOCK / 32][KNN_QCAP][32];
     const int lane = threadIdx.x & 31;
     uint64_t(*queue)[32] = queue_all[threadIdx.x >> 5];
-    const int64_t qp = (int64_t)blockIdx.x * KNN_BLOCK + threadIdx.x;
-    const bool valid = qp < n;
+    // query t: sorted position t, or qlist[t] (ascending positions) when given
+    const int64_t qt = (int64_t)blockIdx.x * KNN_BLOCK + threadIdx.x;
+    const bool valid = qt < nq;
+    const int64_t qp = valid ? (qlist ? (int64_t)qlist[qt] : qt) : n;
     // this query's scene: its Morton frame and its cell table
     const int sc = (ssid && valid) ? ssid[qp] : 0;
     const int lt = lts[sc];
@@ -585,16 +588,19 @@ void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
     launch(c, "cell_count", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_cell_count,
            in.scode, in.ssid, n, (const int32_t *)dlt, (const int64_t *)doff, T);
     scan_i32(c, T, T, tlen);
-    const unsigned grid = blocks_for(n, KNN_BLOCK);
+    const int64_t nq = in.qlist ? in.nq : n;
+    const unsigned grid = blocks_for(nq, KNN_BLOCK);
     const int32_t *cT = T;
 #define KNN_LAUNCH(KM, NAME)                                                                   \
     launch(c, NAME, dim3(grid), dim3(KNN_BLOCK), 0, k_knn_grid<KM>, in.pts, in.scode, in.sidx,   \
            in.ssid, n, cT, (const int32_t *)dlt, (const int64_t *)doff, in.frames, k_eff,      \
-           in.out_by_cid, c->tune.knn_block_min, nbr)
-    if (k_eff <= 4) KNN_LAUNCH(4, "knn_k4");
-    else if (k_eff <= 8) KNN_LAUNCH(8, "knn_k8");
-    else if (k_eff <= 16) KNN_LAUNCH(16, "knn_k16");
-    else KNN_LAUNCH(32, "knn_k32");
+           in.out_by_cid, c->tune.knn_block_min, in.qlist, nq, nbr)
+    if (nq > 0) {
+        if (k_eff <= 4) KNN_LAUNCH(4, "knn_k4");
+        else if (k_eff <= 8) KNN_LAUNCH(8, "knn_k8");
+        else if (k_eff <= 16) KNN_LAUNCH(16, "knn_k16");
+        else KNN_LAUNCH(32, "knn_k32");
+    }
 #undef KNN_LAUNCH
     if (!in.out_by_cid) {
         // rows are internal indices; translate the neighbours' canonical ids

@@ -214,6 +214,7 @@ extern "C" void ngs_default_params(ngs_params *p) {
     p->prefilter = 1;
     p->eig_floor = 1e-30;
     p->cost_tol = 3e-5;
+    p->refresh_period = 1;
 }
 
 static int check_params(const ngs_params *p) {
@@ -225,6 +226,7 @@ static int check_params(const ngs_params *p) {
     if (p->fp64_policy < 0 || p->fp64_policy > 3) return 0;
     if (!(p->eig_floor > 0.0)) return 0;
     if (!(p->cost_tol >= 0.0 && p->cost_tol <= 1e-4)) return 0;
+    if (p->refresh_period < 1 || p->refresh_period > NGS_STATS_MAX_PASSES) return 0;
     return 1;
 }
 
@@ -268,7 +270,8 @@ static void release_all(ngs_ctx *c) {
                       &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
                       &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2,
                       &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc, &c->b_fp64list, &c->b_mstate, &c->b_offer, &c->b_order0,
-                      &c->b_tiebits, &c->b_tielist};
+                      &c->b_tiebits, &c->b_tielist, &c->b_prevnbr, &c->b_rmap, &c->b_rsrc, &c->b_qflag,
+                      &c->b_qlist};
     for (DevBuf *b : bufs) ws_free(c, *b);
     for (int k = 0; k < 5; k++) {
         ws_free(c, c->b_sA[k]);
@@ -431,6 +434,82 @@ static void graph_canonical(ngs_ctx *c, const ngs_splats *s) {
     c->g_xyz = s->xyz;
 }
 
+// canonical-mode graph of `s`, the result of merging `pairs` into a set of
+// n_old splats whose lists were prev_nbr (Sec. 3.4 local refresh)
+static int64_t graph_canonical_refresh(ngs_ctx *c, const ngs_splats *s, const int32_t *prev_nbr,
+                                       int64_t n_old, int k_old, const int32_t *pairs,
+                                       int64_t np) {
+    const int64_t n = s->n;
+    if (n_old < 0 || n_old > NGS_MAX_N || np < 0 || n != n_old - np)
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_build_graph_refresh: n=%lld is not n_old=%lld - n_pairs=%lld",
+                 (long long)n, (long long)n_old, (long long)np);
+    if (n_old >= 2 && (k_old < 1 || k_old > NGS_MAX_K || !prev_nbr))
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_build_graph_refresh: bad previous lists (k_old=%d)", k_old);
+    if (np > 0 && !pairs) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_build_graph_refresh: pairs is NULL");
+    GraphDev &g = c->g;
+    g = GraphDev{};
+    c->g_valid = false;
+    check_slots(n, c->prm.k, "ngs_build_graph_refresh");
+    g.n = n;
+    g.k_eff = n >= 2 ? k_eff_of(n, c->prm.k) : 0;
+    g.cid = nullptr;
+    int64_t nq = 0;
+    if (n >= 2) {
+        int32_t *prev = ws<int32_t>(c, c->b_prevnbr, n_old * k_old);
+        NGS_CHECK_CUDA(cudaMemcpyAsync(prev, prev_nbr, sizeof(int32_t) * n_old * k_old,
+                                       cudaMemcpyDeviceToDevice, c->st));
+        if (!ids_in_range(c, prev, n_old * k_old, n_old))
+            NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_build_graph_refresh: a list entry is outside [0, %lld)",
+                     (long long)n_old);
+        int32_t *role = ws<int32_t>(c, c->b_role, n_old);
+        if (!pairs_to_role(c, pairs, np, n_old, role))
+            NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_build_graph_refresh: pairs out of range, unordered or not disjoint");
+        int32_t *map_old = ws<int32_t>(c, c->b_rmap, n_old), *src = ws<int32_t>(c, c->b_rsrc, n);
+        refresh_map(c, n_old, role, map_old, src);
+        float *frame = ws<float>(c, c->b_frame, 8);
+        morton_frame(c, s->xyz, n, frame);
+        check_finite_frame(c, frame);
+        uint32_t *keys = ws<uint32_t>(c, c->b_codes, n), *vals = ws<uint32_t>(c, c->b_vals, n);
+        uint32_t *k2 = ws<uint32_t>(c, c->b_codes2, n), *v2 = ws<uint32_t>(c, c->b_vals2, n);
+        morton_keys(c, s->xyz, n, frame, keys, vals);
+        radix_sort_u32(c, keys, vals, k2, v2, n, 30);
+        float4 *pts = ws<float4>(c, c->b_pts, n);
+        gather_points(c, s->xyz, nullptr, vals, n, pts);
+        int32_t *nbr = ws<int32_t>(c, c->b_nbr, n * g.k_eff);
+        int32_t *qlist = ws<int32_t>(c, c->b_qlist, n + 1);
+        nq = refresh_rows(c, n, g.k_eff, k_old, n_old, src, prev, map_old, s->xyz, nullptr, vals,
+                          nbr, qlist);
+        const int64_t sn = n;
+        knn_search(c, KnnInput{pts, keys, vals, nullptr, frame, &sn, 1, n, 1, nullptr, qlist, nq},
+                   g.k_eff, nbr);
+        build_edges(c, nbr, g);
+        build_lex_view(c, g);
+    }
+    c->g_valid = true;
+    c->g_n = n;
+    c->g_k = g.k_eff;
+    c->g_edges = g.n_edges;
+    c->g_xyz = s->xyz;
+    return nq;
+}
+
+extern "C" int ngs_build_graph_refresh(ngs_ctx *c, const ngs_splats *s, const int32_t *prev_nbr,
+                                       int64_t n_old, int32_t k_old, const int32_t *pairs,
+                                       int64_t n_pairs, ngs_graph *out, int64_t *n_requeried) {
+    if (!c || !out) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    check_splats(s, "ngs_build_graph_refresh");
+    const int64_t nq = graph_canonical_refresh(c, s, prev_nbr, n_old, k_old, pairs, n_pairs);
+    if (n_requeried) *n_requeried = nq;
+    out->n = s->n;
+    out->k_eff = c->g.k_eff;
+    out->n_edges = c->g.n_edges;
+    out->nbr = (const int32_t *)c->b_nbr.p;
+    out->edge_lo = c->g.n_edges ? c->g.elo : nullptr;
+    out->edge_hi = c->g.n_edges ? c->g.ehi : nullptr;
+    API_END
+}
+
 extern "C" int ngs_build_graph(ngs_ctx *c, const ngs_splats *s, ngs_graph *out) {
     if (!c || !out) return NGS_ERR_INVALID_ARG;
     API_BEGIN
@@ -558,6 +637,7 @@ extern "C" int ngs_batch_simplify(ngs_ctx *c, ngs_splats *scenes, const int64_t 
         acc.matching_rounds += x.matching_rounds;
         acc.fp64_cost_edges += x.fp64_cost_edges;
         acc.near_tie_slots += x.near_tie_slots;
+        acc.requeried_rows += x.requeried_rows;
         acc.eig_floor_hits += x.eig_floor_hits;
     };
     for (int s = 0; s < nscenes; s++) {

@@ -125,6 +125,7 @@ struct ngs_ctx {
     DevBuf b_sC[5];              // third splat array set (several scenes at once)
     DevBuf b_fp64list;           // edges whose cost is evaluated in FP64
     DevBuf b_tiebits, b_tielist; // near-tie slot marks and the slots to recompute in FP64
+    DevBuf b_prevnbr, b_rmap, b_rsrc, b_qflag, b_qlist;  // local refresh: old lists, id maps, queries
     DevBuf b_mstate;             // device-side state of the captured matching rounds
     DevBuf b_offer;              // best offer per vertex (proposal form of the matching)
     DevBuf b_eng[32];            // per-scene tables and scratch of the multi-scene engine
@@ -152,6 +153,7 @@ struct ngs_ctx {
     // per-call counters
     int64_t fp64_edges = 0;
     int64_t tie_slots = 0;
+    int64_t requeried = 0;        // rows queried by the last graph build (refresh or full)
     int64_t floor_hits = 0;
     int32_t rounds = 0;
 };
@@ -238,6 +240,8 @@ struct KnnInput {
     int64_t n;
     int out_by_cid;
     const int32_t *cid;
+    const int32_t *qlist = nullptr;  // sorted positions to query (nullptr: all n)
+    int64_t nq = 0;                  // their count (with qlist)
 };
 int knn_table_level(int64_t n, int cells_per_point = 4);
 // neighbours per splat in a pass over n splats: min(max(1, k), n - 1)
@@ -270,6 +274,27 @@ void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr);
 void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g);
 // Lexicographic edge list (elo, ehi, lex_slot) of the graph, for the C ABI.
 void build_lex_view(ngs_ctx *c, GraphDev &g);
+
+// Local neighbourhood refresh (Sec. 3.4).  After a merge of n_old rows
+// (role: >= 0 partner for the lower member, -2 removed, -1 kept; surviving
+// rows keep their order), map_old[o] = new row of old row o (a removed row
+// takes its partner's) and src_new[r] = old row of a kept new row r, -1 for a
+// merged splat.  Uses b_qflag and b_qlist as scratch.
+void refresh_map(ngs_ctx *c, int64_t n_old, const int32_t *role, int32_t *map_old,
+                 int32_t *src_new);
+// Lists of the n new rows carried from prev (n_old x k_old, rows of the old
+// set): a kept row whose mapped list has k_eff distinct ids other than itself
+// gets them sorted by (FP32 d^2, canonical id), written as canonical ids
+// (cid[m], or m when cid is null); the others are flagged in qflag[r] for a
+// query.  Then qlist receives the sorted positions (order: sorted position
+// -> row) of the flagged rows; returns their count (host).  An old list entry
+// outside [0, n_old) fails with NGS_ERR_INVALID_ARG.
+// true when every a[i], i < m, lies in [0, n) (synchronises)
+bool ids_in_range(ngs_ctx *c, const int32_t *a, int64_t m, int64_t n);
+int64_t refresh_rows(ngs_ctx *c, int64_t n, int k_eff, int k_old, int64_t n_old,
+                     const int32_t *src_new, const int32_t *prev, const int32_t *map_old,
+                     const float *xyz, const int32_t *cid, const uint32_t *order, int32_t *nbr,
+                     int32_t *qlist);
 
 // ---------------------------------------------------------------- cost (k_cost.cu)
 // Cost of every edge into g.cost_slot (both slots of a mutual edge).  With
