@@ -86,7 +86,9 @@ class ngs_stats(ctypes.Structure):
 class ngs_tuning(ctypes.Structure):
     _fields_ = [("knn_block_min", ctypes.c_int32), ("cells_per_point", ctypes.c_int32),
                 ("cost_blocks_per_sm", ctypes.c_int32), ("match_method", ctypes.c_int32),
-                ("match_max_steps", ctypes.c_int32)]
+                ("match_max_steps", ctypes.c_int32), ("scan_method", ctypes.c_int32),
+                ("wait_budget_cycles", ctypes.c_int32),
+                ("wait_test_tile", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1,5 +1,6 @@
 // Device-wide primitives: exclusive scan, stable LSD radix sort and radix
-// select.  Deterministic three-phase designs (no inter-block waiting).
+// select.  The scan is single-pass (decoupled look-back) with bounded waits;
+// the sort and select are deterministic multi-kernel designs (no waiting).
 #include <cstring>
 
 #include "ngs_device.cuh"
@@ -116,6 +117,179 @@ __global__ void k_scan_apply(const int32_t *in, int32_t *out, int64_t n, const i
         ex += v[r];
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = part[gridDim.x];
+}
+
+// ---------------------------------------------------------------- single-pass scan
+// Exclusive scan in one kernel by decoupled look-back (Merrill and Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016): tile t
+// is block t (blocks start in index order, so a tile's predecessors are
+// running or done; a counter handing out tile ids costs a serialised atomic
+// per tile, a third of the time of the 134 M-entry cell-table scan); each
+// publishes its aggregate,
+// then walks back over its predecessors' published words (an aggregate, or
+// an inclusive prefix that ends the walk), publishes its own inclusive prefix
+// and writes its outputs.  Published word: flag (bits 63..62: 1 aggregate,
+// 2 inclusive) | 32-bit value.
+//
+// Every wait is bounded: a predecessor that has published nothing after
+// `budget` clock cycles has its tile summed from the inputs instead (then
+// read again: if it published meanwhile its word is used), and *err is set
+// (reported as NGS_ERR_TIMEOUT).  Results stay exact, also in place: a tile
+// writes outputs only after publishing, so inputs read while it has published
+// nothing are still inputs.  delay_tile (tests of the bounded wait) makes that
+// tile wait 4 budgets before publishing.
+constexpr int LB_THREADS = 256;
+constexpr int LB_ITEMS = 32;  // consecutive items per thread: 8192 per tile
+constexpr int LB_TILE = LB_THREADS * LB_ITEMS;
+constexpr int LB_WORDS = 4;   // predecessors read per lane and round: a window of 128
+constexpr uint64_t LB_AGG = 1ull << 62, LB_INC = 2ull << 62;
+
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// polling load: the word carries its own value, so no acquire ordering is needed
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Exclusive prefix of tile `tile` by warp 0.  Each round reads the 128
+// nearest unread predecessors (lane l the four at distances 4l .. 4l+3); the
+// nearest inclusive word ends the walk, and every nearer word must hold an
+// aggregate (else the round is read again); without an inclusive word the
+// 128 aggregates are added and the window moves back.  The inclusive
+// frontier so advances up to 128 tiles (1 M items) per L2 round trip.
+__device__ __forceinline__ int lookback_warp(const int32_t *in, int64_t n, int64_t tile,
+                                             uint64_t *status, long long budget, bool &late) {
+    const int lane = threadIdx.x & 31;
+    const long long t0 = clock64();
+    int prefix = 0;
+    for (int64_t p = tile - 1;;) {
+        uint64_t w[LB_WORDS];
+#pragma unroll
+        for (int k = 0; k < LB_WORDS; k++) {
+            const int64_t q = p - LB_WORDS * lane - k;
+            w[k] = q >= 0 ? ld_relaxed_u64(status + 1 + q) : LB_INC;  // before tile 0: 0
+        }
+        // nearest inclusive word of this lane (LB_WORDS: none), then of the warp
+        int lfi = LB_WORDS;
+#pragma unroll
+        for (int k = LB_WORDS - 1; k >= 0; k--)
+            if ((w[k] >> 62) == 2) lfi = k;
+        unsigned inc = __ballot_sync(FULL_MASK, lfi < LB_WORDS);
+        int fl = inc ? __ffs(inc) - 1 : 32;  // first lane holding one
+        // words needed: all of lanes before fl, those up to lfi in lane fl
+        auto needed = [&](int k) { return lane < fl || (lane == fl && k <= lfi); };
+        bool miss = false;
+#pragma unroll
+        for (int k = 0; k < LB_WORDS; k++) miss = miss || (needed(k) && (w[k] >> 62) == 0);
+        if (__any_sync(FULL_MASK, miss)) {
+            long long el = lane == 0 ? clock64() - t0 : 0;
+            el = __shfl_sync(FULL_MASK, el, 0);
+            if (!late && el <= budget) {  // wait: read the window again
+                __nanosleep(64);
+                continue;
+            }
+            late = true;
+            // out of budget: a needed tile that published nothing is summed
+            // from its inputs, unless it publishes meanwhile
+#pragma unroll
+            for (int k = 0; k < LB_WORDS; k++) {
+                if (needed(k) && (w[k] >> 62) == 0) {
+                    const int64_t q = p - LB_WORDS * lane - k;
+                    int s = 0;
+                    const int64_t e = (q + 1) * LB_TILE < n ? (q + 1) * LB_TILE : n;
+                    for (int64_t i = q * LB_TILE; i < e; i++) s += in[i];
+                    __threadfence();  // the inputs were read before the word is read again
+                    const uint64_t w2 = ld_relaxed_u64(status + 1 + q);
+                    w[k] = (w2 >> 62) ? w2 : (LB_AGG | (uint32_t)s);
+                }
+            }
+            lfi = LB_WORDS;
+#pragma unroll
+            for (int k = LB_WORDS - 1; k >= 0; k--)
+                if ((w[k] >> 62) == 2) lfi = k;
+            inc = __ballot_sync(FULL_MASK, lfi < LB_WORDS);
+            fl = inc ? __ffs(inc) - 1 : 32;
+        }
+        int v = 0;
+#pragma unroll
+        for (int k = 0; k < LB_WORDS; k++)
+            if (needed(k)) v += (int)(uint32_t)w[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+        prefix += v;
+        if (inc) return prefix;
+        p -= 32 * LB_WORDS;
+    }
+}
+
+__global__ void __launch_bounds__(LB_THREADS)
+    k_scan_lookback(const int32_t *in, int32_t *out, int64_t n, int64_t ntiles,
+                    uint64_t *status /* [1 + t] tile t */, long long budget,
+                    int64_t delay_tile, volatile int32_t *err) {
+    __shared__ int s_prefix;
+    const int64_t tile = blockIdx.x;
+    const int64_t i0 = tile * LB_TILE + (int64_t)threadIdx.x * LB_ITEMS;
+    const bool full = i0 + LB_ITEMS <= n;
+    int v[LB_ITEMS];
+    if (full && ((((uintptr_t)in) & 15) == 0)) {
+#pragma unroll
+        for (int r = 0; r < LB_ITEMS / 4; r++) {
+            const int4 a = *(const int4 *)(in + i0 + 4 * r);
+            v[4 * r] = a.x; v[4 * r + 1] = a.y; v[4 * r + 2] = a.z; v[4 * r + 3] = a.w;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < LB_ITEMS; r++) v[r] = i0 + r < n ? in[i0 + r] : 0;
+    }
+    int sum = 0;
+#pragma unroll
+    for (int r = 0; r < LB_ITEMS; r++) sum += v[r];
+    int tot;
+    const int ex = block_excl_scan(sum, &tot);
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0 && tile == delay_tile) {
+            const long long t0 = clock64();
+            while (clock64() - t0 < 4 * budget) {
+            }
+        }
+        __syncwarp();
+        int prefix = 0;
+        if (tile == 0) {
+            if (threadIdx.x == 0) st_release_u64(status + 1, LB_INC | (uint32_t)tot);
+        } else {
+            if (threadIdx.x == 0) st_release_u64(status + 1 + tile, LB_AGG | (uint32_t)tot);
+            bool late = false;
+            prefix = lookback_warp(in, n, tile, status, budget, late);
+            if (threadIdx.x == 0) {
+                if (late) *err = NGS_ERR_TIMEOUT;
+                st_release_u64(status + 1 + tile, LB_INC | (uint32_t)(prefix + tot));
+            }
+        }
+        if (threadIdx.x == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    int o = s_prefix + ex;
+    if (full && ((((uintptr_t)out) & 15) == 0)) {
+#pragma unroll
+        for (int r = 0; r < LB_ITEMS / 4; r++) {
+            int4 q;
+            q.x = o; o += v[4 * r];
+            q.y = o; o += v[4 * r + 1];
+            q.z = o; o += v[4 * r + 2];
+            q.w = o; o += v[4 * r + 3];
+            *(int4 *)(out + i0 + 4 * r) = q;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < LB_ITEMS; r++) {
+            if (i0 + r < n) out[i0 + r] = o;
+            o += v[r];
+        }
+    }
+    if (tile == ntiles - 1 && threadIdx.x == 0) out[n] = s_prefix + tot;
 }
 
 // ---------------------------------------------------------------- small uploads
@@ -279,6 +453,16 @@ __global__ void k_sel_out(const SelState *s, K *out) {
 }  // namespace
 
 void scan_i32(ngs_ctx *c, const int32_t *in, int32_t *out, int64_t n) {
+    if (c->tune.scan_method == 1 && c->err_word) {
+        // single pass; the tile words start at zero
+        int64_t nt = (n + LB_TILE - 1) / LB_TILE;
+        if (nt < 1) nt = 1;
+        uint64_t *st = ws<uint64_t>(c, c->b_scan_part, nt + 1);
+        NGS_CHECK_CUDA(cudaMemsetAsync(st, 0, sizeof(uint64_t) * (nt + 1), c->st));
+        launch(c, "scan", dim3((unsigned)nt), dim3(LB_THREADS), 0, k_scan_lookback, in, out, n, nt,
+               st, (long long)c->tune.wait_budget_cycles, (int64_t)c->tune.wait_test_tile, c->err_word);
+        return;
+    }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb < 1) nb = 1;
     int32_t *part = ws<int32_t>(c, c->b_scan_part, nb + 1);

@@ -116,7 +116,15 @@ static void ws_free(ngs_ctx *c, DevBuf &b) {
     b.bytes = 0;
 }
 
-void sync_stream(ngs_ctx *c) { NGS_CHECK_CUDA(cudaStreamSynchronize(c->st)); }
+void sync_stream(ngs_ctx *c) {
+    NGS_CHECK_CUDA(cudaStreamSynchronize(c->st));
+    if (c->h_pin && c->err_word == (volatile int32_t *)(c->h_pin + 8) && *c->err_word) {
+        const int e = *c->err_word;
+        *c->err_word = 0;
+        NGS_FAIL(e, "a device-wide wait ran past ngs_tuning.wait_budget_cycles (the waiting blocks "
+                    "completed the work without it)");
+    }
+}
 
 // ---------------------------------------------------------------- profiling
 int prof_slot(ngs_ctx *c, const char *name) {
@@ -252,6 +260,7 @@ extern "C" int ngs_create(ngs_ctx **out, const ngs_params *p, void *stream) {
     NGS_CHECK_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
     NGS_CHECK_CUDA(cudaMallocHost(&c->h_pin, 1 << 16));
     memset(c->h_pin, 0, 1 << 16);
+    c->err_word = (volatile int32_t *)(c->h_pin + 8);
     *out = c;
     }
     catch (const NgsError &e) {
@@ -765,6 +774,9 @@ extern "C" void ngs_default_tuning(ngs_tuning *t) {
     t->cost_blocks_per_sm = d.cost_blocks_per_sm;
     t->match_method = d.match_method;
     t->match_max_steps = d.match_max_steps;
+    t->scan_method = d.scan_method;
+    t->wait_budget_cycles = d.wait_budget_cycles;
+    t->wait_test_tile = d.wait_test_tile;
 }
 
 extern "C" int ngs_get_tuning(ngs_ctx *c, ngs_tuning *t) {
@@ -774,6 +786,9 @@ extern "C" int ngs_get_tuning(ngs_ctx *c, ngs_tuning *t) {
     t->cost_blocks_per_sm = c->tune.cost_blocks_per_sm;
     t->match_method = c->tune.match_method;
     t->match_max_steps = c->tune.match_max_steps;
+    t->scan_method = c->tune.scan_method;
+    t->wait_budget_cycles = c->tune.wait_budget_cycles;
+    t->wait_test_tile = c->tune.wait_test_tile;
     return NGS_OK;
 }
 
@@ -783,7 +798,8 @@ extern "C" int ngs_set_tuning(ngs_ctx *c, const ngs_tuning *t) {
     if (t->knn_block_min < 16 || t->knn_block_min > 1024 ||
         !(cpp == 1 || cpp == 2 || cpp == 4 || cpp == 8) || t->cost_blocks_per_sm < 1 ||
         t->cost_blocks_per_sm > 64 || t->match_method < 0 || t->match_method > 2 ||
-        t->match_max_steps < 1 || t->match_max_steps > (1 << 30)) {
+        t->match_max_steps < 1 || t->match_max_steps > (1 << 30) || t->wait_budget_cycles < 1 ||
+        t->wait_test_tile < -1 || t->scan_method < 0 || t->scan_method > 1) {
         ngs_set_error("ngs_set_tuning: field out of range");
         return NGS_ERR_INVALID_ARG;
     }
@@ -792,6 +808,9 @@ extern "C" int ngs_set_tuning(ngs_ctx *c, const ngs_tuning *t) {
     c->tune.cost_blocks_per_sm = t->cost_blocks_per_sm;
     c->tune.match_method = t->match_method;
     c->tune.match_max_steps = t->match_max_steps;
+    c->tune.scan_method = t->scan_method;
+    c->tune.wait_budget_cycles = t->wait_budget_cycles;
+    c->tune.wait_test_tile = t->wait_test_tile;
     return NGS_OK;
 }
 

@@ -96,6 +96,9 @@ struct Tuning {
     int cost_blocks_per_sm = 8;  // edge-cost grid, 256-thread blocks per SM
     int match_method = 2;        // 2 proposals, 1 rounds in a CUDA graph, 0 host-driven rounds
     int match_max_steps = 1 << 16;  // proposal steps per thread before the round form takes over
+    int scan_method = 1;         // 1: single pass (decoupled look-back); 0: reduce, partials, apply
+    int wait_budget_cycles = 2000000000;  // a device-wide wait gives up after this many cycles
+    int wait_test_tile = -1;     // tests of the bounded waits: this scan tile publishes late
 };
 
 struct ngs_ctx {
@@ -132,6 +135,10 @@ struct ngs_ctx {
 
     // pinned host scratch
     int64_t *h_pin = nullptr;
+    // where a kernel records that a bounded device-wide wait ran out (pinned
+    // host memory, h_pin + 8, checked by sync_stream; a device word in the
+    // allocation-free entry point); nullptr: the scan uses no waits
+    volatile int32_t *err_word = nullptr;
 
     // instrumentation
     bool prof = false;

@@ -349,3 +349,46 @@ def test_simplify_host_equals_device(ngs, F):
     assert hs.n == ds.n
     for a, b in zip(hs.numpy(), ds.numpy()):
         assert np.array_equal(a, b)
+
+
+def test_scan_wait_budget_runs_out_and_ctx_stays_usable(ngs):
+    """The single-pass scan's look-back waits are bounded: with one tile made
+    to publish 4 budgets late, its successor gives up, completes the prefix
+    from the inputs, and the call returns NGS_ERR_TIMEOUT without a hang; the
+    same ctx then runs normally and matches a fresh one bit for bit."""
+    scene = small_scene(200000, seed=12)
+    target = O.target_count(scene.n, 0.5)
+    c = ngs.Context()
+    try:
+        c.set_tuning(scan_method=1, wait_budget_cycles=2000, wait_test_tile=1)
+        with pytest.raises(ngs.NgsError) as e:
+            c.simplify(ngs.DeviceSplats.from_numpy(scene), target)
+        assert e.value.code == ngs.NGS_ERR_TIMEOUT
+        d = ngs.ngs_default_tuning()
+        c.set_tuning(wait_budget_cycles=d.wait_budget_cycles, wait_test_tile=-1)   # scan_method stays 1
+        ds = ngs.DeviceSplats.from_numpy(scene)
+        c.simplify(ds, target)
+        got = ds.numpy()
+    finally:
+        c.close()
+    with ngs.Context() as f:
+        ref = ngs.DeviceSplats.from_numpy(scene)
+        f.simplify(ref, target)
+        for a, b in zip(got, ref.numpy()):
+            assert np.array_equal(a, b)
+
+
+def test_scan_methods_give_identical_results(ngs):
+    """The single-pass scan (decoupled look-back) and the three-kernel scan
+    are exact: the whole loop gives the same splats with either."""
+    scene = small_scene(150000, seed=14, kind="patch")
+    target = O.target_count(scene.n, 0.1)
+    outs = []
+    for method in (0, 1):
+        with ngs.Context() as c:
+            c.set_tuning(scan_method=method)
+            ds = ngs.DeviceSplats.from_numpy(scene)
+            c.simplify(ds, target)
+            outs.append(ds.numpy())
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
