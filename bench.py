@@ -645,7 +645,7 @@ def main():
     roofs = [r for r in (roofline(p) for p in sorted(prof, key=lambda p: -p[2])) if r]
     kernels = [{"name": p[0], "launches_per_step": p[1] / args.steps,
                 "ms_per_step": p[2] / args.steps, "share": p[2] / kern_total}
-               for p in sorted(prof, key=lambda p: -p[2])[:12]]
+               for p in sorted(prof, key=lambda p: -p[2])[:40]]
 
     # ---- end to end through the host API (pinned host buffers)
     e2e = None

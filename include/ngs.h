@@ -367,10 +367,10 @@ typedef struct {
     int32_t match_max_steps;     /* proposals a thread may make before the pass
                                     falls back to the round form (1..2^30), default
                                     65536 */
-    int32_t scan_method;         /* exclusive scans: 1: one kernel with decoupled
-                                    look-back (bounded waits below; default);
-                                    0: reduce, partials, apply (three kernels, no
-                                    inter-block waiting) */
+    int32_t scan_method;         /* exclusive scans: 0: reduce, partials, apply (three
+                                    kernels, no inter-block waiting; default);
+                                    1: one kernel with decoupled look-back (bounded
+                                    waits below); the same results */
     int32_t wait_budget_cycles;  /* device-wide waits (the single-pass scan's look-back)
                                     give up after this many SM clock cycles (>= 1,
                                     default 2e9, about 1 s): the waiting block then

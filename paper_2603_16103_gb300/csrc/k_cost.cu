@@ -51,12 +51,13 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
     R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
 }
 
-// y = R diag(s) R^T z
-__device__ __forceinline__ void sym_sqrt_apply(const float *R, const float *s, const float *z,
+// y = R diag(s) R^T z, with s = 1 / invs (the same rounding as a stored s)
+__device__ __forceinline__ void sym_sqrt_apply(const float *R, const float *invs, const float *z,
                                                float *y) {
     float t[3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) t[k] = s[k] * (R[k] * z[0] + R[3 + k] * z[1] + R[6 + k] * z[2]);
+    for (int k = 0; k < 3; k++)
+        t[k] = (1.0f / invs[k]) * (R[k] * z[0] + R[3 + k] * z[1] + R[6 + k] * z[2]);
 #pragma unroll
     for (int a = 0; a < 3; a++) y[a] = R[3 * a] * t[0] + R[3 * a + 1] * t[1] + R[3 * a + 2] * t[2];
 }
@@ -445,7 +446,9 @@ __global__ void __launch_bounds__(256, 3)
                              fmaxf(fmaxf(invs_j[0], invs_j[1]), invs_j[2]);
             flag = flag || ri < 1e-3f || rj < 1e-3f;
         }
-        float dgeo, eg = 0.f;  // eg: running error estimate of dgeo (times S)
+        // running error estimate of dgeo:
+        //   (eg + u gw + e_gmul gsum) / S + e_const
+        float dgeo, eg = 0.f, gw = 0.f, gsum = 0.f, e_const = 0.f, e_gmul = 0.f;
         bool tie = false;      // mode 1: u_s within FP32 reach of pi
         if (!flag) {
             // a_c = log sqrt(det Sm / det Sigma_c) as a product of O(1) ratios
@@ -456,14 +459,16 @@ __global__ void __launch_bounds__(256, 3)
             // ratios Sm_kk / L_kk^2), the c terms, log w, the inverse scales
             const float r1 = Sm[3] * il[1] * il[1], r2 = Sm[5] * il[2] * il[2];
             const float rmax = fmaxf(1.f, fmaxf(r1, r2));
-            // (one bound for both c terms)
-            const float e_c = U32 * (12.f + 4.f * (r1 + r2) + fabsf(lpi) + fabsf(ai) +
-                                     fabsf(lpj) + fabsf(aj));
-            const float e_ld = 2.f * U32 * (fabsf(i0.w) + fabsf(j0.w));
-            const float dm = absmax3(d);
-            const float imx_i = fmaxf(fmaxf(invs_i[0], invs_i[1]), invs_i[2]);
-            const float imx_j = fmaxf(fmaxf(invs_j[0], invs_j[1]), invs_j[2]);
-            const float ilmx = fmaxf(fmaxf(il[0], il[1]), il[2]);
+            // terms of the estimate that do not depend on the sample, added
+            // after the loop: the c terms (one bound for both; every sample
+            // weighs them by pi + (1 - pi) = 1), and the log-weight
+            // difference through pi (1 - pi), which multiplies |g|
+            e_const = U32 * (12.f + 4.f * (r1 + r2) + fabsf(lpi) + fabsf(ai) + fabsf(lpj) + fabsf(aj));
+            if (MODE != 1) {
+                const float e_ld = 2.f * U32 * (fabsf(i0.w) + fabsf(j0.w));
+                e_const += 2.f * ppd * e_ld;
+                e_gmul = ppd * e_ld;
+            }
             float acc = 0.f;
             const bool est = tol > 0.f;
             for (int s = 0; s < S; s++) {
@@ -476,8 +481,8 @@ __global__ void __launch_bounds__(256, 3)
                 float gi, e_gi = 0.f;
                 {
                     float yi[3];
-                    sym_sqrt_apply(Rm, si, z, yi);
-                    const float vi = dm + absmax3(yi);
+                    sym_sqrt_apply(Rm, invs_i, z, yi);
+                    const float vi = absmax3(d) + absmax3(yi);
                     float v1[3] = {d[0] + yi[0], d[1] + yi[1], d[2] + yi[2]};
                     float v2[3] = {pj * d[0] + yi[0], pj * d[1] + yi[1], pj * d[2] + yi[2]};
                     const float qj = maha_splat(Rn, invs_j, v1);
@@ -487,19 +492,21 @@ __global__ void __launch_bounds__(256, 3)
                     const float l1 = lse2w(A1, B1, wa1);
                     gi = l1 + (MODE == 2 ? 1.5f : 0.5f * qmi);
                     if (est) {
+                        const float imx_j = fmaxf(fmaxf(invs_j[0], invs_j[1]), invs_j[2]);
                         const float e_qj = 8.f * U32 * sqrt_nn(qj) * vi * imx_j + 2.f * U32 * qj;
+                        const float ilmx = fmaxf(fmaxf(il[0], il[1]), il[2]);
                         const float e_qm = MODE == 2 ? 0.f : 8.f * U32 * sqrt_nn(qmi) * vi * ilmx + 4.f * U32 * rmax * qmi;
                         // rounding of the log-sum-exp inputs, weighted, is within
                         // |l| + 1 (l = lse >= the larger input), its output within |l|
-                        e_gi = e_c + (1.f - wa1) * 0.5f * e_qj + 0.5f * e_qm + U32 * (2.f * fabsf(l1) + 1.f + qmi);
+                        e_gi = (1.f - wa1) * 0.5f * e_qj + 0.5f * e_qm + U32 * (2.f * fabsf(l1) + 1.f + qmi);
                     }
                 }
                 // x = x_j
                 float gj, e_gj = 0.f;
                 {
                     float yj[3];
-                    sym_sqrt_apply(Rn, sj, z, yj);
-                    const float vj = dm + absmax3(yj);
+                    sym_sqrt_apply(Rn, invs_j, z, yj);
+                    const float vj = absmax3(d) + absmax3(yj);
                     float w1[3] = {yj[0] - d[0], yj[1] - d[1], yj[2] - d[2]};
                     float w2[3] = {yj[0] - pi * d[0], yj[1] - pi * d[1], yj[2] - pi * d[2]};
                     const float qi = maha_splat(Rm, invs_i, w1);
@@ -509,18 +516,23 @@ __global__ void __launch_bounds__(256, 3)
                     const float l2 = lse2w(A2, B2, wa2);
                     gj = l2 + (MODE == 2 ? 1.5f : 0.5f * qmj);
                     if (est) {
+                        const float imx_i = fmaxf(fmaxf(invs_i[0], invs_i[1]), invs_i[2]);
                         const float e_qi = 8.f * U32 * sqrt_nn(qi) * vj * imx_i + 2.f * U32 * qi;
+                        const float ilmx = fmaxf(fmaxf(il[0], il[1]), il[2]);
                         const float e_qm = MODE == 2 ? 0.f : 8.f * U32 * sqrt_nn(qmj) * vj * ilmx + 4.f * U32 * rmax * qmj;
-                        e_gj = e_c + wa2 * 0.5f * e_qi + 0.5f * e_qm + U32 * (2.f * fabsf(l2) + 1.f + qmj);
+                        e_gj = wa2 * 0.5f * e_qi + 0.5f * e_qm + U32 * (2.f * fabsf(l2) + 1.f + qmj);
                     }
                 }
                 acc += MODE != 1 ? (pi * gi + pj * gj) : (us[s] < pi ? gi : gj);
                 if (est) {
                     if (MODE != 1) {
-                        eg += pi * e_gi + pj * e_gj + ppd * e_ld * (fabsf(gi) + fabsf(gj) + 2.f) +
-                              U32 * (pi * fabsf(gi) + pj * fabsf(gj));
+                        eg += pi * e_gi + pj * e_gj;
+                        gw += pi * fabsf(gi) + pj * fabsf(gj);
+                        gsum += fabsf(gi) + fabsf(gj);
                     } else {
-                        eg += us[s] < pi ? e_gi + U32 * fabsf(gi) : e_gj + U32 * fabsf(gj);
+                        const bool first = us[s] < pi;
+                        eg += first ? e_gi : e_gj;
+                        gw += fabsf(first ? gi : gj);
                         tie = tie || fabsf(us[s] - pi) <= 1e-5f;
                     }
                 }
@@ -533,7 +545,8 @@ __global__ void __launch_bounds__(256, 3)
         if (tol > 0.f && !flag) {
             // keep the FP32 cost only when twice its error estimate is within
             // tol max(|C|, 1); D_app: F/4 + 4 roundings per lane sum, 16 in all
-            const float E = lg * (eg / (float)S) + la * 16.f * U32 * dapp + U32 * fabsf(c);
+            const float E = lg * ((eg + U32 * gw + e_gmul * gsum) / (float)S + e_const) + la * 16.f * U32 * dapp +
+                            U32 * fabsf(c);
             flag = tie || !(2.f * E <= tol * fmaxf(fabsf(c), 1.f));
         }
         // flagged edges go to the FP64 list (one atomic per warp)

@@ -96,7 +96,7 @@ struct Tuning {
     int cost_blocks_per_sm = 8;  // edge-cost grid, 256-thread blocks per SM
     int match_method = 2;        // 2 proposals, 1 rounds in a CUDA graph, 0 host-driven rounds
     int match_max_steps = 1 << 16;  // proposal steps per thread before the round form takes over
-    int scan_method = 1;         // 1: single pass (decoupled look-back); 0: reduce, partials, apply
+    int scan_method = 0;         // 0: reduce, partials, apply; 1: single pass (decoupled look-back)
     int wait_budget_cycles = 2000000000;  // a device-wide wait gives up after this many cycles
     int wait_test_tile = -1;     // tests of the bounded waits: this scan tile publishes late
 };

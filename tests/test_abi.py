@@ -95,7 +95,7 @@ def test_default_tuning_host_only():
     from paper_2603_16103_gb300 import binding
     t = binding.ngs_default_tuning()
     assert (t.knn_block_min, t.cells_per_point, t.cost_blocks_per_sm, t.match_method,
-            t.match_max_steps, t.scan_method, t.wait_test_tile) == (64, 4, 8, 2, 65536, 1, -1)
+            t.match_max_steps, t.scan_method, t.wait_test_tile) == (64, 4, 8, 2, 65536, 0, -1)
 
 
 def test_product_path_does_not_import_the_oracle():
