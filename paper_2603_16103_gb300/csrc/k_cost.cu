@@ -87,11 +87,7 @@ __global__ void k_prep(const float *__restrict__ xyz, const float *__restrict__ 
     }
 }
 
-__device__ __forceinline__ float lse2(float a, float b) {
-    float m = fmaxf(a, b);
-    return m + log1pf(__expf(-fabsf(a - b)));
-}
-// the same value, and wa = the weight of a in it (exp(a - lse))
+// log(e^a + e^b), and wa = the weight of a in it (e^(a - lse))
 __device__ __forceinline__ float lse2w(float a, float b, float &wa) {
     const float m = fmaxf(a, b);
     const float e = __expf(-fabsf(a - b));
@@ -295,8 +291,8 @@ __global__ void __launch_bounds__(256, 3)
                 float lg, float la, int policy, const float *__restrict__ xyz,
                 const float *__restrict__ ls, const float *__restrict__ rot,
                 const float *__restrict__ logit, float *__restrict__ cost_slot,
-                float *__restrict__ cost_out, unsigned long long *fp64_count,
-                int32_t *__restrict__ fp64_list, float tol) {
+                float *__restrict__ revcost, float *__restrict__ cost_out,
+                unsigned long long *fp64_count, int32_t *__restrict__ fp64_list, float tol) {
     const int lane = threadIdx.x & 31;
     const int F4 = F >> 2;
     const float4 *sh4 = (const float4 *)sh;
@@ -402,6 +398,7 @@ __global__ void __launch_bounds__(256, 3)
             const float c = lg * dgeo + la * dapp;
             cost_slot[sl] = c;
             if (er.w >= 0) cost_slot[er.w] = c;
+        else if (er.w <= -2) revcost[-2 - er.w] = c;
             if (cost_out) cost_out[e] = c;
             continue;
         }
@@ -562,6 +559,7 @@ __global__ void __launch_bounds__(256, 3)
         if (flag) continue;
         cost_slot[sl] = c;
         if (er.w >= 0) cost_slot[er.w] = c;
+        else if (er.w <= -2) revcost[-2 - er.w] = c;
         if (cost_out) cost_out[e] = c;
     }
 }
@@ -574,7 +572,8 @@ __global__ void k_edge_cost64(const int32_t *__restrict__ list, const unsigned l
                               const float *__restrict__ xyz, const float *__restrict__ ls,
                               const float *__restrict__ rot, const float *__restrict__ logit,
                               const float *__restrict__ sh, int F,
-                              float *__restrict__ cost_slot, float *__restrict__ cost_out) {
+                              float *__restrict__ cost_slot, float *__restrict__ revcost,
+                              float *__restrict__ cost_out) {
     const int64_t cnt = (int64_t)*count;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -583,6 +582,7 @@ __global__ void k_edge_cost64(const int32_t *__restrict__ list, const unsigned l
         const float c = cost_fp64(xyz, ls, rot, logit, sh, F, er.y, er.z, S, zs, us, mode, lg, la);
         cost_slot[er.x] = c;
         if (er.w >= 0) cost_slot[er.w] = c;
+        else if (er.w <= -2) revcost[-2 - er.w] = c;
         if (cost_out) cost_out[e] = c;
     }
 }
@@ -624,7 +624,7 @@ __device__ __forceinline__ void sort_asc_u32(uint32_t (&a)[N]) {
 // Exact pairwise marks of one vertex (any slot width, any number of in-slots).
 template <int KM>
 __device__ __forceinline__ void near_ties_pairwise(const float (&c)[KM], int64_t base, int32_t r0,
-                                                   int32_t r1, const float *__restrict__ cost_slot,
+                                                   int32_t r1, const float *__restrict__ revcost,
                                                    const int32_t *__restrict__ rev, float tol,
                                                    uint32_t *bits, int32_t *list,
                                                    unsigned long long *cnt) {
@@ -635,8 +635,7 @@ __device__ __forceinline__ void near_ties_pairwise(const float (&c)[KM], int64_t
         for (int b = a + 1; b < KM; b++)
             if (near_tie(c[a], c[b], tol)) own |= (1u << a) | (1u << b);
     for (int32_t r = r0; r < r1; r++) {
-        const int32_t sr = __ldg(rev + r);
-        const float cr = __ldg(cost_slot + sr);
+        const float cr = __ldg(revcost + r);
         bool hit = false;
 #pragma unroll
         for (int a = 0; a < KM; a++)
@@ -645,13 +644,12 @@ __device__ __forceinline__ void near_ties_pairwise(const float (&c)[KM], int64_t
                 hit = true;
             }
         for (int32_t r2 = r + 1; r2 < r1; r2++) {
-            const int32_t s2 = __ldg(rev + r2);
-            if (near_tie(cr, __ldg(cost_slot + s2), tol)) {
+            if (near_tie(cr, __ldg(revcost + r2), tol)) {
                 hit = true;
-                mark_slot(bits, s2, list, cnt);
+                mark_slot(bits, __ldg(rev + r2), list, cnt);
             }
         }
-        if (hit) mark_slot(bits, sr, list, cnt);
+        if (hit) mark_slot(bits, __ldg(rev + r), list, cnt);
     }
     while (own) {
         const int a = __ffs(own) - 1;
@@ -683,7 +681,8 @@ template <int K>
 __global__ void __launch_bounds__(128)
     k_near_ties(int64_t n, int kk, const float *__restrict__ cost_slot,
                 const int32_t *__restrict__ rev_ptr, const int32_t *__restrict__ rev,
-                float tol, uint32_t *bits, int32_t *list, unsigned long long *cnt) {
+                const float *__restrict__ revcost, float tol, uint32_t *bits, int32_t *list,
+                unsigned long long *cnt) {
     constexpr int KM = K > 0 ? K : NGS_MAX_K;
     constexpr int KS = K > 0 ? K : 1;
     constexpr uint32_t IMASK = K > 0 ? (uint32_t)K - 1u : 0u;
@@ -702,7 +701,7 @@ __global__ void __launch_bounds__(128)
             float c[KM];
 #pragma unroll
             for (int t = 0; t < KM; t++) c[t] = t < kk ? cost_slot[base + t] : NAN;
-            near_ties_pairwise<KM>(c, base, r0, r1, cost_slot, rev, tol, bits, list, cnt);
+            near_ties_pairwise<KM>(c, base, r0, r1, revcost, rev, tol, bits, list, cnt);
             continue;
         }
         uint32_t key[KS];
@@ -730,8 +729,7 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int a = 0; a < KS; a++) skey[a][threadIdx.x] = key[a];
             for (int32_t r = r0; r < r1; r++) {
-                const int32_t sr = __ldg(rev + r);
-                const float cr = __ldg(cost_slot + sr);
+                const float cr = __ldg(revcost + r);
                 const uint32_t kr = cost_order_bits(cr);
                 // first sorted own key above kr, then its two neighbours
                 int lo = 0, hi = KS;
@@ -749,13 +747,12 @@ __global__ void __launch_bounds__(128)
                     if (close(key_value<KS>(ka), cr)) { own |= 1u << (ka & IMASK); hit = true; }
                 }
                 for (int32_t r2 = r + 1; r2 < r1; r2++) {
-                    const int32_t s2 = __ldg(rev + r2);
-                    if (near_tie(cr, __ldg(cost_slot + s2), tol)) {
+                    if (near_tie(cr, __ldg(revcost + r2), tol)) {
                         hit = true;
-                        mark_slot(bits, s2, list, cnt);
+                        mark_slot(bits, __ldg(rev + r2), list, cnt);
                     }
                 }
-                if (hit) mark_slot(bits, sr, list, cnt);
+                if (hit) mark_slot(bits, __ldg(rev + r), list, cnt);
             }
         }
         while (own) {
@@ -778,7 +775,9 @@ __global__ void k_refine_costs(const int32_t *__restrict__ list, const unsigned 
                                int mode, float lg, float la, const float *__restrict__ xyz,
                                const float *__restrict__ ls, const float *__restrict__ rot,
                                const float *__restrict__ logit, const float *__restrict__ sh, int F,
-                               float *cost_slot, const int32_t *__restrict__ elo,
+                               float *cost_slot, const int32_t *__restrict__ rev_ptr,
+                               const int32_t *__restrict__ rev, float *revcost,
+                               const int32_t *__restrict__ elo,
                                const int32_t *__restrict__ ehi, int64_t m, float *cost_out) {
     const int64_t cnt = (int64_t)*count;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
@@ -789,8 +788,15 @@ __global__ void k_refine_costs(const int32_t *__restrict__ list, const unsigned 
         const int64_t lo = ca < cb ? a : b, hi = ca < cb ? b : a;
         const float c = cost_fp64(xyz, ls, rot, logit, sh, F, lo, hi, S, zs, us, mode, lg, la);
         cost_slot[s] = c;
+        bool mutual = false;
         for (int q = 0; q < kk; q++)  // the mirror slot of a mutual edge
-            if (nbr[b * kk + q] == (int32_t)a) cost_slot[b * kk + q] = c;
+            if (nbr[b * kk + q] == (int32_t)a) {
+                cost_slot[b * kk + q] = c;
+                mutual = true;
+            }
+        if (!mutual)  // the in-edge entry of b
+            for (int32_t r = rev_ptr[b]; r < rev_ptr[b + 1]; r++)
+                if (rev[r] == s) revcost[r] = c;
         if (cost_out) {
             // lexicographic position of (lo, hi) in canonical ids
             const uint64_t key = ((uint64_t)(ca < cb ? ca : cb) << 32) | (ca < cb ? cb : ca);
@@ -806,13 +812,15 @@ __global__ void k_refine_costs(const int32_t *__restrict__ list, const unsigned 
 }
 
 __global__ void k_costs_to_slots(const int4 *__restrict__ erec_lex, int64_t m,
-                                 const float *__restrict__ cost, float *cost_slot) {
+                                 const float *__restrict__ cost, float *cost_slot,
+                                 float *revcost) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int4 r = erec_lex[e];
         const float c = cost[e];
         cost_slot[r.x] = c;
         if (r.w >= 0) cost_slot[r.w] = c;
+        else if (r.w <= -2) revcost[-2 - r.w] = c;
     }
 }
 
@@ -850,13 +858,13 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
     launch(c, "edge_cost", dim3(grid_stride_blocks(c, m, 256, c->tune.cost_blocks_per_sm)), dim3(256), 0,
            kern, er, m, (const float *)rec, (const float *)s.sh, s.F, (const float *)zs, us, S, lg,
            la, c->prm.fp64_policy, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
-           (const float *)s.logit, g.cost_slot, cout, cnt, list, tol);
+           (const float *)s.logit, g.cost_slot, g.revcost, cout, cnt, list, tol);
     // the flagged edges (few) in FP64; the grid covers the worst case, threads
     // past the device count exit at once
     launch(c, "edge_cost64", dim3(grid_stride_blocks(c, m, 128, 2)), dim3(128), 0, k_edge_cost64,
            (const int32_t *)list, (const unsigned long long *)cnt, er, (const float *)zs, us, S, mode,
            lg, la, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
-           (const float *)s.logit, (const float *)s.sh, s.F, g.cost_slot, cout);
+           (const float *)s.logit, (const float *)s.sh, s.F, g.cost_slot, g.revcost, cout);
     if (tol > 0.f) {
         const int64_t ns = g.n * g.k_eff;
         uint32_t *bits = ws<uint32_t>(c, c->b_tiebits, (ns + 31) / 32);
@@ -866,12 +874,14 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
         auto nt = g.k_eff == 4 ? k_near_ties<4> : g.k_eff == 8 ? k_near_ties<8>
                 : g.k_eff == 16 ? k_near_ties<16> : g.k_eff == 32 ? k_near_ties<32> : k_near_ties<0>;
         launch(c, "near_ties", gr, bl, 0, nt, g.n, g.k_eff, (const float *)g.cost_slot,
-               (const int32_t *)g.rev_ptr, (const int32_t *)g.rev, tol, bits, tl, cnt + 1);
+               (const int32_t *)g.rev_ptr, (const int32_t *)g.rev, (const float *)g.revcost, tol,
+               bits, tl, cnt + 1);
         launch(c, "refine_costs", dim3(grid_stride_blocks(c, ns, 128, 4)), dim3(128), 0,
                k_refine_costs, (const int32_t *)tl, (const unsigned long long *)(cnt + 1), g.k_eff,
                g.nbr, g.cid, (const float *)zs, us, S, mode, lg, la, (const float *)s.xyz,
                (const float *)s.ls, (const float *)s.rot, (const float *)s.logit,
-               (const float *)s.sh, s.F, g.cost_slot, lex ? (const int32_t *)g.elo : nullptr,
+               (const float *)s.sh, s.F, g.cost_slot, (const int32_t *)g.rev_ptr,
+               (const int32_t *)g.rev, g.revcost, lex ? (const int32_t *)g.elo : nullptr,
                lex ? (const int32_t *)g.ehi : nullptr, m, cout);
     }
     get_small(c, c->h_pin + 1, cnt, 8);
@@ -882,5 +892,5 @@ void costs_to_slots(ngs_ctx *c, GraphDev &g, const float *cost_lex) {
     const int64_t m = g.n_edges;
     if (m <= 0) return;
     launch(c, "costs_to_slots", dim3(grid_stride_blocks(c, m, 256, 8)), dim3(256), 0,
-           k_costs_to_slots, (const int4 *)g.erec_lex, m, cost_lex, g.cost_slot);
+           k_costs_to_slots, (const int4 *)g.erec_lex, m, cost_lex, g.cost_slot, g.revcost);
 }

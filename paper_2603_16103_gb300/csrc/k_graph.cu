@@ -8,10 +8,12 @@
 //     k_slot_classify_rows.)
 //   * Each undirected edge has exactly one canonical slot: a non-mutual slot,
 //     or the mutual slot whose row has the lower canonical id.  erec[] lists
-//     one record (slot, lo row, hi row, mirror slot) per canonical slot in
-//     slot order; |E| = their number.
+//     one record (slot, lo row, hi row, mirror) per canonical slot in slot
+//     order; |E| = their number.  mirror: the partner slot of a mutual edge,
+//     else -2 - r with r the edge's position in rev[].
 //   * rev[] lists, per vertex u, the non-mutual slots that point at u (its
-//     in-edges not already in its own list).
+//     in-edges not already in its own list); revcost[] holds their costs
+//     in the same order, so a vertex reads its in-edge costs contiguously.
 // So the incident edges of v are its k slots plus its rev entries, each once,
 // and costs live per slot (mirrored for mutual edges).  No sort is needed on
 // the simplification path; the C-ABI view additionally sorts the canonical
@@ -71,12 +73,16 @@ __global__ void k_slot_fill(const int32_t *__restrict__ nbr, int64_t n, int k,
          s += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = nbr[s];
         const int32_t mr = mirror[s];
+        int32_t rp = -1;
+        if (mr < 0) {
+            rp = rev_ptr[u] + atomicAdd(&revfill[u], 1);
+            rev[rp] = (int32_t)s;
+        }
         if (canon[s]) {
             const int32_t v = (int32_t)(s / k);
             const bool vlo = cid_of(cid, v) < cid_of(cid, u);
-            erec[epos[s]] = make_int4((int32_t)s, vlo ? v : u, vlo ? u : v, mr);
+            erec[epos[s]] = make_int4((int32_t)s, vlo ? v : u, vlo ? u : v, mr >= 0 ? mr : -2 - rp);
         }
-        if (mr < 0) rev[rev_ptr[u] + atomicAdd(&revfill[u], 1)] = (int32_t)s;
     }
 }
 
@@ -179,7 +185,8 @@ __global__ void k_slot_fill_rows(const int32_t *__restrict__ nbr, int64_t n, int
         if (canon) {
             const int32_t pos = rp + __popc(cm & ((1u << lane) - 1u) & ~((1u << first) - 1u));
             const bool vlo = c >= 0 || c == -1;
-            erec[pos] = make_int4((int32_t)s, vlo ? v : u, vlo ? u : v, c >= 0 ? c : -1);
+            // 4th field: the mirror slot of a mutual edge, else -2 - (in-slot position)
+            erec[pos] = make_int4((int32_t)s, vlo ? v : u, vlo ? u : v, c >= 0 ? c : -2 - (rv + at));
         }
         if (in_rev) rev[rv + at] = (int32_t)s;
     }
@@ -378,6 +385,7 @@ void build_edges(ngs_ctx *c, const int32_t *nbr, GraphDev &g) {
     const int64_t nrev = ((int32_t *)c->h_pin)[1];
     g.erec = ws<int4>(c, c->b_elo, g.n_edges);
     g.rev = ws<int32_t>(c, c->b_upc, nrev);
+    g.revcost = ws<float>(c, c->b_revcost, nrev);
     if (rows)
         launch(c, "slot_fill", dim3(grid_stride_blocks(c, m, 256, 16)), dim3(256), 0,
                k_slot_fill_rows, nbr, n, k, (const int32_t *)g.mirror,

@@ -79,9 +79,10 @@ struct GraphDev {
     const int32_t *cid;     // canonical ids (nullptr = identity)
     const int32_t *nbr;     // n*k directed neighbours (slot s = v*k + t)
     int32_t *mirror;        // n*k partner slot of a mutual edge, else -1 (row form: slot code)
-    int4 *erec;             // |E| edge records (slot, lo row, hi row, mirror slot)
+    int4 *erec;             // |E| edge records (slot, lo row, hi row, mirror slot or -2 - rev position)
     int32_t *rev_ptr;       // n+1 offsets into rev
     int32_t *rev;           // non-mutual slots pointing at each vertex
+    float *revcost;         // cost of each rev entry (the same order)
     float *cost_slot;       // n*k cost of the edge of each slot
     int64_t n_edges;        // |E| (host copy)
     int32_t *elo, *ehi;     // C-ABI view: lexicographic edges (canonical ids)
@@ -128,6 +129,7 @@ struct ngs_ctx {
     DevBuf b_sC[5];              // third splat array set (several scenes at once)
     DevBuf b_fp64list;           // edges whose cost is evaluated in FP64
     DevBuf b_tiebits, b_tielist; // near-tie slot marks and the slots to recompute in FP64
+    DevBuf b_revcost;            // in-edge costs in rev order
     DevBuf b_prevnbr, b_rmap, b_rsrc, b_qflag, b_qlist;  // local refresh: old lists, id maps, queries
     DevBuf b_mstate;             // device-side state of the captured matching rounds
     DevBuf b_offer;              // best offer per vertex (proposal form of the matching)
