@@ -123,18 +123,61 @@ __global__ void k_gather_pts(const float *__restrict__ xyz, const int32_t *__res
 }
 
 // ---------------------------------------------------------------- cell table
-// Per-cell point counts at the table level; an exclusive scan turns them into
-// T[c] = first sorted position of cell c (T[ncell] = n).
-__global__ void k_cell_count(const uint32_t *__restrict__ scode, const int32_t *__restrict__ ssid,
-                             int64_t n, const int32_t *__restrict__ lts,
-                             const int64_t *__restrict__ toff, int32_t *cnt) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+// T[c] = first sorted position whose global cell id is >= c, for every c in
+// [0, tlen] (T[tlen] = n): the start of cell c and the end of cell c - 1.
+// The global cell id of position p is toff[scene] + (Morton code >> the
+// scene's level shift); it does not decrease along the sorted positions.
+// Position p (0 < p < n) therefore owns the cells (id(p-1), id(p)]: all of
+// them start at p; position 0 owns [0, id(0)] and a virtual position n owns
+// (id(n-1), tlen].  Each position writes its run; a run longer than 64 cells
+// (the empty space between surfaces) is cut into chunks of at most 16384
+// cells that whole blocks write, so one huge gap does not serialise on one
+// block.  Every cell is written once: no zeroing, no atomics per point and no
+// scan over the (mostly empty) table.
+constexpr int CELL_RUN_DIRECT = 64;
+constexpr int CELL_CHUNK = 16384;
+
+__device__ __forceinline__ int64_t gcell_at(const uint32_t *__restrict__ scode,
+                                            const int32_t *__restrict__ ssid,
+                                            const int32_t *__restrict__ lts,
+                                            const int64_t *__restrict__ toff, int64_t p) {
+    const int sc = ssid ? ssid[p] : 0;
+    return toff[sc] + (int64_t)(scode[p] >> (3 * (10 - lts[sc])));
+}
+
+// chunk record: x = first cell, y = (cell count << 32) | position
+__global__ void k_cell_runs(const uint32_t *__restrict__ scode, const int32_t *__restrict__ ssid,
+                            int64_t n, const int32_t *__restrict__ lts,
+                            const int64_t *__restrict__ toff, int64_t tlen, int32_t *T,
+                            longlong2 *chunks, unsigned long long *nchunk) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const int sc = ssid ? ssid[p] : 0;
-        const int64_t c = toff[sc] + (int64_t)(scode[p] >> (3 * (10 - lts[sc])));
-        // one atomic per run of equal cells inside the warp
-        const unsigned peers = __match_any_sync(__activemask(), (unsigned long long)c);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[c], __popc(peers));
+        const int64_t hi = p < n ? gcell_at(scode, ssid, lts, toff, p) : tlen;
+        const int64_t lo = p > 0 ? gcell_at(scode, ssid, lts, toff, p - 1) + 1 : 0;
+        const int64_t len = hi - lo + 1;
+        if (len <= CELL_RUN_DIRECT) {
+            for (int64_t c = lo; c <= hi; c++) T[c] = (int32_t)p;
+        } else {
+            const int64_t m = (len + CELL_CHUNK - 1) / CELL_CHUNK;
+            const unsigned long long at = atomicAdd(nchunk, (unsigned long long)m);
+            for (int64_t j = 0; j < m; j++) {
+                const int64_t c0 = lo + j * CELL_CHUNK;
+                const int64_t cl = len - j * CELL_CHUNK < CELL_CHUNK ? len - j * CELL_CHUNK : CELL_CHUNK;
+                chunks[at + j] = make_longlong2(c0, (long long)(((uint64_t)cl << 32) | (uint32_t)p));
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cell_chunks(const longlong2 *__restrict__ chunks,
+                                                     const unsigned long long *__restrict__ nchunk,
+                                                     int32_t *T) {
+    const int64_t cnt = (int64_t)*nchunk;
+    for (int64_t r = blockIdx.x; r < cnt; r += gridDim.x) {
+        const longlong2 ch = chunks[r];
+        const int cl = (int)((uint64_t)ch.y >> 32);
+        const int32_t v = (int32_t)(uint32_t)ch.y;
+        for (int i = threadIdx.x; i < cl; i += blockDim.x) T[ch.x + i] = v;
     }
 }
 
@@ -584,10 +627,17 @@ void knn_search(ngs_ctx *c, const KnnInput &in, int k_eff, int32_t *nbr) {
     put_small(c, dlt, hlt, 4 * (size_t)S);
     put_small(c, doff, hoff, 8 * (size_t)(S + 1));
     int32_t *T = ws<int32_t>(c, c->b_nodes, tlen + 1);
-    NGS_CHECK_CUDA(cudaMemsetAsync(T, 0, sizeof(int32_t) * tlen, c->st));
-    launch(c, "cell_count", dim3(grid_stride_blocks(c, n, 256, 8)), dim3(256), 0, k_cell_count,
-           in.scode, in.ssid, n, (const int32_t *)dlt, (const int64_t *)doff, T);
-    scan_i32(c, T, T, tlen);
+    // chunks: at most one per position plus one per CELL_CHUNK cells
+    const int64_t max_chunks = n + 2 + tlen / CELL_CHUNK;
+    uint8_t *lr = ws<uint8_t>(c, c->b_knnlong, 16 * (max_chunks + 1));
+    unsigned long long *nchunk = (unsigned long long *)lr;
+    longlong2 *chunks = (longlong2 *)(lr + 16);
+    NGS_CHECK_CUDA(cudaMemsetAsync(nchunk, 0, 8, c->st));
+    launch(c, "cell_runs", dim3(grid_stride_blocks(c, n + 1, 256, 8)), dim3(256), 0, k_cell_runs,
+           in.scode, in.ssid, n, (const int32_t *)dlt, (const int64_t *)doff, tlen, T, chunks,
+           nchunk);
+    launch(c, "cell_chunks", dim3((unsigned)c->num_sms * 8), dim3(256), 0, k_cell_chunks,
+           (const longlong2 *)chunks, (const unsigned long long *)nchunk, T);
     const int64_t nq = in.qlist ? in.nq : n;
     const unsigned grid = blocks_for(nq, KNN_BLOCK);
     const int32_t *cT = T;

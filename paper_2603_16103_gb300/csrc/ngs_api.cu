@@ -279,7 +279,7 @@ static void release_all(ngs_ctx *c) {
                       &c->b_pos, &c->b_flag, &c->b_scan_part, &c->b_status, &c->b_misc, &c->b_cid,
                       &c->b_cid2, &c->b_cflag, &c->b_cscan, &c->b_pairs, &c->b_partner, &c->b_nbr2,
                       &c->b_lexrec, &c->b_sel2, &c->b_cflag2, &c->b_knnsc, &c->b_fp64list, &c->b_mstate, &c->b_offer, &c->b_order0,
-                      &c->b_tiebits, &c->b_tielist, &c->b_revcost, &c->b_prevnbr, &c->b_rmap, &c->b_rsrc, &c->b_qflag,
+                      &c->b_tiebits, &c->b_tielist, &c->b_revcost, &c->b_knnlong, &c->b_prevnbr, &c->b_rmap, &c->b_rsrc, &c->b_qflag,
                       &c->b_qlist};
     for (DevBuf *b : bufs) ws_free(c, *b);
     for (int k = 0; k < 5; k++) {

@@ -130,6 +130,7 @@ struct ngs_ctx {
     DevBuf b_fp64list;           // edges whose cost is evaluated in FP64
     DevBuf b_tiebits, b_tielist; // near-tie slot marks and the slots to recompute in FP64
     DevBuf b_revcost;            // in-edge costs in rev order
+    DevBuf b_knnlong;            // long runs of empty cells of the kNN cell table
     DevBuf b_prevnbr, b_rmap, b_rsrc, b_qflag, b_qlist;  // local refresh: old lists, id maps, queries
     DevBuf b_mstate;             // device-side state of the captured matching rounds
     DevBuf b_offer;              // best offer per vertex (proposal form of the matching)

@@ -42,8 +42,9 @@ constexpr size_t kHist = align256(4 * (256 * kTiles + 1));
 constexpr size_t kPart = align256(4 * (kCells / 2048 + 2));
 constexpr size_t kPts = align256(16 * kMaxN);
 constexpr size_t kTable = align256(4 * (kCells + 2));
+constexpr size_t kLong = align256(16 * (kMaxN + 3 + kCells / 16384));  // chunks of empty cells
 constexpr size_t kKnnSc = align256(16 * 2 + 256);
-constexpr size_t kScratchBytes = kAcc + kFrame + 4 * kKeys + kHist + kPart + kPts + kTable + kKnnSc;
+constexpr size_t kScratchBytes = kAcc + kFrame + 4 * kKeys + kHist + kPart + kPts + kTable + kKnnSc + kLong;
 
 __device__ __align__(256) unsigned char g_knn_scratch[kScratchBytes];
 
@@ -148,6 +149,7 @@ extern "C" int ngs_knn_noalloc(const float *xyz, int64_t n, int32_t k, int32_t *
     bind(c.b_pts, cur, kPts);
     bind(c.b_nodes, cur, kTable);
     bind(c.b_knnsc, cur, kKnnSc);
+    bind(c.b_knnlong, cur, kLong);
     int rc = NGS_OK;
     try {
         const int ke = (int)(k < n - 1 ? k : n - 1);
@@ -172,7 +174,7 @@ extern "C" int ngs_knn_noalloc(const float *xyz, int64_t n, int32_t k, int32_t *
     }
     // the slices belong to the static array: detach them before the stack ctx goes away
     DevBuf *bound[] = {&c.b_bbox, &c.b_frame, &c.b_codes, &c.b_vals, &c.b_codes2,
-                       &c.b_vals2, &c.b_hist, &c.b_scan_part, &c.b_pts, &c.b_nodes, &c.b_knnsc};
+                       &c.b_vals2, &c.b_hist, &c.b_scan_part, &c.b_pts, &c.b_nodes, &c.b_knnsc, &c.b_knnlong};
     for (DevBuf *b : bound) *b = DevBuf{};
     return rc;
 }
