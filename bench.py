@@ -63,17 +63,20 @@ ALGO = {
     "suitor": ("hbm", lambda n, e, p: n * (16 * 8 + 8 + 8), "GB/s"),
 }
 
-# DRAM traffic per launch from ncu captures on the first pass of the
-# 1,000,000-splat patch scene (999,792 splats after the pre-filter), in bytes
-# per splat of the pass.
+# DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of pass 0 of the 1,000,000-splat patch scene
+# (999,792 splats after the pre-filter), in bytes per splat of the pass.
+# Writes that are still in L2 when a kernel ends (the 64-byte cost records,
+# the kept rows) are not in its figure.
 NCU_TRAFFIC_PER_SPLAT = {
-    "knn_k16": 42.44,        # 42.43 MB
-    "edge_cost": 480.5,      # 480.37 MB
-    "slot_classify": 104.8,  # 104.76 MB
-    "slot_fill": 250.6,      # 250.57 MB
-    "merge": 335.6,          # 335.52 MB
-    "match_scan": 154.8,     # 154.81 MB, round 0
-    "suitor": 170.9,         # 170.88 MB
+    "knn_k16": 41.42,        # 41.41 MB
+    "slot_classify": 102.93, # 102.91 MB
+    "slot_fill": 247.47,     # 247.42 MB
+    "cost_prep": 48.90,      # 48.89 MB
+    "edge_cost": 501.71,     # 501.61 MB
+    "suitor": 168.11,        # 168.07 MB
+    "merge": 331.69,         # 331.62 MB
+    "copy_kept": 32.72,      # 32.71 MB
 }
 
 
