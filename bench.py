@@ -95,6 +95,8 @@ def parse():
                     help="splats of the one-thread oracle timing (0: skip it)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched, serving and cost-variant measurements")
+    ap.add_argument("--forms", default="batched,serving,cost_variants,precision,refresh",
+                    help="comma-separated forms to measure")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--no-autotune", action="store_true",
@@ -293,23 +295,41 @@ def batched_form(B, torch, synth, args):
     stream = torch.cuda.current_stream()
     res = {}
     outs = {}
+    def counts(sts):
+        return [sum(st[k] for st in sts) for k in ("gpu_launches", "host_syncs", "passes")]
+
     for mode in ("batched", "sequential"):
         if mode == "batched":
-            run = lambda: ctx.batch_simplify(work, targets)["gpu_launches"]
+            run = lambda: counts([ctx.batch_simplify(work, targets)])
         else:
-            run = lambda: sum(ctx.simplify(w, t)["gpu_launches"] for w, t in zip(work, targets))
-        times, launches = [], 0
+            run = lambda: counts([ctx.simplify(w, t) for w, t in zip(work, targets)])
+        times, tot = [], [0, 0, 0]
         for it in range(1 + args.form_steps):
             restore()
             torch.cuda.synchronize()
-            ms, nl = _timed(torch, stream, run)
+            ms, cnt = _timed(torch, stream, run)
             if it >= 1:
                 times.append(ms)
-                launches += nl
+                tot = [a + b for a, b in zip(tot, cnt)]
         outs[mode] = [tuple(a[:w.n].clone() for a in w.tensors()) for w in work]
+        # one more run with CUDA events around every launch: the gap between the
+        # call's wall time and the sum of its kernel times bounds what the host
+        # round trips (count read-backs, launch gaps) cost
+        B.ngs_profile_reset(ctx.handle)
+        B.ngs_profile_enable(ctx.handle, True)
+        restore()
+        torch.cuda.synchronize()
+        prof_wall, _ = _timed(torch, stream, run)
+        B.ngs_profile_enable(ctx.handle, False)
+        kern_ms = sum(p[2] for p in B.ngs_profile(ctx.handle))
         ms = statistics.median(times)
+        launches, syncs, passes = (x / args.form_steps for x in tot)
         res[mode] = {"value": total / (ms / 1e3), "unit": UNIT, "ms": ms,
-                     "gpu_launches": launches / args.form_steps}
+                     "gpu_launches": launches, "host_syncs": syncs, "passes": passes,
+                     "gpu_launches_per_pass": launches / max(passes, 1),
+                     "host_syncs_per_pass": syncs / max(passes, 1),
+                     "profiled_run": {"wall_ms": prof_wall, "kernel_ms": kern_ms,
+                                      "gap_ms": prof_wall - kern_ms}}
     identical = all(all(torch.equal(a, b) for a, b in zip(x, y))
                     for x, y in zip(outs["batched"], outs["sequential"]))
     ctx.close()
@@ -676,11 +696,17 @@ def main():
 
     forms = {}
     if not args.no_forms and ws == 1:  # the forms are measured on one GPU
-        forms["batched"] = batched_form(B, torch, synth, args)
-        forms["serving"] = serving_form(B, torch, synth, args)
-        forms["cost_variants"] = cost_variants_form(B, torch, pristine, target, tuning, args)
-        forms["precision"] = precision_form(B, torch, pristine, target, tuning, args)
-        forms["refresh"] = refresh_form(B, torch, pristine, target, tuning, args)
+        which = set(args.forms.split(","))
+        if "batched" in which:
+            forms["batched"] = batched_form(B, torch, synth, args)
+        if "serving" in which:
+            forms["serving"] = serving_form(B, torch, synth, args)
+        if "cost_variants" in which:
+            forms["cost_variants"] = cost_variants_form(B, torch, pristine, target, tuning, args)
+        if "precision" in which:
+            forms["precision"] = precision_form(B, torch, pristine, target, tuning, args)
+        if "refresh" in which:
+            forms["refresh"] = refresh_form(B, torch, pristine, target, tuning, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -700,6 +726,7 @@ def main():
                        "cost_tol": ctx.params.cost_tol,
                        "fp64_cost_edges": stats["fp64_cost_edges"],
                        "near_tie_slots": stats["near_tie_slots"],
+                       "host_syncs": stats["host_syncs"],
                        "l2": "inputs (1.42 GB) larger than L2, restored from a pristine "
                              "device copy before every step",
                        "parallelism": f"replicas x{ws}"},

@@ -164,6 +164,9 @@ typedef struct {
                              * (a mutual edge may count twice)             */
     int64_t requeried_rows; /* kNN queries over all passes (a rebuild queries
                              * every row; a local refresh only some)       */
+    int64_t host_syncs;     /* times the host waited for the ctx stream in
+                             * this call (counts read back to size the next
+                             * launches)                                    */
 } ngs_stats;
 
 /* ---- lifecycle ---- */

@@ -69,7 +69,7 @@ class ngs_stats(ctypes.Structure):
                 ("pass_pairs", ctypes.c_int64 * NGS_STATS_MAX_PASSES),
                 ("fp64_cost_edges", ctypes.c_int64), ("eig_floor_hits", ctypes.c_int64),
                 ("gpu_launches", ctypes.c_int64), ("near_tie_slots", ctypes.c_int64),
-                ("requeried_rows", ctypes.c_int64)]
+                ("requeried_rows", ctypes.c_int64), ("host_syncs", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         p = self.passes
@@ -80,7 +80,8 @@ class ngs_stats(ctypes.Structure):
                 "pass_pairs": list(self.pass_pairs[:p]),
                 "fp64_cost_edges": self.fp64_cost_edges,
                 "eig_floor_hits": self.eig_floor_hits, "gpu_launches": self.gpu_launches,
-                "near_tie_slots": self.near_tie_slots, "requeried_rows": self.requeried_rows}
+                "near_tie_slots": self.near_tie_slots, "requeried_rows": self.requeried_rows,
+                "host_syncs": self.host_syncs}
 
 
 class ngs_tuning(ctypes.Structure):

@@ -426,7 +426,7 @@ void download(ngs_ctx *c, T *h, const T *d, size_t count) {
 
 void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, ngs_stats *st) {
     const int F = sc[0].sh_dim;
-    const int64_t launches0 = c->launches;
+    const int64_t launches0 = c->launches, syncs0 = c->syncs;
     c->fp64_edges = 0;
     c->floor_hits = 0;
     std::vector<int64_t> in0(S + 1, 0);
@@ -653,6 +653,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
     // p % refresh_period != 0 the previous lists are carried through the merge
     const int R = multi ? 1 : c->prm.refresh_period;
     bool have_prev = false;
+    bool rows_sorted = true;  // A in (scene, Morton code) order (no merge yet)
     int64_t n_prev = 0;
     int k_prev = 0;
     while (pass < c->prm.max_passes) {
@@ -679,17 +680,24 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         launch(c, "morton", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0, k_morton_rows,
                (const float *)A.xyz, multi ? (const int32_t *)sidA : (const int32_t *)nullptr, nA,
                (const float *)frames, (const int32_t *)nullptr, pk, pv);
+        // Until the first merge the rows are still in the order of the initial
+        // sort, (scene, Morton code) under the same frames: the sorts below
+        // would return the identity, so they are skipped.
         if (multi) {
-            NGS_CHECK_CUDA(cudaMemcpyAsync(code_row, pk, 4 * nA, cudaMemcpyDeviceToDevice, c->st));
-            radix_sort_u32(c, pk, pv, pk2, pv2, nA, 30);
             uint32_t *sk = ws<uint32_t>(c, c->b_eng[E_SSID], nA);
-            launch(c, "gather_sid", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0,
-                   k_gather_sid, (const int32_t *)sidA, (const uint32_t *)pv, nA, S,
-                   (const int32_t *)nullptr, sk);
-            radix_sort_u32(c, sk, pv, pk2, pv2, nA, bits_for(S));
-            gather_u32(c, code_row, pv, nA, pk);
+            if (rows_sorted) {
+                NGS_CHECK_CUDA(cudaMemcpyAsync(sk, sidA, 4 * nA, cudaMemcpyDeviceToDevice, c->st));
+            } else {
+                NGS_CHECK_CUDA(cudaMemcpyAsync(code_row, pk, 4 * nA, cudaMemcpyDeviceToDevice, c->st));
+                radix_sort_u32(c, pk, pv, pk2, pv2, nA, 30);
+                launch(c, "gather_sid", dim3(grid_stride_blocks(c, nA, 256, 8)), dim3(256), 0,
+                       k_gather_sid, (const int32_t *)sidA, (const uint32_t *)pv, nA, S,
+                       (const int32_t *)nullptr, sk);
+                radix_sort_u32(c, sk, pv, pk2, pv2, nA, bits_for(S));
+                gather_u32(c, code_row, pv, nA, pk);
+            }
             ssid = (int32_t *)sk;
-        } else {
+        } else if (!rows_sorted) {
             radix_sort_u32(c, pk, pv, pk2, pv2, nA, 30);
         }
         float4 *pts = ws<float4>(c, c->b_pts, nA);
@@ -795,6 +803,7 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
             partner_to_role(c, partner, cidA, nA, role);
             B.n = nA;
             const int64_t nn = merge_compact(c, A, role, B, cidA, cidB);
+            rows_sorted = false;
             if (R > 1 && pass % R != 0) {
                 // the next pass carries these lists: keep them and the row maps
                 refresh_map(c, nA, role, ws<int32_t>(c, c->b_rmap, nA), ws<int32_t>(c, c->b_rsrc, nn));
@@ -835,5 +844,6 @@ void engine_simplify(ngs_ctx *c, ngs_splats *sc, const int64_t *targets, int S, 
         st->requeried_rows = requeried_total;
         st->eig_floor_hits = c->floor_hits;
         st->gpu_launches = c->launches - launches0;
+        st->host_syncs = c->syncs - syncs0;
     }
 }

@@ -500,7 +500,10 @@ static bool match_rounds_graph(ngs_ctx *c, const GraphDev &g, int32_t *mate, int
     if (le == cudaSuccess) {
         k_get_state<<<1, 32, 0, c->st>>>(hstate, stt);
         se = cudaGetLastError();
-        if (se == cudaSuccess) se = cudaStreamSynchronize(c->st);
+        if (se == cudaSuccess) {
+            c->syncs++;
+            se = cudaStreamSynchronize(c->st);
+        }
     }
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);

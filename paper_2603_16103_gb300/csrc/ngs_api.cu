@@ -117,6 +117,7 @@ static void ws_free(ngs_ctx *c, DevBuf &b) {
 }
 
 void sync_stream(ngs_ctx *c) {
+    c->syncs++;
     NGS_CHECK_CUDA(cudaStreamSynchronize(c->st));
     if (c->h_pin && c->err_word == (volatile int32_t *)(c->h_pin + 8) && *c->err_word) {
         const int e = *c->err_word;
@@ -632,7 +633,7 @@ extern "C" int ngs_batch_simplify(ngs_ctx *c, ngs_splats *scenes, const int64_t 
     ngs_stats acc, one;
     memset(&acc, 0, sizeof(acc));
     const int ke = k_eff_of(INT64_MAX, c->prm.k);
-    const int64_t l0 = c->launches;
+    const int64_t l0 = c->launches, s0 = c->syncs;
     auto add = [&](const ngs_stats &x) {
         acc.n_input += x.n_input;
         acc.n_filtered += x.n_filtered;
@@ -665,6 +666,7 @@ extern "C" int ngs_batch_simplify(ngs_ctx *c, ngs_splats *scenes, const int64_t 
         for (size_t i = 0; i < big.size(); i++) scenes[big_idx[i]].n = big[i].n;
     }
     acc.gpu_launches = c->launches - l0;
+    acc.host_syncs = c->syncs - s0;
     if (st) *st = acc;
     API_END
 }

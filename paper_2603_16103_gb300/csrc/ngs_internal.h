@@ -149,6 +149,7 @@ struct ngs_ctx {
     std::vector<PendingEv> pending;
     std::vector<cudaEvent_t> ev_free;
     int64_t launches = 0;
+    int64_t syncs = 0;            // host waits on the ctx stream
     int64_t ws_bytes = 0;         // device workspace currently held
     bool ws_fixed = false;        // workspaces are bound to fixed memory: growing one fails
     cudaStream_t cap_st = nullptr;  // private stream the graph is captured on
