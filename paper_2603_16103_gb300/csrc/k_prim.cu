@@ -331,48 +331,87 @@ __global__ void k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shif
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Stable scatter: items of a tile are ranked in index order (round-major,
-// then thread) using warp match + per-warp digit counts.
-__global__ void k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
-                             int shift, const int32_t *__restrict__ offs, int64_t ntiles) {
-    __shared__ int run[256];
-    __shared__ int wc[RS_THREADS / 32][256];
+// Stable scatter of one tile.  Warp w ranks the tile's items
+// [256 w, 256 w + 256) in index order, 32 at a time, against its own digit
+// counts (warp match, no block barrier); one prefix per digit over the warps
+// then places every item in shared memory in digit order, and the tile is
+// written out from there, consecutive threads at consecutive positions of a
+// digit's run.  offs is the exclusive scan of the digit-major tile counts; a
+// tile's count of digit d is the difference of two adjacent entries.
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                 uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
+                 const int32_t *__restrict__ offs, int64_t ntiles) {
+    constexpr int NW = RS_THREADS / 32;
+    static_assert(RS_ITEMS * 32 * NW == RS_TILE, "a warp ranks RS_ITEMS rows of 32 items");
+    __shared__ uint32_t sk[RS_TILE], sv[RS_TILE];
+    __shared__ int wh[NW][256];  // per-warp digit counts, then per-warp start positions
+    __shared__ int gb[256];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    run[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const int tcount = (int)(n - base < RS_TILE ? n - base : RS_TILE);
+#pragma unroll
+    for (int w = 0; w < NW; w++) wh[w][tid] = 0;
+    int lo;
+    {
+        const int64_t at = (int64_t)tid * ntiles + blockIdx.x;
+        const int g = offs[at];
+        const int cnt = offs[at + 1] - g;
+        int tot;
+        lo = block_excl_scan(cnt, &tot);  // ends with a barrier: wh is zero
+        gb[tid] = g - lo;                 // global position = gb[d] + local position
+    }
     const unsigned lt_mask = (1u << lane) - 1u;
+    uint32_t key[RS_ITEMS], val[RS_ITEMS];
+    int dg[RS_ITEMS], rk[RS_ITEMS];
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; r++) {
+        const int j = warp * (32 * RS_ITEMS) + r * 32 + lane;
+        const bool valid = j < tcount;
+        key[r] = valid ? kin[base + j] : 0u;
+        val[r] = valid ? vin[base + j] : 0u;
+        const int d = valid ? (int)((key[r] >> shift) & 255u) : 256 + lane;  // invalid: own group
+        const unsigned peers = __match_any_sync(FULL_MASK, d);
+        const int before = valid ? wh[warp][d] : 0;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wh[warp][d] = before + __popc(peers);
+        __syncwarp();
+        dg[r] = d;
+        rk[r] = before + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    {
+        int p = lo;  // digit tid: its local start, then each warp's share in order
 #pragma unroll
-        for (int w = 0; w < RS_THREADS / 32; w++) wc[w][tid] = 0;
-        __syncthreads();
-        int64_t i = base + r * RS_THREADS + tid;
-        bool valid = i < n;
-        uint32_t key = valid ? kin[i] : 0u;
-        uint32_t val = valid ? vin[i] : 0u;
-        int d = valid ? (int)((key >> shift) & 255u) : 256 + lane;  // invalid: own group
-        unsigned peers = __match_any_sync(FULL_MASK, d);
-        int rank = __popc(peers & lt_mask);
-        int leader = __ffs(peers) - 1;
-        if (valid && lane == leader) wc[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            int p = run[tid];
+        for (int w = 0; w < NW; w++) {
+            const int t = wh[w][tid];
+            wh[w][tid] = p;
+            p += t;
+        }
+    }
+    __syncthreads();
 #pragma unroll
-            for (int w = 0; w < RS_THREADS / 32; w++) {
-                int t = wc[w][tid];
-                wc[w][tid] = p;
-                p += t;
+    for (int r = 0; r < RS_ITEMS; r++) {
+        if (dg[r] < 256) {
+            const int lp = wh[warp][dg[r]] + rk[r];
+            if ((unsigned)lp < (unsigned)RS_TILE) {
+                sk[lp] = key[r];
+                sv[lp] = val[r];
             }
-            run[tid] = p;
         }
-        __syncthreads();
-        if (valid) {
-            int pos = wc[warp][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        const int j = r * RS_THREADS + tid;
+        if (j < tcount) {
+            const uint32_t k = sk[j];
+            const int64_t p = (int64_t)gb[(k >> shift) & 255u] + j;
+            if ((uint64_t)p < (uint64_t)n) {
+                kout[p] = k;
+                vout[p] = sv[j];
+            }
         }
-        __syncthreads();
     }
 }
 
