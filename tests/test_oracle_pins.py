@@ -365,6 +365,27 @@ def test_splitmix64_published_vector():
     assert abs(math.hypot(float(z[0, 0]), float(z[0, 1])) - r) < 1e-6
 
 
+def test_mc_draws_angles_and_selector_from_published_outputs():
+    """The first five SplitMix64 outputs from seed 0 (published reference
+    sequence) fix every number of the first draw: the pair (z0, z1) has radius
+    sqrt(-2 ln u1) and angle 2 pi u2, z2 has radius sqrt(-2 ln u3) and angle
+    2 pi u4, and the component selector is u5.  The angles are read back with
+    atan2, so a swapped sine/cosine, a wrong uniform or a dropped 2 pi fails."""
+    outs = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F,
+            0xF88BB8A8724C81EC, 0x1B39896A51A8749B]
+    u1, u2, u3, u4, u5 = (((o >> 11) + 1) / 2.0 ** 53 for o in outs)
+    z, u = O.mc_draws(0, 0, 1)
+    z0, z1, z2 = (float(v) for v in z[0])
+    ang = math.atan2(z1, z0) % (2 * math.pi)
+    assert abs(ang - 2 * math.pi * u2) < 1e-6
+    assert abs(math.hypot(z0, z1) - math.sqrt(-2 * math.log(u1))) < 1e-6
+    # z2 alone fixes the angle of the second pair up to its sign
+    r2 = math.sqrt(-2 * math.log(u3))
+    assert abs(abs(z2) - abs(r2 * math.cos(2 * math.pi * u4))) < 1e-6
+    assert math.copysign(1.0, z2) == math.copysign(1.0, math.cos(2 * math.pi * u4))
+    assert float(u[0]) == np.float32(u5)
+
+
 # ---------------------------------------------------------------- kNN (A3)
 
 def _check_knn_against_ckdtree(xyz, nbr, k):
