@@ -767,7 +767,7 @@ int64_t orc_merge_compact(int64_t n, const double *xyz, const double *log_scale,
 
 /* ------------------------------------------------------------------------ */
 /* Sec. 3.4, local neighbourhood refresh: the lists of the pass after a merge */
-/* from the lists before it, re-running kNN queries only around new splats.   */
+/* from the lists before it; only the new splats are queried again.          */
 
 /* Row order after a merge (merged splat at the lower row, the higher row
    removed, the others in order): new id of every old row, the removed row

@@ -225,7 +225,8 @@ __global__ void k_lex_view(const uint32_t *__restrict__ klo, const uint32_t *__r
 }
 
 // ---------------------------------------------------------------- local refresh
-// Sec. 3.4: "re-running KNN queries around newly formed splats".  The lists
+// Sec. 3.4, local neighbourhood refresh: the kNN is queried again near the
+// splats a pass created, instead of for every row.  The lists
 // of a pass are carried through its merge: a kept row keeps the new ids of
 // its old neighbours when they are still k_eff distinct splats other than
 // itself; new splats and rows whose list collapsed are queried again.
