@@ -331,17 +331,35 @@ __global__ void k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shif
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// Exclusive scan, in place, of each digit's row of tile counts (one block per
+// digit, rows of the digit-major histogram); the row total goes to tot[d].
+__global__ void __launch_bounds__(1024) k_rs_rowscan(int32_t *hist, int64_t ntiles, int32_t *tot) {
+    int32_t *row = hist + (int64_t)blockIdx.x * ntiles;
+    int carry = 0;
+    for (int64_t b = 0; b < ntiles; b += blockDim.x) {
+        const int64_t i = b + threadIdx.x;
+        const int v = i < ntiles ? row[i] : 0;
+        int t;
+        const int ex = block_excl_scan(v, &t);  // ends with a barrier
+        if (i < ntiles) row[i] = carry + ex;
+        carry += t;
+    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
 // Stable scatter of one tile.  Warp w ranks the tile's items
 // [256 w, 256 w + 256) in index order, 32 at a time, against its own digit
 // counts (warp match, no block barrier); one prefix per digit over the warps
 // then places every item in shared memory in digit order, and the tile is
 // written out from there, consecutive threads at consecutive positions of a
-// digit's run.  offs is the exclusive scan of the digit-major tile counts; a
-// tile's count of digit d is the difference of two adjacent entries.
+// digit's run.  offs[d * ntiles + t] counts the keys of digit d in tiles
+// before t, tot[d] all keys of digit d; a tile's count of digit d is the
+// difference of two adjacent entries of its row.
 __global__ void __launch_bounds__(RS_THREADS)
     k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                  uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
-                 const int32_t *__restrict__ offs, int64_t ntiles) {
+                 const int32_t *__restrict__ offs, const int32_t *__restrict__ tot,
+                 int64_t ntiles) {
     constexpr int NW = RS_THREADS / 32;
     static_assert(RS_ITEMS * 32 * NW == RS_TILE, "a warp ranks RS_ITEMS rows of 32 items");
     __shared__ uint32_t sk[RS_TILE], sv[RS_TILE];
@@ -355,11 +373,13 @@ __global__ void __launch_bounds__(RS_THREADS)
     int lo;
     {
         const int64_t at = (int64_t)tid * ntiles + blockIdx.x;
-        const int g = offs[at];
-        const int cnt = offs[at + 1] - g;
-        int tot;
-        lo = block_excl_scan(cnt, &tot);  // ends with a barrier: wh is zero
-        gb[tid] = g - lo;                 // global position = gb[d] + local position
+        const int o = offs[at];
+        const int td = tot[tid];
+        const int cnt = (blockIdx.x + 1 < ntiles ? offs[at + 1] : td) - o;
+        int all, tcnt;
+        const int base = block_excl_scan(td, &all);  // keys of smaller digits
+        lo = block_excl_scan(cnt, &tcnt);            // ends with a barrier: wh is zero
+        gb[tid] = base + o - lo;                     // global position = gb[d] + local position
     }
     const unsigned lt_mask = (1u << lane) - 1u;
     uint32_t key[RS_ITEMS], val[RS_ITEMS];
@@ -519,17 +539,19 @@ void radix_sort_u32(ngs_ctx *c, uint32_t *keys, uint32_t *vals, uint32_t *keys_t
                     uint32_t *vals_tmp, int64_t n, int bits) {
     if (n <= 1) return;
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-    int32_t *hist = ws<int32_t>(c, c->b_hist, 256 * ntiles + 1);
+    // digit-major tile counts, then the 256 digit totals
+    int32_t *hist = ws<int32_t>(c, c->b_hist, 256 * ntiles + 256 + 1);
+    int32_t *tot = hist + 256 * ntiles;
     uint32_t *ka = keys, *va = vals, *kb = keys_tmp, *vb = vals_tmp;
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
         launch(c, "rs_hist", dim3((unsigned)ntiles), dim3(RS_THREADS), 0, k_rs_hist,
                (const uint32_t *)ka, n, shift, hist, ntiles);
-        scan_i32(c, hist, hist, 256 * ntiles);
+        launch(c, "rs_rowscan", dim3(256), dim3(1024), 0, k_rs_rowscan, hist, ntiles, tot);
         launch(c, "rs_scatter", dim3((unsigned)ntiles), dim3(RS_THREADS), 0, k_rs_scatter,
                (const uint32_t *)ka, (const uint32_t *)va, kb, vb, n, shift,
-               (const int32_t *)hist, ntiles);
+               (const int32_t *)hist, (const int32_t *)tot, ntiles);
         uint32_t *t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
     }

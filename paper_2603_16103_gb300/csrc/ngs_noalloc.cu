@@ -38,7 +38,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kAcc = align256(8 * 4);
 constexpr size_t kFrame = align256(8 * 4);
 constexpr size_t kKeys = align256(4 * kMaxN);
-constexpr size_t kHist = align256(4 * (256 * kTiles + 1));
+constexpr size_t kHist = align256(4 * (256 * kTiles + 256 + 1));  // tile counts, digit totals
 constexpr size_t kPart = align256(4 * (kCells / 2048 + 2));
 constexpr size_t kPts = align256(16 * kMaxN);
 constexpr size_t kTable = align256(4 * (kCells + 2));
