@@ -296,14 +296,15 @@ def batched_form(B, torch, synth, args):
     res = {}
     outs = {}
     def counts(sts):
-        return [sum(st[k] for st in sts) for k in ("gpu_launches", "host_syncs", "passes")]
+        return [sum(st[k] for st in sts)
+                for k in ("gpu_launches", "host_syncs", "passes", "fp64_cost_edges", "near_tie_slots")]
 
     for mode in ("batched", "sequential"):
         if mode == "batched":
             run = lambda: counts([ctx.batch_simplify(work, targets)])
         else:
             run = lambda: counts([ctx.simplify(w, t) for w, t in zip(work, targets)])
-        times, tot = [], [0, 0, 0]
+        times, tot = [], [0, 0, 0, 0, 0]
         for it in range(1 + args.form_steps):
             restore()
             torch.cuda.synchronize()
@@ -321,15 +322,19 @@ def batched_form(B, torch, synth, args):
         torch.cuda.synchronize()
         prof_wall, _ = _timed(torch, stream, run)
         B.ngs_profile_enable(ctx.handle, False)
-        kern_ms = sum(p[2] for p in B.ngs_profile(ctx.handle))
+        prof = B.ngs_profile(ctx.handle)
+        kern_ms = sum(p[2] for p in prof)
+        top = [{"name": nm, "launches": nl, "ms": km}
+               for nm, nl, km in sorted(prof, key=lambda p: -p[2])[:12]]
         ms = statistics.median(times)
-        launches, syncs, passes = (x / args.form_steps for x in tot)
+        launches, syncs, passes, fp64_edges, tie_slots = (x / args.form_steps for x in tot)
         res[mode] = {"value": total / (ms / 1e3), "unit": UNIT, "ms": ms,
                      "gpu_launches": launches, "host_syncs": syncs, "passes": passes,
                      "gpu_launches_per_pass": launches / max(passes, 1),
                      "host_syncs_per_pass": syncs / max(passes, 1),
+                     "fp64_cost_edges": fp64_edges, "near_tie_slots": tie_slots,
                      "profiled_run": {"wall_ms": prof_wall, "kernel_ms": kern_ms,
-                                      "gap_ms": prof_wall - kern_ms}}
+                                      "gap_ms": prof_wall - kern_ms, "top_kernels": top}}
     identical = all(all(torch.equal(a, b) for a, b in zip(x, y))
                     for x, y in zip(outs["batched"], outs["sequential"]))
     ctx.close()

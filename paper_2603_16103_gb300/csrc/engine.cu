@@ -339,13 +339,23 @@ __global__ void k_gather_cid(const uint32_t *__restrict__ order, const int32_t *
 }
 
 // ---- per-scene pair counts and caps
+// Rows of a scene are contiguous, so the lanes of a warp mostly share one
+// scene: one atomic per scene present in the warp.
 __global__ void k_scene_pairs(int64_t n, const int32_t *__restrict__ mate,
                               const int32_t *__restrict__ cid, const int32_t *__restrict__ sid,
                               int32_t *cnt) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t u = mate[v];
-        if (u >= 0 && cid[v] < cid[u]) atomicAdd(&cnt[sid[v]], 1);
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = b + threadIdx.x;
+        bool has = false;
+        int32_t s = 0;
+        if (v < n) {
+            const int32_t u = mate[v];
+            has = u >= 0 && cid[v] < cid[u];
+            s = sid[v];
+        }
+        const unsigned peers = __match_any_sync(FULL_MASK, has ? s : -1 - lane);
+        if (has && lane == __ffs(peers) - 1) atomicAdd(&cnt[s], __popc(peers));
     }
 }
 
