@@ -343,6 +343,18 @@ int ngs_release_workspace(ngs_ctx *ctx);
  * (the pool every ctx's workspace comes from; both 0 before its first use).
  * Errors: INVALID_ARG, CUDA. */
 int ngs_pool_usage(int device, int64_t *used_bytes, int64_t *reserved_bytes);
+
+/* Self test of the extended-precision (float-float, about 48-bit) arithmetic
+ * that evaluates the edges the accuracy contract refines (App. A estimator,
+ * Sec. 3.3 moments) when fp64_policy is not 3.  x, y, out: n doubles in HOST
+ * memory (caller-owned); each x[i] (and y[i]) is first rounded to
+ * float-float, and out[i] is the float-float result widened to double.
+ * op: 0 exp(x), 1 log(x), 2 log1p(x) for x >= 0, 3 sqrt(x), 4 x / y,
+ *     5 log(1 + e^x), 6 log(e^x + e^y), 7 x * y.
+ * Runs on the ctx stream and synchronises it.  Errors: INVALID_ARG (op out
+ * of range, n < 0, null pointer with n > 0), CUDA, OOM. */
+int ngs_selftest_ff(ngs_ctx *ctx, int32_t op, const double *x, const double *y, int64_t n,
+                    double *out);
 /* Move the ctx to another CUDA stream (NULL = legacy default stream) after
  * the work queued on its current stream has finished.  Errors: CUDA. */
 int ngs_set_stream(ngs_ctx *ctx, void *stream);

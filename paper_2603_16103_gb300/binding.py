@@ -144,6 +144,7 @@ _SIGS = {
     "ngs_select_pairs": (ctypes.c_int, [_P, ctypes.POINTER(ngs_graph), _P, ctypes.c_int64, _P,
                                         ctypes.POINTER(ctypes.c_int64)]),
     "ngs_merge_compact": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), _P, ctypes.c_int64]),
+    "ngs_selftest_ff": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P]),
     "ngs_simplify": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats), ctypes.c_int64,
                                     ctypes.POINTER(ngs_stats)]),
     "ngs_batch_simplify": (ctypes.c_int, [_P, ctypes.POINTER(ngs_splats),
@@ -486,6 +487,18 @@ class Context:
         for ds, s in zip(scenes, structs):
             ds.n = s.n
         return st
+
+    def selftest_ff(self, op: int, x, y=None):
+        """Float-float arithmetic of the refined edge costs on host float64
+        arrays (ngs_selftest_ff); returns the results widened to float64."""
+        import numpy as np
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        yy = None if y is None else np.ascontiguousarray(y, dtype=np.float64)
+        out = np.empty_like(x)
+        _check(load().ngs_selftest_ff(_P(self.handle), op, x.ctypes.data,
+                                      None if yy is None else yy.ctypes.data, x.size,
+                                      out.ctypes.data))
+        return out
 
     def simplify_host(self, hs: DeviceSplats, target: int) -> dict:
         s = hs.struct()

@@ -31,6 +31,7 @@
 // and stored rounded to FP32.  Every comparison the greedy rule of Sec. 3.4
 // makes is between adjacent edges, so the pair set then follows the FP64
 // costs except where two FP64 costs round to the same FP32 value.
+#include "ffmath.cuh"
 #include "ngs_device.cuh"
 #include "ngs_internal.h"
 
@@ -251,6 +252,200 @@ __device__ double dapp_fp64(const float *sh, int F, int64_t i, int64_t j) {
         a += d * d;
     }
     return a;
+}
+
+// ---------------------------------------------------------------- float-float path
+// The same evaluation as the FP64 path, step for step, in float-float
+// arithmetic on the FP32 pipes (ffmath.cuh): about 48 significant bits, so
+// the cost rounds to the same float as the FP64 evaluation except within a
+// few units of 2^-48 of a rounding boundary.  GB300 runs FP64 at about 1/64
+// of the FP32 rate; this path is the default for the edges the accuracy
+// contract refines, FP64 the option (fp64_policy 3).
+struct Gff {
+    float mu[3];
+    ff R[9], s[3], is[3], Sig[6], sum_ls, lw;
+};
+
+constexpr float FF_HLOG2PI_H = 0x1.60df56p+1f;   // 1.5 log(2 pi), head
+constexpr float FF_HLOG2PI_L = -0x1.368e2p-24f;  // and tail
+
+__device__ __forceinline__ ff ff_twice(ff a) { return {__fmul_rn(a.h, 2.f), __fmul_rn(a.l, 2.f)}; }
+
+__device__ __noinline__ void splat_ff(const float *xyz, const float *ls, const float *rot,
+                                      const float *logit, int64_t v, Gff &g) {
+    const float qw = rot[4 * v], qx = rot[4 * v + 1], qy = rot[4 * v + 2], qz = rot[4 * v + 3];
+    const ff nn = ff_add(ff_add(ff_prod(qw, qw), ff_prod(qx, qx)), ff_add(ff_prod(qy, qy), ff_prod(qz, qz)));
+    const ff inv = ff_div(ff_of(1.f), ff_sqrt(nn));
+    const ff w = ff_mulf(inv, qw), x = ff_mulf(inv, qx), y = ff_mulf(inv, qy), z = ff_mulf(inv, qz);
+    const ff xx = ff_sqr(x), yy = ff_sqr(y), zz = ff_sqr(z);
+    const ff xy = ff_mul(x, y), xz = ff_mul(x, z), yz = ff_mul(y, z);
+    const ff wx = ff_mul(w, x), wy = ff_mul(w, y), wz = ff_mul(w, z);
+    const ff one = ff_of(1.f);
+    g.R[0] = ff_sub(one, ff_twice(ff_add(yy, zz)));
+    g.R[1] = ff_twice(ff_sub(xy, wz));
+    g.R[2] = ff_twice(ff_add(xz, wy));
+    g.R[3] = ff_twice(ff_add(xy, wz));
+    g.R[4] = ff_sub(one, ff_twice(ff_add(xx, zz)));
+    g.R[5] = ff_twice(ff_sub(yz, wx));
+    g.R[6] = ff_twice(ff_sub(xz, wy));
+    g.R[7] = ff_twice(ff_add(yz, wx));
+    g.R[8] = ff_sub(one, ff_twice(ff_add(xx, yy)));
+    ff s2[3];
+    for (int a = 0; a < 3; a++) {
+        g.mu[a] = xyz[3 * v + a];
+        g.s[a] = ff_exp(ff_of(ls[3 * v + a]));
+        g.is[a] = ff_div(one, g.s[a]);
+        s2[a] = ff_sqr(g.s[a]);
+    }
+    g.sum_ls = ff_add_acc(ff_two_sum(ls[3 * v], ls[3 * v + 1]), ff_of(ls[3 * v + 2]));
+    int idx = 0;
+    for (int a = 0; a < 3; a++)
+        for (int b = a; b < 3; b++) {
+            ff acc = ff_of(0.f);
+            for (int k = 0; k < 3; k++) acc = ff_add(acc, ff_mul(ff_mul(g.R[3 * a + k], s2[k]), g.R[3 * b + k]));
+            g.Sig[idx++] = acc;
+        }
+    g.lw = ff_add(ff_sub(ff{FF_HLOG2PI_H, FF_HLOG2PI_L}, ff_softplus(ff_of(-logit[v]))), g.sum_ls);
+}
+
+__device__ __forceinline__ ff maha_ff(const Gff &g, const ff *v) {
+    ff q = ff_of(0.f);
+    for (int k = 0; k < 3; k++) {
+        const ff t = ff_mul(ff_add(ff_add(ff_mul(g.R[k], v[0]), ff_mul(g.R[3 + k], v[1])), ff_mul(g.R[6 + k], v[2])),
+                            g.is[k]);
+        q = ff_add(q, ff_sqr(t));
+    }
+    return q;
+}
+
+// log(a b c) for a, b, c > 0, without forming a product that could leave the
+// float range: the factors' binary exponents are taken out first
+__device__ __forceinline__ ff ff_log_prod3(ff a, ff b, ff c) {
+    int ea, eb, ec;
+    frexpf(a.h, &ea);
+    frexpf(b.h, &eb);
+    frexpf(c.h, &ec);
+    const ff m = ff_mul(ff_mul(ff_ldexp(a, -ea), ff_ldexp(b, -eb)), ff_ldexp(c, -ec));
+    ff y = ff_log(m);
+    const float ef = (float)(ea + eb + ec);
+    y = ff_add_acc(y, ff_prod(ef, FF_LN2_H));
+    y = ff_add_acc(y, ff_prod(ef, FF_LN2_M));
+    return ff_add(y, ff_of(__fmul_rn(ef, FF_LN2_L)));
+}
+
+__device__ __noinline__ ff dgeo_ff(const float *xyz, const float *ls, const float *rot,
+                                   const float *logit, int64_t i, int64_t j, int S,
+                                   const float *__restrict__ zs, const float *__restrict__ us, int mode) {
+    Gff gi, gj;
+    splat_ff(xyz, ls, rot, logit, i, gi);
+    splat_ff(xyz, ls, rot, logit, j, gj);
+    if (mode == 3) {
+        ff r = ff_of(0.f);
+        for (int a = 0; a < 3; a++) r = ff_add(r, ff_sqr(ff_two_sum(gi.mu[a], -gj.mu[a])));
+        for (int t = 0; t < 6; t++) {
+            const ff dd = ff_sub_acc(gi.Sig[t], gj.Sig[t]);
+            const ff e2 = ff_sqr(dd);
+            r = ff_add(r, (t == 0 || t == 3 || t == 5) ? e2 : ff_twice(e2));
+        }
+        return r;
+    }
+    const ff inf = ff_of(__int_as_float(0x7f800000));
+    // pi = sigmoid(ld) and its complement share t = e^{-|ld|}
+    const ff ld = ff_sub_acc(gi.lw, gj.lw);
+    const bool ldpos = !(ld.h < 0.f);
+    const ff t = ff_exp(ff_neg(ff_abs(ld))), l1t = ff_log1p(t);
+    const ff zero = ff_of(0.f);
+    const ff lpi = ff_neg(ff_add(ldpos ? zero : ff_neg(ld), l1t));
+    const ff lpj = ff_neg(ff_add(ldpos ? ld : zero, l1t));
+    const ff big = ff_div(ff_of(1.f), ff_add_acc(ff_of(1.f), t)), small = ff_mul(t, big);
+    const ff pi = ldpos ? big : small, pj = ldpos ? small : big;
+    const ff pp = ff_mul(pi, pj);
+    ff d[3];
+    for (int a = 0; a < 3; a++) d[a] = ff_two_sum(gi.mu[a], -gj.mu[a]);
+    ff Sm[6];
+    int idx = 0;
+    for (int a = 0; a < 3; a++)
+        for (int b = a; b < 3; b++, idx++)
+            Sm[idx] = ff_add(ff_add(ff_mul(pi, gi.Sig[idx]), ff_mul(pj, gj.Sig[idx])),
+                             ff_mul(ff_mul(pp, d[a]), d[b]));
+    // Sm = (00 01 02 11 12 22)
+    const ff l00 = ff_sqrt(Sm[0]);
+    const ff l10 = ff_div(Sm[1], l00), l20 = ff_div(Sm[2], l00);
+    const ff t11 = ff_sub_acc(Sm[3], ff_sqr(l10));
+    if (!ff_pos(t11)) return inf;
+    const ff l11 = ff_sqrt(t11);
+    const ff l21 = ff_div(ff_sub_acc(Sm[4], ff_mul(l20, l10)), l11);
+    const ff t22 = ff_sub_acc(ff_sub_acc(Sm[5], ff_sqr(l20)), ff_sqr(l21));
+    if (!ff_pos(t22)) return inf;
+    const ff l22 = ff_sqrt(t22);
+    const ff half_ldm = ff_mulf(ff_log_prod3(Sm[0], t11, t22), 0.5f);  // log(l00 l11 l22)
+    const ff ai = ff_sub_acc(half_ldm, gi.sum_ls), aj = ff_sub_acc(half_ldm, gj.sum_ls);
+    const ff ci = ff_add(lpi, ai), cj = ff_add(lpj, aj);
+    ff acc = zero;
+    for (int s = 0; s < S; s++) {
+        const float z[3] = {zs[3 * s], zs[3 * s + 1], zs[3 * s + 2]};
+        const ff zz = ff_add(ff_add(ff_prod(z[0], z[0]), ff_prod(z[1], z[1])), ff_prod(z[2], z[2]));
+        ff yi[3], yj[3];
+        for (int pass = 0; pass < 2; pass++) {
+            const Gff &g = pass == 0 ? gi : gj;
+            ff *y = pass == 0 ? yi : yj;
+            ff tt[3];
+            for (int k = 0; k < 3; k++)
+                tt[k] = ff_mul(g.s[k], ff_add(ff_add(ff_mulf(g.R[k], z[0]), ff_mulf(g.R[3 + k], z[1])),
+                                              ff_mulf(g.R[6 + k], z[2])));
+            for (int a = 0; a < 3; a++)
+                y[a] = ff_add(ff_add(ff_mul(g.R[3 * a], tt[0]), ff_mul(g.R[3 * a + 1], tt[1])),
+                              ff_mul(g.R[3 * a + 2], tt[2]));
+        }
+        ff gv[2];
+        for (int side = 0; side < 2; side++) {
+            // side 0: x = x_i, side 1: x = x_j; offsets from each mean
+            ff vi[3], vj[3], vm[3];
+            for (int a = 0; a < 3; a++) {
+                if (side == 0) {
+                    vi[a] = yi[a];
+                    vj[a] = ff_add(d[a], yi[a]);
+                    vm[a] = ff_add(ff_mul(pj, d[a]), yi[a]);
+                } else {
+                    vi[a] = ff_sub(yj[a], d[a]);
+                    vj[a] = yj[a];
+                    vm[a] = ff_sub(yj[a], ff_mul(pi, d[a]));
+                }
+            }
+            const ff qi = side == 0 ? zz : maha_ff(gi, vi);
+            const ff qj = side == 1 ? zz : maha_ff(gj, vj);
+            const ff y0 = ff_div(vm[0], l00);
+            const ff y1 = ff_div(ff_sub(vm[1], ff_mul(l10, y0)), l11);
+            const ff y2 = ff_div(ff_sub(ff_sub(vm[2], ff_mul(l20, y0)), ff_mul(l21, y1)), l22);
+            const ff qm = ff_add(ff_add(ff_sqr(y0), ff_sqr(y1)), ff_sqr(y2));
+            const ff l = ff_lse2(ff_sub(ci, ff_mulf(qi, 0.5f)), ff_sub(cj, ff_mulf(qj, 0.5f)));
+            gv[side] = ff_add(l, mode == 2 ? ff_of(1.5f) : ff_mulf(qm, 0.5f));
+        }
+        if (mode != 1) {
+            acc = ff_add(acc, ff_add(ff_mul(pi, gv[0]), ff_mul(pj, gv[1])));
+        } else {
+            // u_s < pi, decided exactly
+            const bool first = ff_pos(ff_sub_acc(pi, ff_of(us[s])));
+            acc = ff_add(acc, first ? gv[0] : gv[1]);
+        }
+    }
+    return ff_div(acc, ff_of((float)S));
+}
+
+// D_app = sum over the F coefficients of (f_i - f_j)^2 (each difference exact)
+__device__ ff dapp_ff(const float *sh, int F, int64_t i, int64_t j) {
+    ff a = ff_of(0.f);
+    for (int t = 0; t < F; t++) a = ff_add(a, ff_sqr(ff_two_sum(sh[i * F + t], -sh[j * F + t])));
+    return a;
+}
+
+// the whole cost in float-float, rounded once to FP32 (i = lower canonical id)
+__device__ float cost_ff(const float *xyz, const float *ls, const float *rot, const float *logit,
+                         const float *sh, int F, int64_t i, int64_t j, int S,
+                         const float *zs, const float *us, int mode, float lg, float la) {
+    const ff dg = dgeo_ff(xyz, ls, rot, logit, i, j, S, zs, us, mode);
+    if (!(dg.h < __int_as_float(0x7f800000))) return dg.h;
+    return ff_to_float(ff_add(ff_mulf(dg, lg), ff_mulf(dapp_ff(sh, F, i, j), la)));
 }
 
 // the whole cost in FP64, rounded once to FP32 (i = lower canonical id)
@@ -566,7 +761,8 @@ __global__ void __launch_bounds__(256, 3)
 
 // FP64 evaluation of the flagged edges: D_geo and D_app in FP64, the cost
 // rounded once to FP32.
-__global__ void k_edge_cost64(const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
+template <bool F64>
+__global__ void k_edge_cost_x(const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
                               const int4 *__restrict__ erec, const float *__restrict__ zs,
                               const float *__restrict__ us, int S, int mode, float lg, float la,
                               const float *__restrict__ xyz, const float *__restrict__ ls,
@@ -579,7 +775,8 @@ __global__ void k_edge_cost64(const int32_t *__restrict__ list, const unsigned l
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = list[t];
         const int4 er = erec[e];
-        const float c = cost_fp64(xyz, ls, rot, logit, sh, F, er.y, er.z, S, zs, us, mode, lg, la);
+        const float c = F64 ? cost_fp64(xyz, ls, rot, logit, sh, F, er.y, er.z, S, zs, us, mode, lg, la)
+                            : cost_ff(xyz, ls, rot, logit, sh, F, er.y, er.z, S, zs, us, mode, lg, la);
         cost_slot[er.x] = c;
         if (er.w >= 0) cost_slot[er.w] = c;
         else if (er.w <= -2) revcost[-2 - er.w] = c;
@@ -769,6 +966,7 @@ __device__ __forceinline__ uint32_t cid_at(const int32_t *cid, int64_t v) {
 
 // FP64 cost of the edge of each listed slot, into both slots of a mutual
 // edge and, for the C-ABI view, into its lexicographic position.
+template <bool F64>
 __global__ void k_refine_costs(const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
                                int kk, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cid,
                                const float *__restrict__ zs, const float *__restrict__ us, int S,
@@ -786,7 +984,8 @@ __global__ void k_refine_costs(const int32_t *__restrict__ list, const unsigned 
         const int64_t a = s / kk, b = nbr[s];
         const uint32_t ca = cid_at(cid, a), cb = cid_at(cid, b);
         const int64_t lo = ca < cb ? a : b, hi = ca < cb ? b : a;
-        const float c = cost_fp64(xyz, ls, rot, logit, sh, F, lo, hi, S, zs, us, mode, lg, la);
+        const float c = F64 ? cost_fp64(xyz, ls, rot, logit, sh, F, lo, hi, S, zs, us, mode, lg, la)
+                            : cost_ff(xyz, ls, rot, logit, sh, F, lo, hi, S, zs, us, mode, lg, la);
         cost_slot[s] = c;
         bool mutual = false;
         for (int q = 0; q < kk; q++)  // the mirror slot of a mutual edge
@@ -824,7 +1023,43 @@ __global__ void k_costs_to_slots(const int4 *__restrict__ erec_lex, int64_t m,
     }
 }
 
+__device__ __forceinline__ ff ff_from_double(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+__global__ void k_ff_selftest(int op, const double *__restrict__ x, const double *__restrict__ y,
+                              int64_t n, double *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const ff a = ff_from_double(x[i]), b = y ? ff_from_double(y[i]) : ff_of(0.f);
+        ff r;
+        switch (op) {
+            case 0: r = ff_exp(a); break;
+            case 1: r = ff_log(a); break;
+            case 2: r = ff_log1p(a); break;
+            case 3: r = ff_sqrt(a); break;
+            case 4: r = ff_div(a, b); break;
+            case 5: r = ff_softplus(a); break;
+            case 6: r = ff_lse2(a, b); break;
+            default: r = ff_mul(a, b); break;
+        }
+        out[i] = ff_to_double(r);
+    }
+}
+
 }  // namespace
+
+void ff_selftest(ngs_ctx *c, int op, const double *x, const double *y, int64_t n, double *out) {
+    if (n <= 0) return;
+    double *d = (double *)ws<uint8_t>(c, c->b_tielist, 8 * (size_t)n * 3);  // edge-cost scratch
+    NGS_CHECK_CUDA(cudaMemcpyAsync(d, x, 8 * n, cudaMemcpyHostToDevice, c->st));
+    if (y) NGS_CHECK_CUDA(cudaMemcpyAsync(d + n, y, 8 * n, cudaMemcpyHostToDevice, c->st));
+    launch(c, "ff_selftest", dim3(grid_stride_blocks(c, n, 128, 4)), dim3(128), 0, k_ff_selftest, op,
+           (const double *)d, y ? (const double *)(d + n) : (const double *)nullptr, n, d + 2 * n);
+    NGS_CHECK_CUDA(cudaMemcpyAsync(out, d + 2 * n, 8 * n, cudaMemcpyDeviceToHost, c->st));
+    sync_stream(c);
+}
 
 void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool lex,
                 float *cost_out) {
@@ -861,7 +1096,9 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
            (const float *)s.logit, g.cost_slot, g.revcost, cout, cnt, list, tol);
     // the flagged edges (few) in FP64; the grid covers the worst case, threads
     // past the device count exit at once
-    launch(c, "edge_cost64", dim3(grid_stride_blocks(c, m, 128, 2)), dim3(128), 0, k_edge_cost64,
+    const bool f64 = c->prm.fp64_policy == 3;
+    launch(c, "edge_cost_x", dim3(grid_stride_blocks(c, m, 128, 2)), dim3(128), 0,
+           f64 ? k_edge_cost_x<true> : k_edge_cost_x<false>,
            (const int32_t *)list, (const unsigned long long *)cnt, er, (const float *)zs, us, S, mode,
            lg, la, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
            (const float *)s.logit, (const float *)s.sh, s.F, g.cost_slot, g.revcost, cout);
@@ -877,7 +1114,8 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
                (const int32_t *)g.rev_ptr, (const int32_t *)g.rev, (const float *)g.revcost, tol,
                bits, tl, cnt + 1);
         launch(c, "refine_costs", dim3(grid_stride_blocks(c, ns, 128, 4)), dim3(128), 0,
-               k_refine_costs, (const int32_t *)tl, (const unsigned long long *)(cnt + 1), g.k_eff,
+               f64 ? k_refine_costs<true> : k_refine_costs<false>, (const int32_t *)tl,
+               (const unsigned long long *)(cnt + 1), g.k_eff,
                g.nbr, g.cid, (const float *)zs, us, S, mode, lg, la, (const float *)s.xyz,
                (const float *)s.ls, (const float *)s.rot, (const float *)s.logit,
                (const float *)s.sh, s.F, g.cost_slot, (const int32_t *)g.rev_ptr,

@@ -17,6 +17,7 @@
 // finish_ff), or in FP64 under fp64_policy 3 (finish_fp64).  Canonical form: eigenvalues descending,
 // each eigenvector's largest-magnitude component positive, det V = +1,
 // quaternion with w >= 0.
+#include "ffmath.cuh"
 #include "ngs_device.cuh"
 #include "ngs_internal.h"
 
@@ -92,46 +93,7 @@ __device__ __forceinline__ T diag2(const T *A) {
 }
 
 // ---------------------------------------------------------------- float-float
-// Extended precision on the FP32 pipes: a value is the unevaluated sum h + l
-// of two floats with |l| <= ulp(h) / 2 (Dekker 1971), about 48 significant
-// bits.  Built from the error-free transformations TwoSum (Knuth), Fast2Sum
-// (Dekker, |a| >= |b|) and TwoProduct with a fused multiply-add.  Explicit
-// _rn intrinsics keep the compiler from contracting or reassociating them.
-struct ff {
-    float h, l;
-};
-
-__device__ __forceinline__ ff ff_fast2(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ ff ff_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-// exact product of two floats
-__device__ __forceinline__ ff ff_prod(float a, float b) {
-    const float p = __fmul_rn(a, b);
-    return {p, __fmaf_rn(a, b, -p)};
-}
-// x + y; absolute error about 2^-46 (|x| + |y|)
-__device__ __forceinline__ ff ff_add(ff x, ff y) {
-    const ff s = ff_two_sum(x.h, y.h);
-    return ff_fast2(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
-}
-// x * b for a float b
-__device__ __forceinline__ ff ff_mulf(ff x, float b) {
-    const float p = __fmul_rn(x.h, b);
-    return ff_fast2(p, __fmaf_rn(x.l, b, __fmaf_rn(x.h, b, -p)));
-}
-// x * y
-__device__ __forceinline__ ff ff_mul(ff x, ff y) {
-    const float p = __fmul_rn(x.h, y.h);
-    const float e = __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, __fmaf_rn(x.h, y.h, -p)));
-    return ff_fast2(p, e);
-}
-__device__ __forceinline__ bool ff_gt(ff x, ff y) { return x.h > y.h || (x.h == y.h && x.l > y.l); }
+// Extended precision (float-float) arithmetic: ffmath.cuh.
 
 // Extended-precision finish of the eigendecomposition of Sigma_m.
 //   * Q: the FP32 Jacobi eigenvectors, re-orthonormalised by Gram-Schmidt in

@@ -727,6 +727,18 @@ extern "C" int ngs_simplify_host(ngs_ctx *c, ngs_splats *h, int64_t target, ngs_
     API_END
 }
 
+extern "C" int ngs_selftest_ff(ngs_ctx *c, int32_t op, const double *x, const double *y,
+                               int64_t n, double *out) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    API_BEGIN
+    if (op < 0 || op > 7) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_selftest_ff: op %d out of range", op);
+    if (n < 0) NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_selftest_ff: n < 0");
+    if (n > 0 && (!x || !out || ((op == 4 || op == 6 || op == 7) && !y)))
+        NGS_FAIL(NGS_ERR_INVALID_ARG, "ngs_selftest_ff: null pointer");
+    ff_selftest(c, op, x, (op == 4 || op == 6 || op == 7) ? y : nullptr, n, out);
+    API_END
+}
+
 // ---------------------------------------------------------------- instrumentation API
 extern "C" int ngs_profile_enable(ngs_ctx *c, int enable) {
     if (!c) return NGS_ERR_INVALID_ARG;

@@ -315,6 +315,8 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
                 float *cost_out);
 // cost_slot from caller costs given in lexicographic edge order.
 void costs_to_slots(ngs_ctx *c, GraphDev &g, const float *cost_lex);
+// float-float arithmetic on host doubles (ngs_selftest_ff)
+void ff_selftest(ngs_ctx *c, int op, const double *x, const double *y, int64_t n, double *out);
 
 // ---------------------------------------------------------------- matching (k_match.cu)
 // Greedy matching under (cost, canonical pair) capped to max_pairs.  Writes
