@@ -85,20 +85,24 @@ typedef struct {
  *   seed        seed of the per-pass common random numbers
  *   max_passes  upper bound on simplification passes (default 64)
  *   fp64_policy 0: merged covariance eigendecomposition finished in
- *               float-float (about 48-bit) arithmetic, and FP64 log-det for
- *               near-degenerate merged covariances (default);
- *               1: additionally FP64 cost terms for edges with a
+ *               float-float (about 48-bit) arithmetic, and the whole cost of
+ *               edges with a near-degenerate merged covariance, or refined
+ *               by the accuracy contract below, evaluated in float-float
+ *               (default);
+ *               1: additionally that extended cost for edges with a
  *               near-degenerate endpoint; 2: the float-float finish only for
- *               ill-conditioned merged covariances; 3: as 0 with the
- *               eigendecomposition finished in FP64 instead of float-float
+ *               ill-conditioned merged covariances; 3: as 0 with FP64
+ *               instead of float-float for the eigendecomposition finish and
+ *               for the extended edge costs
  *   prefilter   1: ngs_simplify first applies the opacity pre-filter
  *   eig_floor   lower bound on merged covariance eigenvalues (default 1e-30)
  *   cost_tol    accuracy contract of the edge costs (default 3e-5; 0 turns
  *               it off; at most 1e-4): an FP32 cost is kept only when twice its running
  *               rounding-error estimate is within cost_tol max(|C|, 1), else
- *               the edge is evaluated in FP64; then any two adjacent edges
- *               whose costs lie within cost_tol (max(|C_e|,1) + max(|C_f|,1))
- *               of each other are both recomputed in FP64 (rounded once to
+ *               the edge is evaluated in extended precision (float-float, or
+ *               FP64 under fp64_policy 3); then any two adjacent edges whose
+ *               costs lie within cost_tol (max(|C_e|,1) + max(|C_f|,1)) of
+ *               each other are both recomputed the same way (rounded once to
  *               FP32), so every decision of the greedy rule (Sec. 3.4)
  *               follows the FP64 costs up to one FP32 rounding
  *   refresh_period  local neighbourhood refresh (Sec. 3.4; default 1, the
@@ -156,8 +160,10 @@ typedef struct {
     int64_t pass_n[NGS_STATS_MAX_PASSES];     /* N at the start of pass p   */
     int64_t pass_edges[NGS_STATS_MAX_PASSES]; /* |E| of pass p              */
     int64_t pass_pairs[NGS_STATS_MAX_PASSES]; /* merged pairs of pass p     */
-    int64_t fp64_cost_edges;/* edges sent to FP64 by their error estimate or
-                             * by a near-degenerate merged covariance       */
+    int64_t fp64_cost_edges;/* edges sent to the extended-precision cost
+                             * (float-float, FP64 under fp64_policy 3) by
+                             * their error estimate or by a near-degenerate
+                             * merged covariance                            */
     int64_t eig_floor_hits; /* merged eigenvalues raised to eig_floor        */
     int64_t gpu_launches;   /* kernels the library launched for this call    */
     int64_t near_tie_slots; /* list slots recomputed in FP64 as near ties
