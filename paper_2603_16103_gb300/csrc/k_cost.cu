@@ -1094,10 +1094,11 @@ void edge_costs(ngs_ctx *c, const SplatView &s, GraphDev &g, uint32_t pass, bool
            kern, er, m, (const float *)rec, (const float *)s.sh, s.F, (const float *)zs, us, S, lg,
            la, c->prm.fp64_policy, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
            (const float *)s.logit, g.cost_slot, g.revcost, cout, cnt, list, tol);
-    // the flagged edges (few) in FP64; the grid covers the worst case, threads
+    // the flagged edges (few) in extended precision, three 128-thread blocks
+    // per SM (the register limit); the grid covers the worst case, threads
     // past the device count exit at once
     const bool f64 = c->prm.fp64_policy == 3;
-    launch(c, "edge_cost_x", dim3(grid_stride_blocks(c, m, 128, 2)), dim3(128), 0,
+    launch(c, "edge_cost_x", dim3(grid_stride_blocks(c, m, 128, 3)), dim3(128), 0,
            f64 ? k_edge_cost_x<true> : k_edge_cost_x<false>,
            (const int32_t *)list, (const unsigned long long *)cnt, er, (const float *)zs, us, S, mode,
            lg, la, (const float *)s.xyz, (const float *)s.ls, (const float *)s.rot,
