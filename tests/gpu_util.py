@@ -120,3 +120,23 @@ def stepwise(ngs, ctx, scene, target, max_passes=64):
             break
         ctx.merge_compact(ds, pairs)
     return ds, p
+
+
+def greedy_certificate_np(n, lo, hi, cost64, pairs, rel=1e-6):
+    """Vectorised form of the greedy certificate: `pairs` is a matching, no
+    edge has two free endpoints, and every other edge touches a pair whose FP64
+    cost is not larger beyond `rel`.  Returns the number of violating edges."""
+    mate = np.full(n, -1, np.int64)
+    assert len(np.unique(pairs.reshape(-1))) == 2 * len(pairs), "not a matching"
+    mate[pairs[:, 0]], mate[pairs[:, 1]] = pairs[:, 1], pairs[:, 0]
+    keys = lo.astype(np.int64) * n + hi
+    pk = pairs[:, 0].astype(np.int64) * n + pairs[:, 1]
+    at = np.searchsorted(keys, pk)               # lo, hi are in lexicographic order
+    assert np.array_equal(keys[at], pk), "a pair is not an edge"
+    pc = np.full(n, np.inf)
+    pc[pairs[:, 0]] = pc[pairs[:, 1]] = cost64[at]
+    member = mate[lo] == hi
+    assert not np.any((mate[lo] < 0) & (mate[hi] < 0)), "an edge has two free endpoints"
+    best = np.minimum(pc[lo], pc[hi])
+    ok = best <= cost64 + rel * np.maximum(np.abs(cost64), 1.0)
+    return int(np.sum(~ok & ~member))

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_util import check_merge_rows, cost_excess, knn_agreement, stepwise
+from gpu_util import check_merge_rows, cost_excess, greedy_certificate_np as certificate, knn_agreement, stepwise
 from paper_2603_16103_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -73,26 +73,6 @@ def test_1m_pairs_exact_on_gpu_costs_and_certified_on_fp64(run1m):
     assert len(run1m["pairs"]) < run1m["P"]      # uncapped: the whole matching is certified
     # the FP64 greedy order wherever FP64 costs differ by more than 1e-6
     assert certificate(cur.n, lo, hi, c64, run1m["pairs"], rel=1e-6) == 0
-
-
-def certificate(n, lo, hi, cost64, pairs, rel):
-    """Vectorised form of the greedy certificate: `pairs` is a matching, no
-    edge has two free endpoints, and every other edge touches a pair whose FP64
-    cost is not larger beyond `rel`.  Returns the number of violating edges."""
-    mate = np.full(n, -1, np.int64)
-    assert len(np.unique(pairs.reshape(-1))) == 2 * len(pairs), "not a matching"
-    mate[pairs[:, 0]], mate[pairs[:, 1]] = pairs[:, 1], pairs[:, 0]
-    keys = lo.astype(np.int64) * n + hi
-    pk = pairs[:, 0].astype(np.int64) * n + pairs[:, 1]
-    at = np.searchsorted(keys, pk)               # lo, hi are in lexicographic order
-    assert np.array_equal(keys[at], pk), "a pair is not an edge"
-    pc = np.full(n, np.inf)
-    pc[pairs[:, 0]] = pc[pairs[:, 1]] = cost64[at]
-    member = mate[lo] == hi
-    assert not np.any((mate[lo] < 0) & (mate[hi] < 0)), "an edge has two free endpoints"
-    best = np.minimum(pc[lo], pc[hi])
-    ok = best <= cost64 + rel * np.maximum(np.abs(cost64), 1.0)
-    return int(np.sum(~ok & ~member))
 
 
 def test_6m_sampled_neighbour_lists(run6m):
