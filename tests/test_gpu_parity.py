@@ -80,18 +80,19 @@ def test_edge_costs_degenerate_and_modes(ngs):
             ref = O.edge_costs(scene, lo.cpu().numpy(), hi.cpu().numpy(), z, u, mode=mode)
             print(mode, S, "cost error / contract: max %.3g" % cost_excess(cost, ref))
             # every edge, every mode: the FP32 costs kept are within the
-            # contract, the others are FP64 (mode 1 included: a draw u_s within
-            # FP32 reach of pi goes to FP64)
+            # contract, the others extended precision, float-float by default
+            # (mode 1 included: a draw u_s within FP32 reach of pi goes there)
             assert cost_excess(cost, ref) <= 1.0
         finally:
             c.close()
 
 
-def test_refined_costs_are_fp64(ngs):
-    """Edges whose cost differs between cost_tol = 0 (FP32 as computed; FP64
-    only for near-degenerate merged covariances) and the default contract were
-    evaluated in FP64 (error estimate or near tie): they equal the oracle's FP64
-    cost rounded to FP32, within one FP32 spacing."""
+def test_refined_costs_match_fp64(ngs):
+    """Edges whose cost differs between cost_tol = 0 (FP32 as computed; the
+    extended path only for near-degenerate merged covariances) and the default
+    contract were evaluated in extended precision (float-float by default;
+    error estimate or near tie): they equal the oracle's FP64 cost rounded to
+    FP32, within one FP32 spacing."""
     scene = small_scene(9001, seed=7, kind="patch")
     costs = {}
     for tol in (0.0, COST_TOL):
@@ -105,7 +106,7 @@ def test_refined_costs_are_fp64(ngs):
     z, u = O.mc_draws(11, 2, 1)
     ref = O.edge_costs(scene, lo.cpu().numpy(), hi.cpu().numpy(), z, u)
     changed = costs[0.0] != costs[COST_TOL]
-    print("edges evaluated in FP64 beyond the pivot rule:", int(changed.sum()), "of", len(ref))
+    print("edges evaluated in extended precision beyond the pivot rule:", int(changed.sum()), "of", len(ref))
     assert changed.any()
     got = costs[COST_TOL][changed].astype(np.float64)
     r = ref[changed]
